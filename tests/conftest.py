@@ -1,0 +1,38 @@
+"""Shared fixtures. GPU tests are marked ``gpu``; everything else runs on CPU."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built library")
+    config.addinivalue_line("markers", "slow: takes more than a few seconds on CPU")
+
+
+@pytest.fixture(scope="session")
+def problem_4444():
+    """4^4, seed-0 links, m_W=-2, mu=0.3, antiperiodic t, Gaussian b (seed 1000):
+    dense H_W, x* = sign(H_W) b by eigendecomposition, and 16 critical eigenpairs."""
+    import synth
+    from oracle import deflation, matsign
+
+    dims = (4, 4, 4, 4)
+    u = synth.gauge_links(dims, 0)
+    b = synth.gaussian_source(dims, 1000)
+    h = deflation.sparse_hw(u, dims, -2.0, 0.3).toarray()
+    w, r = np.linalg.eig(h)
+    rinv = np.linalg.inv(r)
+    xs = r @ (np.sign(w.real) * (rinv @ b.ravel()))
+    order = np.argsort(np.abs(w))
+    idx = order[:16]
+    return {
+        "dims": dims, "links": u, "b": b, "h": h, "xstar": xs.reshape(b.shape),
+        "lam16": w[idx], "R16": r[:, idx], "L16": np.conj(rinv[idx, :]).T,
+        "gap16": float(abs(w[order[16]])), "eig": w,
+    }
