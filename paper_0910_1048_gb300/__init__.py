@@ -1,0 +1,337 @@
+"""Python binding of libovl.so, the GB300 library for x = sign(H_W(mu)) b.
+
+Thin ctypes marshalling over the C ABI declared in include/ovl.h: every function here has
+the C name, converts arguments (numpy arrays for host buffers, torch CUDA tensors for
+device buffers) and raises OvlError on a failing status. All arithmetic runs in the
+library's CUDA kernels; there is no Python or CPU fallback. Importing this package fails
+loudly when libovl.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libovl.so")
+
+# status codes (include/ovl.h)
+OVL_OK, OVL_PENDING = 0, 1
+OVL_EINVAL, OVL_ENOMEM, OVL_ECUDA, OVL_EBREAKDOWN = -1, -2, -3, -4
+OVL_ENOCONV, OVL_ETIMEOUT, OVL_EBUSY, OVL_EILLPOSED, OVL_ENOTFOUND = -5, -6, -7, -8, -9
+STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EBREAKDOWN",
+                -5: "ENOCONV", -6: "ETIMEOUT", -7: "EBUSY", -8: "EILLPOSED", -9: "ENOTFOUND"}
+OVL_F64, OVL_F32, OVL_F16R12 = 1, 2, 4
+OVL_C128, OVL_C64 = 0, 1
+OVL_DAGGER, OVL_GAMMA5, OVL_NATIVE, OVL_LINKS_F32, OVL_LINKS_F16R12 = 1, 2, 4, 8, 16
+OVL_DIRECT_2SL, OVL_MULTISHIFT_BICG = 0, 1
+OVL_PREC_F64, OVL_PREC_F32, OVL_PREC_F32_F16LINKS = 0, 1, 2
+OVL_RAT_NEUBERGER, OVL_RAT_ZOLOTAREV, OVL_RAT_CUSTOM = 0, 1, 2
+
+
+class OvlError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (STATUS_NAMES.get(status, "?"), status, msg))
+        self.status = status
+
+
+class ovl_sign_params(ctypes.Structure):
+    _fields_ = [
+        ("method", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("m_W", ctypes.c_double), ("mu", ctypes.c_double), ("tol", ctypes.c_double),
+        ("k_max", ctypes.c_int32), ("check_every", ctypes.c_int32), ("use_deflation", ctypes.c_int32),
+        ("rational_kind", ctypes.c_int32), ("s", ctypes.c_int32),
+        ("spec_lo", ctypes.c_double), ("spec_hi", ctypes.c_double),
+        ("omega", ctypes.POINTER(ctypes.c_double)), ("sigma", ctypes.POINTER(ctypes.c_double)),
+        ("host_io", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("fixed_k", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class ovl_sign_info(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("matvecs", ctypes.c_int32),
+        ("poles", ctypes.c_int32), ("est_error", ctypes.c_double), ("t_total_ms", ctypes.c_double),
+        ("t_small_ms", ctypes.c_double), ("residual", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ovl_server_cfg(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("streams", ctypes.c_int32)]
+
+
+class ovl_request(ctypes.Structure):
+    _fields_ = [
+        ("field_id", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("mu", ctypes.c_double), ("m_W", ctypes.c_double),
+        ("tol", ctypes.c_double), ("k_max", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("b", ctypes.c_void_p),
+    ]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int32
+_D = ctypes.c_double
+_PROTOS = {
+    "ovl_ctx_create": (_I, [_I, ctypes.POINTER(_P)]),
+    "ovl_ctx_destroy": (_I, [_P]),
+    "ovl_last_error": (ctypes.c_char_p, []),
+    "ovl_version": (ctypes.c_char_p, []),
+    "ovl_create_lattice": (_I, [_P, ctypes.POINTER(_I), _I, ctypes.POINTER(_P)]),
+    "ovl_destroy_lattice": (_I, [_P]),
+    "ovl_lattice_n": (ctypes.c_int64, [_P]),
+    "ovl_set_links": (_I, [_P, _P, _I, ctypes.c_uint32]),
+    "ovl_set_deflation": (_I, [_P, _D, _D, _I, _P, _P, _P, _I]),
+    "ovl_to_native": (_I, [_P, _I, _I, _P, _P, _P]),
+    "ovl_from_native": (_I, [_P, _I, _I, _P, _P, _P]),
+    "ovl_apply_DW": (_I, [_P, _D, _D, ctypes.c_uint32, _I, _I, _P, _P, _P]),
+    "ovl_sign_params_default": (None, [ctypes.POINTER(ovl_sign_params)]),
+    "ovl_apply_sign": (_I, [_P, ctypes.POINTER(ovl_sign_params), _I, _P, _P, ctypes.POINTER(ovl_sign_info), _P]),
+    "ovl_get_tridiag": (_I, [_P, _I, _I, ctypes.POINTER(_I), _P, _P, _P]),
+    "ovl_small_sign": (_I, [_I, _P, _P, _P, _P, _I]),
+    "ovl_rational_coeffs": (_I, [_I, _I, _D, _D, _D, _I, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "ovl_server_create": (_I, [_P, ctypes.POINTER(ovl_server_cfg), ctypes.POINTER(_P)]),
+    "ovl_server_add_field": (_I, [_P, _P, ctypes.POINTER(_I)]),
+    "ovl_submit": (_I, [_P, ctypes.POINTER(ovl_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "ovl_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(ovl_sign_info), _P]),
+    "ovl_server_destroy": (_I, [_P]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libovl.so is not built (%s): run `python -c 'import __graft_entry__ as g; g.build()'`"
+                          % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _PROTOS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _err(status):
+    return OvlError(status, lib.ovl_last_error().decode())
+
+
+def _check(status):
+    if status < 0:
+        raise _err(status)
+    return status
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError("expected a numpy array or torch tensor, got %r" % type(a))
+
+
+def _on_device(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _stream(stream, *tensors):
+    if stream is not None:
+        return stream
+    if any(_on_device(t) for t in tensors):
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return None
+
+
+def _dtype_code(a):
+    name = str(a.dtype)
+    if name.endswith("complex128"):
+        return OVL_C128
+    if name.endswith("complex64"):
+        return OVL_C64
+    raise TypeError("spinor buffers must be complex128 or complex64, got %s" % name)
+
+
+# ------------------------------------------------------------------ context, lattice
+def ovl_version() -> str:
+    return lib.ovl_version().decode()
+
+
+def ovl_ctx_create(device: int = 0):
+    h = _P()
+    _check(lib.ovl_ctx_create(device, ctypes.byref(h)))
+    return h
+
+
+def ovl_ctx_destroy(ctx):
+    _check(lib.ovl_ctx_destroy(ctx))
+
+
+def ovl_create_lattice(ctx, dims, t_bc: int = -1):
+    arr = (_I * 4)(*[int(d) for d in dims])
+    h = _P()
+    _check(lib.ovl_create_lattice(ctx, arr, int(t_bc), ctypes.byref(h)))
+    return h
+
+
+def ovl_destroy_lattice(lat):
+    _check(lib.ovl_destroy_lattice(lat))
+
+
+def ovl_lattice_n(lat) -> int:
+    return int(lib.ovl_lattice_n(lat))
+
+
+def ovl_set_links(lat, U, formats: int = OVL_F64):
+    if isinstance(U, np.ndarray):
+        U = np.ascontiguousarray(U, dtype=np.complex128)
+    _check(lib.ovl_set_links(lat, _ptr(U), 1 if _on_device(U) else 0, formats))
+
+
+def ovl_set_deflation(lat, m_W, mu, R, L, lam):
+    """R, L: [m][n] complex128 (canonical), lam: [m] complex128; host or device."""
+    if R is None or len(R) == 0:
+        _check(lib.ovl_set_deflation(lat, m_W, mu, 0, None, None, None, 0))
+        return
+    dev = _on_device(R)
+    if not dev:
+        R = np.ascontiguousarray(R, dtype=np.complex128)
+        L = np.ascontiguousarray(L, dtype=np.complex128)
+        lam = np.ascontiguousarray(lam, dtype=np.complex128)
+    _check(lib.ovl_set_deflation(lat, m_W, mu, int(R.shape[0]), _ptr(R), _ptr(L), _ptr(lam), 1 if dev else 0))
+
+
+def ovl_to_native(lat, inp, out, stream=None):
+    nrhs = inp.numel() // ovl_lattice_n(lat)
+    _check(lib.ovl_to_native(lat, _dtype_code(inp), nrhs, _ptr(inp), _ptr(out), _stream(stream, inp)))
+
+
+def ovl_from_native(lat, inp, out, stream=None):
+    nrhs = inp.numel() // ovl_lattice_n(lat)
+    _check(lib.ovl_from_native(lat, _dtype_code(inp), nrhs, _ptr(inp), _ptr(out), _stream(stream, inp)))
+
+
+def ovl_apply_DW(lat, m_W, mu, flags, inp, out, stream=None):
+    """out = D_W(mu) inp (flags OVL_DAGGER / OVL_GAMMA5 / OVL_NATIVE / OVL_LINKS_*); device tensors."""
+    n = ovl_lattice_n(lat)
+    nrhs = inp.numel() // n
+    if inp.numel() != nrhs * n or out.numel() != inp.numel() or out.dtype != inp.dtype:
+        raise ValueError("in/out must hold nrhs * n elements of the same dtype")
+    _check(lib.ovl_apply_DW(lat, m_W, mu, flags, _dtype_code(inp), nrhs, _ptr(inp), _ptr(out),
+                            _stream(stream, inp, out)))
+
+
+# ------------------------------------------------------------------ sign
+def ovl_sign_params_default(**kw) -> ovl_sign_params:
+    p = ovl_sign_params()
+    lib.ovl_sign_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def ovl_apply_sign(lat, params: ovl_sign_params, b, x, stream=None, raise_on_error=False):
+    """x = sign(H_W(mu)) b. b, x: complex128 [nrhs][...] as torch CUDA tensors, or numpy arrays
+    (then params.host_io is set). Returns (status, [info dict per rhs]); raises OvlError for
+    argument/CUDA/memory errors (and for every error if raise_on_error)."""
+    n = ovl_lattice_n(lat)
+    nrhs = (b.numel() if hasattr(b, "numel") else b.size) // n
+    host = isinstance(b, np.ndarray)
+    if host != isinstance(x, np.ndarray):
+        raise TypeError("b and x must both be host (numpy) or both device (torch) buffers")
+    if host:
+        params.host_io = 1
+        if b.dtype != np.complex128 or x.dtype != np.complex128:
+            raise TypeError("complex128 buffers required")
+    infos = (ovl_sign_info * nrhs)()
+    st = lib.ovl_apply_sign(lat, ctypes.byref(params), nrhs, _ptr(b), _ptr(x), infos, _stream(stream, b, x))
+    if st in (OVL_EINVAL, OVL_ENOMEM, OVL_ECUDA) or (raise_on_error and st < 0):
+        raise _err(st)
+    return st, [i.as_dict() for i in infos]
+
+
+def ovl_get_tridiag(lat, rhs: int = 0, k_cap: int = 100000):
+    k = _I()
+    st = lib.ovl_get_tridiag(lat, rhs, 0, ctypes.byref(k), None, None, None)
+    if st not in (OVL_OK, OVL_EINVAL):
+        raise _err(st)
+    kk = k.value
+    a = np.zeros(kk, np.complex128)
+    b = np.zeros(max(kk - 1, 0), np.complex128)
+    d = np.zeros(max(kk - 1, 0), np.complex128)
+    _check(lib.ovl_get_tridiag(lat, rhs, kk, ctypes.byref(k), _ptr(a), _ptr(b) if kk > 1 else None,
+                               _ptr(d) if kk > 1 else None))
+    return a, b, d
+
+
+# ------------------------------------------------------------------ host-side pieces
+def ovl_small_sign(alpha, beta, delta, method: int = 0):
+    """(status, y) with y = sign(T) e_1 for the tridiagonal (alpha, beta super, delta sub)."""
+    a = np.ascontiguousarray(alpha, dtype=np.complex128)
+    b = np.ascontiguousarray(beta, dtype=np.complex128)
+    d = np.ascontiguousarray(delta, dtype=np.complex128)
+    y = np.zeros(len(a), np.complex128)
+    st = lib.ovl_small_sign(len(a), _ptr(a), _ptr(b) if len(b) else None, _ptr(d) if len(d) else None, _ptr(y),
+                            method)
+    if st == OVL_EINVAL:
+        raise _err(st)
+    return st, y
+
+
+def ovl_rational_coeffs(kind, s, lo, hi, eps=0.0, s_cap=512):
+    om = np.zeros(s_cap)
+    sg = np.zeros(s_cap)
+    so = _I()
+    err = _D()
+    _check(lib.ovl_rational_coeffs(kind, s, lo, hi, eps, s_cap, _ptr(om), _ptr(sg), ctypes.byref(so),
+                                   ctypes.byref(err)))
+    return om[:so.value].copy(), sg[:so.value].copy(), err.value
+
+
+# ------------------------------------------------------------------ serving
+def ovl_server_create(ctx, mem_budget_bytes: int, max_slots: int = 8, streams: int = 4):
+    cfg = ovl_server_cfg(mem_budget_bytes, max_slots, streams)
+    h = _P()
+    _check(lib.ovl_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def ovl_server_add_field(srv, lat) -> int:
+    fid = _I()
+    _check(lib.ovl_server_add_field(srv, lat, ctypes.byref(fid)))
+    return fid.value
+
+
+def ovl_submit(srv, field_id, b: np.ndarray, mu, tol, m_W=-2.0, k_max=600, precision=OVL_PREC_F64, nrhs=None):
+    b = np.ascontiguousarray(b, dtype=np.complex128)
+    req = ovl_request(field_id, int(nrhs if nrhs is not None else (b.shape[0] if b.ndim > 1 else 1)),
+                      mu, m_W, tol, k_max, precision, b.ctypes.data)
+    t = ctypes.c_uint64()
+    _check(lib.ovl_submit(srv, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def ovl_poll(srv, ticket, nrhs, x_out: np.ndarray | None = None):
+    """Returns (status, infos); status OVL_PENDING while running."""
+    infos = (ovl_sign_info * max(nrhs, 1))()
+    st = lib.ovl_poll(srv, ticket, infos, _ptr(x_out) if x_out is not None else None)
+    if st in (OVL_EINVAL, OVL_ENOTFOUND, OVL_ECUDA, OVL_ENOMEM):
+        raise _err(st)
+    return st, [i.as_dict() for i in infos]
+
+
+def ovl_server_destroy(srv):
+    _check(lib.ovl_server_destroy(srv))

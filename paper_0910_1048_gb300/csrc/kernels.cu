@@ -1,0 +1,561 @@
+// CUDA kernels of the sign(H_W(mu)) b path for sm_103a.
+//
+// Data layout in HBM: fields are component-major ("native"): element (rhs, c, site) at
+// (rhs*12 + c)*V + site with c = spin*3 + colour, so the 32 threads of a warp (32
+// consecutive sites) read one contiguous 256 B (FP32) / 512 B (FP64) segment per
+// component; links likewise [dir][comp][V]. Reductions are deterministic: fixed-order
+// warp-shuffle and shared-memory trees per block, block partials to global memory, and
+// the last block to finish (atomic ticket) sums the partials in block order.
+#include <cuda_fp16.h>
+
+#include "kernels.h"
+#include "wilson.cuh"
+
+namespace ovl {
+
+template <class R> struct V2;
+template <> struct V2<double> { using T = double2; };
+template <> struct V2<float> { using T = float2; };
+
+template <class R>
+__device__ __forceinline__ cplx<R> ldc(const typename V2<R>::T* p, size_t i) {
+  typename V2<R>::T v = p[i];
+  return mk<R>(v.x, v.y);
+}
+template <class R>
+__device__ __forceinline__ void stc(typename V2<R>::T* p, size_t i, cplx<R> a) {
+  typename V2<R>::T v;
+  v.x = a.re;
+  v.y = a.im;
+  p[i] = v;
+}
+
+__device__ __forceinline__ int lin_tid() { return threadIdx.x + threadIdx.y * blockDim.x; }
+__device__ __forceinline__ int lin_nthreads() { return blockDim.x * blockDim.y; }
+
+// Sum NV doubles over the block; result valid in thread 0. Block size multiple of 32.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sm[NV][32];
+  const int t = lin_tid();
+  const int lane = t & 31, warp = t >> 5, nw = lin_nthreads() >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sm[i][warp] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      v[i] = lane < nw ? sm[i][lane] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
+    }
+  }
+  __syncthreads();
+}
+
+// Write this block's NV partials; returns true in every thread of the last block to arrive.
+// The counter is reset to 0 by the last block so the next launch starts clean.
+template <int NV>
+__device__ __forceinline__ bool publish_partials(double (&v)[NV], double* part, unsigned* count) {
+  __shared__ bool last;
+  if (lin_tid() == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) part[(size_t)blockIdx.x * NV + i] = v[i];
+    __threadfence();
+    unsigned t = atomicAdd(count, 1u);
+    last = (t == gridDim.x - 1);
+    if (last) *count = 0u;
+  }
+  __syncthreads();
+  return last;
+}
+
+// Fixed-order sum of nblk partials (NV each) by the last block; result in thread 0.
+template <int NV>
+__device__ __forceinline__ void reduce_partials(const double* part, int nblk, double (&v)[NV]) {
+  __threadfence();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = 0.0;
+  for (int b = lin_tid(); b < nblk; b += lin_nthreads())
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __ldcg(part + (size_t)b * NV + i);
+  block_sum<NV>(v);
+}
+
+// ------------------------------------------------------------------ layout conversion
+template <class Tin, class Tout>
+__global__ void k_to_native(int vol, int nrhs, const Tin* in, Tout* out) {
+  size_t n = (size_t)vol * 12;
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (e >= n) return;
+  int c = (int)(e / vol), s = (int)(e % vol);
+  Tin v = in[(size_t)r * n + (size_t)s * 12 + c];
+  Tout o;
+  o.x = v.x;
+  o.y = v.y;
+  out[(size_t)r * n + e] = o;
+}
+
+template <class Tin, class Tout>
+__global__ void k_from_native(int vol, int nrhs, const Tin* in, Tout* out) {
+  size_t n = (size_t)vol * 12;
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  if (e >= n) return;
+  int c = (int)(e / vol), s = (int)(e % vol);
+  Tin v = in[(size_t)r * n + e];
+  Tout o;
+  o.x = v.x;
+  o.y = v.y;
+  out[(size_t)r * n + (size_t)s * 12 + c] = o;
+}
+
+template <class A, class B>
+static cudaError_t conv(const Geom& g, int nrhs, const void* in, void* out, bool to, cudaStream_t st) {
+  size_t n = (size_t)g.vol * 12;
+  dim3 grid((unsigned)((n + 255) / 256), nrhs);
+  if (to)
+    k_to_native<A, B><<<grid, 256, 0, st>>>(g.vol, nrhs, (const A*)in, (B*)out);
+  else
+    k_from_native<A, B><<<grid, 256, 0, st>>>(g.vol, nrhs, (const A*)in, (B*)out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_native(const Geom& g, int nrhs, bool in_f64, const void* in, bool out_f64, void* out, cudaStream_t st) {
+  if (in_f64 && out_f64) return conv<double2, double2>(g, nrhs, in, out, true, st);
+  if (in_f64) return conv<double2, float2>(g, nrhs, in, out, true, st);
+  if (out_f64) return conv<float2, double2>(g, nrhs, in, out, true, st);
+  return conv<float2, float2>(g, nrhs, in, out, true, st);
+}
+cudaError_t launch_from_native(const Geom& g, int nrhs, bool in_f64, const void* in, bool out_f64, void* out, cudaStream_t st) {
+  if (in_f64 && out_f64) return conv<double2, double2>(g, nrhs, in, out, false, st);
+  if (in_f64) return conv<double2, float2>(g, nrhs, in, out, false, st);
+  if (out_f64) return conv<float2, double2>(g, nrhs, in, out, false, st);
+  return conv<float2, float2>(g, nrhs, in, out, false, st);
+}
+
+// ------------------------------------------------------------------ link ingest
+__global__ void k_ingest_links(int vol, const double2* ucan, double2* u64, float2* u32, uint32_t* u16) {
+  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // over 4*9*V
+  if (e >= (size_t)36 * vol) return;
+  int s = (int)(e % vol);
+  int k = (int)((e / vol) % 9);
+  int mu = (int)(e / ((size_t)9 * vol));
+  double2 v = ucan[((size_t)mu * vol + s) * 9 + k];
+  if (u64) u64[e] = v;
+  if (u32) u32[e] = make_float2((float)v.x, (float)v.y);
+  if (u16 && k < 6) {
+    __half2 h = __floats2half2_rn((float)v.x, (float)v.y);
+    u16[((size_t)mu * 6 + k) * vol + s] = *reinterpret_cast<uint32_t*>(&h);
+  }
+}
+
+cudaError_t launch_ingest_links(const Geom& g, const double* ucan, double2* u64, float2* u32, uint32_t* u16, cudaStream_t st) {
+  size_t n = (size_t)36 * g.vol;
+  k_ingest_links<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g.vol, (const double2*)ucan, u64, u32, u16);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ spinor loaders
+template <class R, bool NATIVE>
+struct Loader {
+  const typename V2<R>::T* p;
+  int vol;
+  bool g5;
+  __device__ __forceinline__ void operator()(int s, Spin<R>& o) const {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      size_t i = NATIVE ? (size_t)c * vol + s : (size_t)s * 12 + c;
+      o.c[c / 3][c % 3] = ldc<R>(p, i);
+    }
+    if (g5) gamma5_inplace(o);
+  }
+};
+
+template <class R, bool NATIVE>
+__device__ __forceinline__ void store_spin(typename V2<R>::T* p, int vol, int s, const Spin<R>& o) {
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    size_t i = NATIVE ? (size_t)c * vol + s : (size_t)s * 12 + c;
+    stc<R>(p, i, o.c[c / 3][c % 3]);
+  }
+}
+
+// ------------------------------------------------------------------ apply D_W
+template <class R, int LF, bool NIN, bool NOUT>
+__global__ void __launch_bounds__(kBlock) k_dslash(Geom g, Links U, HopCoef<R> c, bool g5_in, bool g5_out,
+                                                   const typename V2<R>::T* in, typename V2<R>::T* out) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.vol) return;
+  size_t off = (size_t)blockIdx.y * 12 * g.vol;
+  Loader<R, NIN> ld{in + off, g.vol, g5_in};
+  Spin<R> o;
+  dslash_site<LF, R>(g, U, s, c, ld, o);
+  if (g5_out) gamma5_inplace(o);
+  store_spin<R, NOUT>(out + off, g.vol, s, o);
+}
+
+template <class R, int LF>
+static cudaError_t dslash_t(const Geom& g, const Links& U, double m_w, double mu, bool gi, bool go, bool nin, bool nout,
+                            int nrhs, const void* in, void* out, cudaStream_t st) {
+  HopCoef<R> c = hop_coef<R>(m_w, mu);
+  dim3 grid((g.vol + kBlock - 1) / kBlock, nrhs);
+  using T = typename V2<R>::T;
+  const T* i = (const T*)in;
+  T* o = (T*)out;
+  if (nin && nout)
+    k_dslash<R, LF, true, true><<<grid, kBlock, 0, st>>>(g, U, c, gi, go, i, o);
+  else if (nin)
+    k_dslash<R, LF, true, false><<<grid, kBlock, 0, st>>>(g, U, c, gi, go, i, o);
+  else if (nout)
+    k_dslash<R, LF, false, true><<<grid, kBlock, 0, st>>>(g, U, c, gi, go, i, o);
+  else
+    k_dslash<R, LF, false, false><<<grid, kBlock, 0, st>>>(g, U, c, gi, go, i, o);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dslash(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, bool g5_in,
+                          bool g5_out, bool native_in, bool native_out, int nrhs, const void* in, void* out,
+                          cudaStream_t st) {
+  if (f64) return dslash_t<double, LINK_F64>(g, U, m_w, mu, g5_in, g5_out, native_in, native_out, nrhs, in, out, st);
+  if (lf == LINK_F16R12)
+    return dslash_t<float, LINK_F16R12>(g, U, m_w, mu, g5_in, g5_out, native_in, native_out, nrhs, in, out, st);
+  return dslash_t<float, LINK_F32>(g, U, m_w, mu, g5_in, g5_out, native_in, native_out, nrhs, in, out, st);
+}
+
+// ------------------------------------------------------------------ Lanczos: start
+// part layout for this kernel: [nrhs][nblk][4] = (|r|^2, Re r^H r~, Im r^H r~, unused)
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_lz_start(Geom g, LzDev lz, typename V2<R>::T* vh, typename V2<R>::T* wh,
+                                                     double2* xp, const double2* b, int m, const double2* Rv,
+                                                     const double2* Lv, const double* lam_sign, const double2* dots) {
+  using T = typename V2<R>::T;
+  const int rhs = blockIdx.y;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t n = (size_t)12 * g.vol;
+  double acc[4] = {0, 0, 0, 0};
+  if (s < g.vol) {
+    T* v1 = vh + (size_t)rhs * (lz.kmax + 1) * n;  // column 1
+    T* w1 = wh + (size_t)(1 * lz.nrhs + rhs) * n;  // slot (1 & 1) = 1
+    const double2* dr = dots + (size_t)rhs * 2 * m;
+    for (int c = 0; c < 12; ++c) {
+      zd bv = ldc<double>(b, (size_t)rhs * n + (size_t)s * 12 + c);
+      zd r = bv, rt = bv, x = mk(0.0, 0.0);
+      for (int i = 0; i < m; ++i) {
+        zd ci = ldc<double>(dr, i), di = ldc<double>(dr, m + i);
+        zd ri = ldc<double>(Rv, (size_t)i * n + (size_t)c * g.vol + s);
+        zd li = ldc<double>(Lv, (size_t)i * n + (size_t)c * g.vol + s);
+        r = r - ci * ri;
+        x = x + lam_sign[i] * (ci * ri);
+        rt = rt - di * li;
+      }
+      size_t e = (size_t)c * g.vol + s;
+      if (xp) stc<double>(xp, (size_t)rhs * n + e, x);
+      stc<R>(v1, e, mk<R>((R)r.re, (R)r.im));
+      stc<R>(w1, e, mk<R>((R)rt.re, (R)rt.im));
+      acc[0] += norm2(r);
+      zd ip = cdot(r, rt);
+      acc[1] += ip.re;
+      acc[2] += ip.im;
+    }
+  }
+  block_sum<4>(acc);
+  double* part = lz.part + (size_t)rhs * lz.nblk * 4;
+  if (publish_partials<4>(acc, part, lz.count + rhs)) {
+    reduce_partials<4>(part, gridDim.x, acc);
+    if (lin_tid() == 0) {
+      double nr2 = acc[0];
+      double b0 = sqrt(nr2);
+      // v1 = r / beta0, w1 = r~ / (v1^H r~) = r~ * beta0 / (r^H r~)
+      zd ip = mk(acc[1], acc[2]);
+      double den = norm2(ip);
+      size_t o = (size_t)rhs * (lz.kmax + 2);
+      lz.beta0[rhs] = b0;
+      lz.sv[o + 1] = 1.0 / b0;
+      lz.sw[o + 1] = make_double2(b0 * ip.re / den, -b0 * ip.im / den);
+      lz.vnorm[o + 1] = 1.0;
+      lz.j[rhs] = 1;
+      // 3: r = 0 (b lies in the deflated space, x = x_P); 1: r^H r~ = 0 (breakdown at start)
+      lz.status[rhs] = nr2 == 0.0 ? 3 : (den > 0.0 ? 0 : 1);
+    }
+  }
+}
+
+// c_i = l_i^H b, d_i = r_i^H b for i < m; partials [nrhs][m][nblk][4], summed by the last block.
+__global__ void __launch_bounds__(kBlock) k_defl_dots(Geom g, int m, const double2* b, const double2* Rv,
+                                                      const double2* Lv, double* part, unsigned* count,
+                                                      double2* dots) {
+  const int rhs = blockIdx.y;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t n = (size_t)12 * g.vol;
+  __shared__ bool last;
+  for (int i = 0; i < m; ++i) {
+    double acc[4] = {0, 0, 0, 0};
+    if (s < g.vol) {
+      for (int c = 0; c < 12; ++c) {
+        zd bv = ldc<double>(b, (size_t)rhs * n + (size_t)s * 12 + c);
+        zd li = ldc<double>(Lv, (size_t)i * n + (size_t)c * g.vol + s);
+        zd ri = ldc<double>(Rv, (size_t)i * n + (size_t)c * g.vol + s);
+        zd a = cdot(li, bv), d = cdot(ri, bv);
+        acc[0] += a.re;
+        acc[1] += a.im;
+        acc[2] += d.re;
+        acc[3] += d.im;
+      }
+    }
+    block_sum<4>(acc);
+    if (threadIdx.x == 0) {
+      double* p = part + (((size_t)rhs * m + i) * gridDim.x + blockIdx.x) * 4;
+      for (int q = 0; q < 4; ++q) p[q] = acc[q];
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned t = atomicAdd(count + rhs, 1u);
+    last = (t == gridDim.x - 1);
+    if (last) count[rhs] = 0u;
+  }
+  __syncthreads();
+  if (!last) return;
+  for (int i = 0; i < m; ++i) {
+    double acc[4];
+    reduce_partials<4>(part + ((size_t)rhs * m + i) * gridDim.x * 4, gridDim.x, acc);
+    if (threadIdx.x == 0) {
+      dots[(size_t)rhs * 2 * m + i] = make_double2(acc[0], acc[1]);
+      dots[(size_t)rhs * 2 * m + m + i] = make_double2(acc[2], acc[3]);
+    }
+  }
+}
+
+cudaError_t launch_lanczos_start(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, const double2* b, int m,
+                                 const double2* R, const double2* L, const double* lam_sign, double2* dots,
+                                 cudaStream_t st) {
+  dim3 grid((g.vol + kBlock - 1) / kBlock, lz.nrhs);
+  if (m > 0) {
+    k_defl_dots<<<grid, kBlock, 0, st>>>(g, m, b, R, L, lz.part, lz.count, dots);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (f64)
+    k_lz_start<double><<<grid, kBlock, 0, st>>>(g, lz, (double2*)vec.vh, (double2*)vec.wh, vec.xp, b, m, R, L,
+                                                 lam_sign, dots);
+  else
+    k_lz_start<float><<<grid, kBlock, 0, st>>>(g, lz, (float2*)vec.vh, (float2*)vec.wh, vec.xp, b, m, R, L, lam_sign,
+                                                dots);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Lanczos: one step
+// Pair stencil: Av_j = sv_j H(mu) vhat_j, Aw_j = sw_j H(-mu) what_j (H(mu)^H = H(-mu)),
+// alpha_j = w_j^H A v_j = conj(sw_j) sum_x what_j(x)^H Av_j(x).
+// Block (kPairSites, 2): threadIdx.y = 0 applies H(mu) to vhat, = 1 applies H(-mu) to what,
+// for the same kPairSites sites, so each thread holds one stencil's registers and the two
+// halves of the block share the link lines in L1.
+template <class R, int LF>
+__global__ void __launch_bounds__(2 * kPairSites) k_lz_pair(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm, LzDev lz,
+                                                            const typename V2<R>::T* vh, const typename V2<R>::T* wh,
+                                                            typename V2<R>::T* av, typename V2<R>::T* aw) {
+  using T = typename V2<R>::T;
+  const int rhs = blockIdx.y;
+  if (lz.status[rhs]) return;
+  const int j = lz.j[rhs];
+  const size_t n = (size_t)12 * g.vol;
+  const size_t o = (size_t)rhs * (lz.kmax + 2);
+  const double2 swd = lz.sw[o + j];
+  const T* vj = vh + ((size_t)rhs * (lz.kmax + 1) + (j - 1)) * n;
+  const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
+  const int s = blockIdx.x * kPairSites + threadIdx.x;
+  const bool is_w = threadIdx.y == 1;
+  double acc[2] = {0, 0};
+  if (s < g.vol) {
+    Spin<R> ov;
+    if (!is_w) {
+      dslash_site<LF, R>(g, U, s, cp, Loader<R, true>{vj, g.vol, false}, ov);
+      const R sv = (R)lz.sv[o + j];
+      cplx<R> a = mk<R>(0, 0);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        cplx<R> x = sv * ov.c[c / 3][c % 3];
+        if (c >= 6) x = -x;  // gamma5
+        stc<R>(av + (size_t)rhs * n, (size_t)c * g.vol + s, x);
+        a = a + cdot(ldc<R>(wj, (size_t)c * g.vol + s), x);
+      }
+      acc[0] = (double)a.re;
+      acc[1] = (double)a.im;
+    } else {
+      dslash_site<LF, R>(g, U, s, cm, Loader<R, true>{wj, g.vol, false}, ov);
+      const cplx<R> sw = mk<R>((R)swd.x, (R)swd.y);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        cplx<R> y = sw * ov.c[c / 3][c % 3];
+        if (c >= 6) y = -y;  // gamma5
+        stc<R>(aw + (size_t)rhs * n, (size_t)c * g.vol + s, y);
+      }
+    }
+  }
+  block_sum<2>(acc);
+  double* part = lz.part + (size_t)rhs * lz.nblk * 4;
+  double pv[4] = {acc[0], acc[1], 0, 0};
+  if (publish_partials<4>(pv, part, lz.count + rhs)) {
+    reduce_partials<4>(part, gridDim.x, pv);
+    if (lin_tid() == 0) {
+      zd sum = mk(pv[0], pv[1]);
+      zd alpha = conj(mk(swd.x, swd.y)) * sum;
+      lz.alpha[o + j] = make_double2(alpha.re, alpha.im);
+    }
+  }
+}
+
+// vhat_{j+1} = Av_j - alpha_j v_j - beta_{j-1} v_{j-1}
+// what_{j+1} = Aw_j - conj(alpha_j) w_j - conj(delta_{j-1}) w_{j-1}    (Eqs. 2sided1/2)
+// then delta_j = sqrt|what^H vhat|, beta_j = what^H vhat / delta_j (scaling reading).
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_lz_update(Geom g, LzDev lz, typename V2<R>::T* vh, typename V2<R>::T* wh,
+                                                      const typename V2<R>::T* av, const typename V2<R>::T* aw) {
+  using T = typename V2<R>::T;
+  const int rhs = blockIdx.y;
+  if (lz.status[rhs]) return;
+  const int j = lz.j[rhs];
+  const size_t n = (size_t)12 * g.vol;
+  const size_t o = (size_t)rhs * (lz.kmax + 2);
+  const zd alpha = ldc<double>(lz.alpha, o + j);
+  const double svj = lz.sv[o + j];
+  const zd swj = ldc<double>(lz.sw, o + j);
+  zd cv1 = svj * alpha, cw1 = swj * conj(alpha), cv2 = mk(0.0, 0.0), cw2 = mk(0.0, 0.0);
+  if (j > 1) {
+    cv2 = lz.sv[o + j - 1] * ldc<double>(lz.beta, o + j - 1);
+    cw2 = lz.delta[o + j - 1] * ldc<double>(lz.sw, o + j - 1);
+  }
+  const cplx<R> a1 = mk<R>((R)cv1.re, (R)cv1.im), a2 = mk<R>((R)cv2.re, (R)cv2.im);
+  const cplx<R> b1 = mk<R>((R)cw1.re, (R)cw1.im), b2 = mk<R>((R)cw2.re, (R)cw2.im);
+  const T* vj = vh + ((size_t)rhs * (lz.kmax + 1) + (j - 1)) * n;
+  const T* vjm = vh + ((size_t)rhs * (lz.kmax + 1) + (j > 1 ? j - 2 : 0)) * n;
+  T* vnew = vh + ((size_t)rhs * (lz.kmax + 1) + j) * n;
+  const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
+  T* wnew = wh + ((size_t)((j + 1) & 1) * lz.nrhs + rhs) * n;  // holds what_{j-1} until overwritten
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[4] = {0, 0, 0, 0};
+  if (s < g.vol) {
+    R ipr = 0, ipi = 0, nv = 0, nw = 0;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      size_t e = (size_t)c * g.vol + s;
+      cplx<R> x = ldc<R>(av + (size_t)rhs * n, e) - a1 * ldc<R>(vj, e);
+      cplx<R> y = ldc<R>(aw + (size_t)rhs * n, e) - b1 * ldc<R>(wj, e);
+      if (j > 1) {
+        x = x - a2 * ldc<R>(vjm, e);
+        y = y - b2 * ldc<R>(wnew, e);
+      }
+      stc<R>(vnew, e, x);
+      stc<R>(wnew, e, y);
+      cplx<R> ip = cdot(y, x);
+      ipr += ip.re;
+      ipi += ip.im;
+      nv += norm2(x);
+      nw += norm2(y);
+    }
+    acc[0] = ipr;
+    acc[1] = ipi;
+    acc[2] = nv;
+    acc[3] = nw;
+  }
+  block_sum<4>(acc);
+  double* part = lz.part + (size_t)rhs * lz.nblk * 4;
+  if (publish_partials<4>(acc, part, lz.count + rhs)) {
+    reduce_partials<4>(part, gridDim.x, acc);
+    if (lin_tid() == 0) {
+      zd ip = mk(acc[0], acc[1]);
+      double aip = sqrt(norm2(ip));
+      if (!(aip > 1e-14 * sqrt(acc[2] * acc[3])) || !(aip < 1e300)) {
+        lz.status[rhs] = 1;  // breakdown (or non-finite)
+      } else {
+        double d = sqrt(aip);
+        zd bt = (1.0 / d) * ip;
+        lz.delta[o + j] = d;
+        lz.beta[o + j] = make_double2(bt.re, bt.im);
+        lz.sv[o + j + 1] = 1.0 / d;
+        double bb = norm2(bt);  // 1/conj(beta) = beta / |beta|^2
+        lz.sw[o + j + 1] = make_double2(bt.re / bb, bt.im / bb);
+        lz.vnorm[o + j + 1] = sqrt(acc[2]) / d;
+        lz.j[rhs] = j + 1;
+      }
+    }
+  }
+}
+
+cudaError_t launch_lanczos_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, const LzDev& lz,
+                                const LzVecs& vec, cudaStream_t st) {
+  dim3 grid((g.vol + kBlock - 1) / kBlock, lz.nrhs);
+  dim3 pgrid((g.vol + kPairSites - 1) / kPairSites, lz.nrhs), pblock(kPairSites, 2);
+  if (f64) {
+    k_lz_pair<double, LINK_F64><<<pgrid, pblock, 0, st>>>(g, U, hop_coef<double>(m_w, mu), hop_coef<double>(m_w, -mu),
+                                                          lz, (const double2*)vec.vh, (const double2*)vec.wh,
+                                                          (double2*)vec.av, (double2*)vec.aw);
+    k_lz_update<double><<<grid, kBlock, 0, st>>>(g, lz, (double2*)vec.vh, (double2*)vec.wh, (const double2*)vec.av,
+                                                  (const double2*)vec.aw);
+  } else {
+    if (lf == LINK_F16R12)
+      k_lz_pair<float, LINK_F16R12><<<pgrid, pblock, 0, st>>>(g, U, hop_coef<float>(m_w, mu),
+                                                              hop_coef<float>(m_w, -mu), lz, (const float2*)vec.vh,
+                                                              (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
+    else
+      k_lz_pair<float, LINK_F32><<<pgrid, pblock, 0, st>>>(g, U, hop_coef<float>(m_w, mu), hop_coef<float>(m_w, -mu),
+                                                           lz, (const float2*)vec.vh, (const float2*)vec.wh,
+                                                           (float2*)vec.av, (float2*)vec.aw);
+    k_lz_update<float><<<grid, kBlock, 0, st>>>(g, lz, (float2*)vec.vh, (float2*)vec.wh, (const float2*)vec.av,
+                                                 (const float2*)vec.aw);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ combine
+// x (canonical complex128) = x_P + sum_{j=1..k} coef_j vhat_j  (x = x_P + beta V_k y with the
+// column scales folded into coef on the host). One thread per (component, site).
+template <class R>
+__global__ void __launch_bounds__(256) k_lz_combine(int vol, int kmax, const int* kr, const typename V2<R>::T* vh,
+                                                    const double2* xp, const double2* coef, int kcoef, double2* x) {
+  __shared__ double2 cs[256];
+  const int rhs = blockIdx.y;
+  const int k = kr[rhs];  // this rhs's Krylov dimension (columns beyond it are never read)
+  const size_t n = (size_t)12 * vol;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const typename V2<R>::T* base = vh + (size_t)rhs * (kmax + 1) * n;
+  zd acc = mk(0.0, 0.0);
+  for (int j0 = 0; j0 < k; j0 += 256) {
+    __syncthreads();
+    if (j0 + (int)threadIdx.x < k) cs[threadIdx.x] = coef[(size_t)rhs * kcoef + j0 + threadIdx.x];
+    __syncthreads();
+    if (e < n) {
+      int jn = min(256, k - j0);
+      for (int jj = 0; jj < jn; ++jj) {
+        cplx<R> v = ldc<R>(base, (size_t)(j0 + jj) * n + e);
+        zd vd = mk((double)v.re, (double)v.im);
+        double2 c = cs[jj];
+        acc = acc + mk(c.x, c.y) * vd;
+      }
+    }
+  }
+  if (e >= n) return;
+  if (xp) acc = acc + ldc<double>(xp, (size_t)rhs * n + e);
+  int c = (int)(e / vol), s = (int)(e % vol);
+  x[(size_t)rhs * n + (size_t)s * 12 + c] = make_double2(acc.re, acc.im);
+}
+
+cudaError_t launch_lanczos_combine(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, const int* kr,
+                                   const double2* coef, int kcoef, double2* x, cudaStream_t st) {
+  size_t n = (size_t)12 * g.vol;
+  dim3 grid((unsigned)((n + 255) / 256), lz.nrhs);
+  if (f64)
+    k_lz_combine<double><<<grid, 256, 0, st>>>(g.vol, lz.kmax, kr, (const double2*)vec.vh, vec.xp, coef, kcoef, x);
+  else
+    k_lz_combine<float><<<grid, 256, 0, st>>>(g.vol, lz.kmax, kr, (const float2*)vec.vh, vec.xp, coef, kcoef, x);
+  return cudaGetLastError();
+}
+
+}  // namespace ovl

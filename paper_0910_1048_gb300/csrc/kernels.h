@@ -1,0 +1,66 @@
+// Launchers of the library's CUDA kernels (implemented in kernels.cu).
+#pragma once
+
+#include "common.h"
+
+namespace ovl {
+
+constexpr int kBlock = 128;     // threads per block of the site-parallel kernels
+constexpr int kPairSites = 64;  // sites per block of the pair stencil (x2 threads)
+
+// Device state of the two-sided Lanczos recurrences for nrhs right-hand sides.
+// Index conventions: column j = 1..kmax+1 of the basis; scalars indexed by j.
+struct LzDev {
+  int kmax = 0;
+  int nrhs = 0;
+  int nblk = 0;             // partial slots per rhs (>= blocks of any reduction kernel)
+  int* j = nullptr;         // [nrhs] current step (1-based)
+  int* status = nullptr;    // [nrhs] 0 running, 1 breakdown
+  double* sv = nullptr;     // [nrhs][kmax+2] v_j = sv_j * vhat_j
+  double2* sw = nullptr;    // [nrhs][kmax+2] w_j = sw_j * what_j
+  double2* alpha = nullptr; // [nrhs][kmax+2]
+  double2* beta = nullptr;  // [nrhs][kmax+2] super-diagonal beta_j = h_{j,j+1}
+  double* delta = nullptr;  // [nrhs][kmax+2] sub-diagonal delta_j = h_{j+1,j}
+  double* vnorm = nullptr;  // [nrhs][kmax+2] ||v_j||
+  double* beta0 = nullptr;  // [nrhs] ||r||
+  double* part = nullptr;   // [nrhs][nblk][4] block partials
+  unsigned* count = nullptr;// [nrhs] last-block counters (kept at 0 between launches)
+};
+
+// Layout conversion canonical [nrhs][V][12] <-> native [nrhs][12][V]; element types by flag.
+cudaError_t launch_to_native(const Geom& g, int nrhs, bool in_f64, const void* in, bool out_f64, void* out, cudaStream_t st);
+cudaError_t launch_from_native(const Geom& g, int nrhs, bool in_f64, const void* in, bool out_f64, void* out, cudaStream_t st);
+
+// Links: canonical complex128 [4][V][3][3] (device) -> [4][9][V] f64 / f32, [4][6][V] f16 rows 0-1.
+cudaError_t launch_ingest_links(const Geom& g, const double* ucan, double2* u64, float2* u32, uint32_t* u16, cudaStream_t st);
+
+// out = [g5^go] D_W(sign*mu) [g5^gi] in; dtype f64 (FP64 links) or f32 (lf = F32 / F16R12).
+cudaError_t launch_dslash(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
+                          bool g5_in, bool g5_out, bool native_in, bool native_out, int nrhs,
+                          const void* in, void* out, cudaStream_t st);
+
+// ---- direct two-sided Lanczos (Algorithm 4), per-step kernels
+// vh: [nrhs][kmax+1][12][V], wh: [2][nrhs][12][V], av/aw: [nrhs][12][V]; element type by f64.
+struct LzVecs {
+  void* vh = nullptr;
+  void* wh = nullptr;
+  void* av = nullptr;
+  void* aw = nullptr;
+  double2* xp = nullptr;    // [nrhs][12][V] FP64 deflated part x_P (nullptr without deflation)
+};
+
+// Start: from b (canonical complex128, device) build vhat_1 = r, what_1 = r~ and the scales.
+// With m > 0 deflation vectors R, L (native FP64 [m][12][V]) and lam (host, 2m doubles):
+// x_P = R sign(Lambda) L^H b, r = b - R L^H b, r~ = b - L R^H b (Algorithm 4, first lines).
+cudaError_t launch_lanczos_start(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, const double2* b,
+                                 int m, const double2* R, const double2* L, const double* lam_sign,
+                                 double2* dots, cudaStream_t st);
+// One step j (read from lz.j): pair stencil + alpha, then the biorthogonal update.
+cudaError_t launch_lanczos_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
+                                const LzDev& lz, const LzVecs& vec, cudaStream_t st);
+// x = x_P + sum_{j<=k_r} coef_j vhat_j, written canonical complex128; coef [nrhs][kcoef],
+// kr [nrhs] (device) the Krylov dimension of each rhs.
+cudaError_t launch_lanczos_combine(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, const int* kr,
+                                   const double2* coef, int kcoef, double2* x, cudaStream_t st);
+
+}  // namespace ovl

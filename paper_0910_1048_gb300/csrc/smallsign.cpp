@@ -1,0 +1,296 @@
+// y = sign(H_k) e_1 for the tridiagonal matrix of two-sided Lanczos (host, FP64).
+//
+// Algorithm 4 ends with x = x_P + beta V_k f(H_k) e_1; Section 2 evaluates f on the small
+// projected matrix by an eigendecomposition or Roberts' Newton iteration, an O(k^3) term
+// (Proposition 2). Here the default route is O(k^2):
+//  1. Diagonal similarity S = D^-1 H_k D with d_1 = 1, d_{j+1} = d_j delta_j / gamma_j,
+//     gamma_j = sqrt(beta_j delta_j), makes S complex symmetric (S^T = S) with diagonal
+//     alpha and off-diagonal gamma. sign(H_k) e_1 = D sign(S) e_1.
+//  2. Implicit shifted QR on S with complex orthogonal plane rotations G (G^T G = I,
+//     c^2 + s^2 = 1) and Wilkinson shifts: S = Z Lambda Z^T, Z = G_1 ... G_N.
+//     Only the first row of Z is accumulated; the rotations are stored.
+//  3. sign(S) e_1 = Z (sign(Re Lambda) .* Z^T e_1), applying the stored rotations in
+//     reverse order (O(N) = O(k^2)).
+// Complex orthogonal rotations are not unitary; the result is therefore checked
+// (sign(S)^2 e_1 = e_1 and H_k y = sign(H_k) H_k e_1) and, if a check fails, recomputed
+// by scaled Newton on the dense k x k matrix (the paper's Roberts iteration, O(k^3)).
+#include <algorithm>
+#include <complex>
+#include <vector>
+
+#include "common.h"
+
+namespace ovl {
+
+using cz = std::complex<double>;
+
+namespace {
+
+struct Rot {
+  int p;
+  cz c, s;
+};
+
+// G w on indices (p, p+1):  (c w_p + s w_q, -s w_p + c w_q)
+inline void rot_apply(const Rot& r, cz* w) {
+  cz a = w[r.p], b = w[r.p + 1];
+  w[r.p] = r.c * a + r.s * b;
+  w[r.p + 1] = -r.s * a + r.c * b;
+}
+// G^T w:  (c w_p - s w_q, s w_p + c w_q)
+inline void rot_apply_t(const Rot& r, cz* w) {
+  cz a = w[r.p], b = w[r.p + 1];
+  w[r.p] = r.c * a - r.s * b;
+  w[r.p + 1] = r.s * a + r.c * b;
+}
+
+struct CsqlResult {
+  std::vector<cz> lam;
+  std::vector<Rot> rots;
+  bool ok = false;
+};
+
+CsqlResult cs_qr(std::vector<cz> d, std::vector<cz> e) {
+  CsqlResult res;
+  const int k = (int)d.size();
+  const double eps = 1e-15;
+  long long budget = 60LL * k + 100;
+  res.rots.reserve((size_t)k * 8);
+  auto negligible = [&](int i) { return std::abs(e[i]) <= eps * (std::abs(d[i]) + std::abs(d[i + 1])); };
+  int hi = k - 1;
+  while (hi > 0) {
+    if (negligible(hi - 1)) {
+      e[hi - 1] = 0;
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && !negligible(lo - 1)) --lo;
+    if (lo > 0) e[lo - 1] = 0;
+    if (--budget < 0) return res;
+    // Wilkinson shift: eigenvalue of the trailing 2x2 closer to d[hi]
+    cz a = d[hi - 1], b = d[hi], ee = e[hi - 1];
+    cz half = 0.5 * (a - b);
+    cz disc = std::sqrt(half * half + ee * ee);
+    cz m1 = 0.5 * (a + b) + disc, m2 = 0.5 * (a + b) - disc;
+    cz shift = std::abs(m1 - b) < std::abs(m2 - b) ? m1 : m2;
+    cz x = d[lo] - shift, z = e[lo];
+    for (int p = lo; p < hi; ++p) {
+      const int q = p + 1;
+      cz rho = std::sqrt(x * x + z * z);
+      double scale = std::sqrt(std::norm(x) + std::norm(z));
+      if (!(std::abs(rho) > 1e-8 * scale) || scale == 0.0) return res;  // (near) isotropic: give up
+      cz c = x / rho, s = -z / rho;
+      if (std::norm(c) + std::norm(s) > 1e8) return res;  // too far from unitary
+      if (p > lo) e[p - 1] = rho;
+      cz dp = d[p], dq = d[q], ep = e[p];
+      cz c2 = c * c, s2 = s * s, cs = c * s;
+      d[p] = dp * c2 - 2.0 * ep * cs + dq * s2;
+      d[q] = dp * s2 + 2.0 * ep * cs + dq * c2;
+      e[p] = cs * (dp - dq) + ep * (c2 - s2);
+      if (q < hi) {
+        z = -s * e[q];
+        e[q] = c * e[q];
+        x = e[p];
+      }
+      res.rots.push_back(Rot{p, c, s});
+    }
+  }
+  res.lam = d;
+  res.ok = true;
+  return res;
+}
+
+// Dense complex LU inverse with partial pivoting (in place). Returns false if singular.
+bool invert(std::vector<cz>& a, int n) {
+  std::vector<int> piv(n);
+  std::vector<cz> inv((size_t)n * n, cz(0));
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int pr = col;
+    double best = std::abs(a[(size_t)col * n + col]);
+    for (int r = col + 1; r < n; ++r)
+      if (std::abs(a[(size_t)r * n + col]) > best) best = std::abs(a[(size_t)r * n + col]), pr = r;
+    if (best == 0.0) return false;
+    if (pr != col) {
+      for (int c = 0; c < n; ++c) {
+        std::swap(a[(size_t)pr * n + c], a[(size_t)col * n + c]);
+        std::swap(inv[(size_t)pr * n + c], inv[(size_t)col * n + c]);
+      }
+    }
+    cz pinv = 1.0 / a[(size_t)col * n + col];
+    for (int c = 0; c < n; ++c) {
+      a[(size_t)col * n + c] *= pinv;
+      inv[(size_t)col * n + c] *= pinv;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      cz f = a[(size_t)r * n + col];
+      if (f == cz(0)) continue;
+      cz* ar = &a[(size_t)r * n];
+      cz* ac = &a[(size_t)col * n];
+      cz* ir = &inv[(size_t)r * n];
+      cz* ic = &inv[(size_t)col * n];
+      for (int c = 0; c < n; ++c) {
+        ar[c] -= f * ac[c];
+        ir[c] -= f * ic[c];
+      }
+    }
+  }
+  a.swap(inv);
+  return true;
+}
+
+}  // namespace
+
+// Dense Roberts-Newton with determinantal scaling on the tridiagonal H (O(k^3)).
+ovl_status small_sign_newton(int k, const cz* al, const cz* be, const cz* de, cz* y) {
+  std::vector<cz> x((size_t)k * k, cz(0));
+  for (int i = 0; i < k; ++i) {
+    x[(size_t)i * k + i] = al[i];
+    if (i + 1 < k) {
+      x[(size_t)i * k + i + 1] = be[i];
+      x[(size_t)(i + 1) * k + i] = de[i];
+    }
+  }
+  bool scaling = true;
+  for (int it = 0; it < 100; ++it) {
+    std::vector<cz> xi = x;
+    // log |det X| from an LU of a copy (partial pivoting)
+    double logdet = 0.0;
+    if (scaling) {
+      std::vector<cz> lu = x;
+      for (int col = 0; col < k; ++col) {
+        int pr = col;
+        double best = std::abs(lu[(size_t)col * k + col]);
+        for (int r = col + 1; r < k; ++r)
+          if (std::abs(lu[(size_t)r * k + col]) > best) best = std::abs(lu[(size_t)r * k + col]), pr = r;
+        if (best == 0.0) {
+          set_error("small_sign: singular projected matrix");
+          return OVL_EILLPOSED;
+        }
+        if (pr != col)
+          for (int c = 0; c < k; ++c) std::swap(lu[(size_t)pr * k + c], lu[(size_t)col * k + c]);
+        cz piv = lu[(size_t)col * k + col];
+        logdet += std::log(std::abs(piv));
+        for (int r = col + 1; r < k; ++r) {
+          cz f = lu[(size_t)r * k + col] / piv;
+          if (f == cz(0)) continue;
+          for (int c = col; c < k; ++c) lu[(size_t)r * k + c] -= f * lu[(size_t)col * k + c];
+        }
+      }
+    }
+    if (!invert(xi, k)) {
+      set_error("small_sign: singular Newton iterate");
+      return OVL_EILLPOSED;
+    }
+    double zeta = scaling ? std::exp(-logdet / k) : 1.0;
+    double num = 0, den = 0;
+    for (size_t i = 0; i < x.size(); ++i) {
+      cz nx = 0.5 * (zeta * x[i] + xi[i] / zeta);
+      num += std::norm(nx - x[i]);
+      den += std::norm(nx);
+      x[i] = nx;
+    }
+    double change = std::sqrt(num / den);
+    if (change < 1e-2) scaling = false;
+    if (change < 1e-14) break;
+  }
+  for (int i = 0; i < k; ++i) y[i] = x[(size_t)i * k];
+  return OVL_OK;
+}
+
+ovl_status small_sign_ql(int k, const cz* al, const cz* be, const cz* de, cz* y, double* check) {
+  // 1. symmetrising diagonal similarity
+  std::vector<cz> dg(k), gm(k > 1 ? k - 1 : 0), dscale(k);
+  dscale[0] = 1.0;
+  for (int i = 0; i < k; ++i) dg[i] = al[i];
+  for (int i = 0; i + 1 < k; ++i) {
+    cz g = std::sqrt(be[i] * de[i]);
+    if (g == cz(0)) {
+      set_error("small_sign: zero off-diagonal");
+      return OVL_EINVAL;
+    }
+    gm[i] = g;
+    dscale[i + 1] = dscale[i] * de[i] / g;
+  }
+  // 2. implicit QR with complex orthogonal rotations
+  CsqlResult r = cs_qr(dg, gm);
+  if (!r.ok) return OVL_ENOCONV;
+  double lmax = 0;
+  for (auto& l : r.lam) lmax = std::max(lmax, std::abs(l));
+  for (auto& l : r.lam)
+    if (std::abs(l.real()) <= 1e-14 * lmax) {
+      set_error("small_sign: Ritz value on the imaginary axis");
+      return OVL_EILLPOSED;
+    }
+  // first row of Z = Z^T e_1
+  std::vector<cz> u(k, cz(0));
+  u[0] = 1.0;
+  for (const Rot& g : r.rots) rot_apply_t(g, u.data());
+  auto apply_sign_s = [&](std::vector<cz>& w) {  // w <- Z sign(L) Z^T w
+    for (const Rot& g : r.rots) rot_apply_t(g, w.data());
+    for (int i = 0; i < k; ++i) w[i] *= (r.lam[i].real() >= 0 ? 1.0 : -1.0);
+    for (auto it = r.rots.rbegin(); it != r.rots.rend(); ++it) rot_apply(*it, w.data());
+  };
+  std::vector<cz> ys(k);
+  for (int i = 0; i < k; ++i) ys[i] = (r.lam[i].real() >= 0 ? 1.0 : -1.0) * u[i];
+  for (auto it = r.rots.rbegin(); it != r.rots.rend(); ++it) rot_apply(*it, ys.data());
+  // 3. checks: sign(S)^2 e1 = e1 and H y = sign(H) (H e1)
+  std::vector<cz> w2 = ys;
+  apply_sign_s(w2);
+  double err1 = std::abs(w2[0] - 1.0);
+  for (int i = 1; i < k; ++i) err1 = std::max(err1, std::abs(w2[i]));
+  for (int i = 0; i < k; ++i) y[i] = dscale[i] * ys[i];
+  std::vector<cz> he1(k, cz(0));  // D^-1 H e1 = (alpha_1, delta_1 / d_2, 0...)
+  he1[0] = al[0];
+  if (k > 1) he1[1] = de[0] / dscale[1];
+  apply_sign_s(he1);
+  double err2 = 0, nrm = 0;
+  for (int i = 0; i < k; ++i) {
+    cz hy = al[i] * y[i];
+    if (i > 0) hy += de[i - 1] * y[i - 1];
+    if (i + 1 < k) hy += be[i] * y[i + 1];
+    cz rhs = dscale[i] * he1[i];
+    err2 = std::max(err2, std::abs(hy - rhs));
+    nrm = std::max(nrm, std::abs(hy));
+  }
+  double err = std::max(err1, err2 / std::max(nrm, 1e-300));
+  if (check) *check = err;
+  if (!(err < 1e-9)) return OVL_ENOCONV;
+  return OVL_OK;
+}
+
+// method 0 auto (QL, Newton on failure), 1 QL only, 2 Newton only
+ovl_status small_sign(int k, const cz* al, const cz* be, const cz* de, cz* y, int method) {
+  if (k < 1) {
+    set_error("small_sign: k < 1");
+    return OVL_EINVAL;
+  }
+  if (k == 1) {
+    if (al[0].real() == 0.0) {
+      set_error("small_sign: eigenvalue on the imaginary axis");
+      return OVL_EILLPOSED;
+    }
+    y[0] = al[0].real() > 0 ? 1.0 : -1.0;
+    return OVL_OK;
+  }
+  if (method != 2) {
+    double chk = 0;
+    ovl_status s = small_sign_ql(k, al, be, de, y, &chk);
+    if (s == OVL_OK || method == 1 || s == OVL_EILLPOSED) return s;
+  }
+  return small_sign_newton(k, al, be, de, y);
+}
+
+}  // namespace ovl
+
+extern "C" ovl_status ovl_small_sign(int32_t k, const void* alpha, const void* beta, const void* delta, void* y,
+                                     int32_t method) {
+  ovl::clear_error();
+  if (k < 1 || !alpha || !y || (k > 1 && (!beta || !delta)) || method < 0 || method > 2) {
+    ovl::set_error("ovl_small_sign: invalid arguments");
+    return OVL_EINVAL;
+  }
+  return ovl::small_sign(k, (const ovl::cz*)alpha, (const ovl::cz*)beta, (const ovl::cz*)delta, (ovl::cz*)y, method);
+}

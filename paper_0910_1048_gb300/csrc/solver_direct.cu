@@ -1,0 +1,466 @@
+// Host driver of direct two-sided Lanczos-LR(m, k), Algorithm 4:
+//   x_P = R f(Lambda) L^H b;  r = b - R L^H b;  r~ = b - L R^H b;  v_1 = r/beta, w_1 ~ r~;
+//   k steps of two-sided Lanczos (Eqs. 2sided1/2);  x = x_P + beta V_k f(H_k) e_1.
+// The paper fixes k a priori; this driver also stops early: every `check_every` steps it
+// copies H_j to the host, evaluates y_j = sign(H_j) e_1 and stops when
+//   sum_i |y_j(i) - y_j'(i)| ||v_i|| <= tol ||y_j||   (j' = previous check).
+// All per-step scalars stay on the device (no host round trip inside a chunk), so a chunk
+// of steps is one CUDA graph, replayed; the next chunk is queued before the host checks
+// the previous one, overlapping sign(H_j) e_1 with device work.
+#include <chrono>
+#include <complex>
+
+#include "kernels.h"
+
+namespace ovl {
+
+ovl_status small_sign(int k, const std::complex<double>* al, const std::complex<double>* be,
+                      const std::complex<double>* de, std::complex<double>* y, int method);
+
+struct DirectWS {
+  int nrhs = 0, kmax = 0, f64 = -1, m = 0, vol = 0;
+  LzDev lz;
+  LzVecs vec;
+  void* dev_block = nullptr;  // one allocation for everything
+  size_t dev_bytes = 0;
+  double2* dots = nullptr;
+  double* lam_sign = nullptr;
+  double2* coef = nullptr;
+  int* kr = nullptr;          // [nrhs] Krylov dimension per rhs for the combine
+  double2* bdev = nullptr;    // staging for host b / x
+  double2* xdev = nullptr;
+  // pinned host mirrors of the device scalars, double-buffered: the copies behind one
+  // chunk's event never overwrite the snapshot the host is reading
+  struct Mirror {
+    double2* alpha = nullptr;
+    double2* beta = nullptr;
+    double* delta = nullptr;
+    double* vnorm = nullptr;
+    double* sv = nullptr;
+    double* beta0 = nullptr;
+    int* j = nullptr;
+    int* status = nullptr;
+  } h[2];
+  void* h_block = nullptr;
+  // graph of `gchunk` steps
+  cudaGraphExec_t graph = nullptr;
+  int gchunk = 0;
+  double g_mw = 0, g_mu = 0;
+  int g_lf = -1;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+};
+
+void free_direct_ws(DirectWS* w) {
+  if (!w) return;
+  if (w->graph) cudaGraphExecDestroy(w->graph);
+  if (w->dev_block) cudaFree(w->dev_block);
+  if (w->h_block) cudaFreeHost(w->h_block);
+  if (w->stream) cudaStreamDestroy(w->stream);
+  if (w->ev) cudaEventDestroy(w->ev);
+  delete w;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int m) {
+  DirectWS* w = lat->dws;
+  const int vol = lat->g.vol;
+  if (w && w->nrhs == nrhs && w->kmax == kmax && w->f64 == (int)f64 && w->m >= m && w->vol == vol) return OVL_OK;
+  free_direct_ws(w);
+  lat->dws = nullptr;
+  w = new DirectWS();
+  w->nrhs = nrhs;
+  w->kmax = kmax;
+  w->f64 = f64;
+  w->m = m;
+  w->vol = vol;
+  const size_t n = (size_t)12 * vol;
+  const size_t elt = f64 ? 16 : 8;
+  const int nblk = (vol + kPairSites - 1) / kPairSites;  // the most blocks of any reduction kernel
+  const int ks = kmax + 2;
+  // carve one device block
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  size_t o_vh = take((size_t)nrhs * (kmax + 1) * n * elt);
+  size_t o_wh = take((size_t)2 * nrhs * n * elt);
+  size_t o_av = take((size_t)nrhs * n * elt);
+  size_t o_aw = take((size_t)nrhs * n * elt);
+  size_t o_xp = take((size_t)nrhs * n * 16);
+  size_t o_j = take((size_t)nrhs * 4);
+  size_t o_st = take((size_t)nrhs * 4);
+  size_t o_sv = take((size_t)nrhs * ks * 8);
+  size_t o_sw = take((size_t)nrhs * ks * 16);
+  size_t o_al = take((size_t)nrhs * ks * 16);
+  size_t o_be = take((size_t)nrhs * ks * 16);
+  size_t o_de = take((size_t)nrhs * ks * 8);
+  size_t o_vn = take((size_t)nrhs * ks * 8);
+  size_t o_b0 = take((size_t)nrhs * 8);
+  size_t o_pa = take((size_t)nrhs * std::max(m, 1) * nblk * 4 * 8);
+  size_t o_cn = take((size_t)nrhs * 4);
+  size_t o_do = take((size_t)nrhs * 2 * std::max(m, 1) * 16);
+  size_t o_ls = take((size_t)std::max(m, 1) * 8);
+  size_t o_co = take((size_t)nrhs * kmax * 16);
+  size_t o_kr = take((size_t)nrhs * 4);
+  size_t o_bd = take((size_t)nrhs * n * 16);
+  size_t o_xd = take((size_t)nrhs * n * 16);
+  char* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, off);
+  if (e != cudaSuccess) {
+    delete w;
+    set_error("apply_sign: cannot allocate %zu bytes of device workspace: %s", off, cudaGetErrorString(e));
+    return OVL_ENOMEM;
+  }
+  w->dev_block = base;
+  w->dev_bytes = off;
+  w->vec.vh = base + o_vh;
+  w->vec.wh = base + o_wh;
+  w->vec.av = base + o_av;
+  w->vec.aw = base + o_aw;
+  w->vec.xp = (double2*)(base + o_xp);
+  LzDev& lz = w->lz;
+  lz.kmax = kmax;
+  lz.nrhs = nrhs;
+  lz.nblk = nblk;
+  lz.j = (int*)(base + o_j);
+  lz.status = (int*)(base + o_st);
+  lz.sv = (double*)(base + o_sv);
+  lz.sw = (double2*)(base + o_sw);
+  lz.alpha = (double2*)(base + o_al);
+  lz.beta = (double2*)(base + o_be);
+  lz.delta = (double*)(base + o_de);
+  lz.vnorm = (double*)(base + o_vn);
+  lz.beta0 = (double*)(base + o_b0);
+  lz.part = (double*)(base + o_pa);
+  lz.count = (unsigned*)(base + o_cn);
+  w->dots = (double2*)(base + o_do);
+  w->lam_sign = (double*)(base + o_ls);
+  w->coef = (double2*)(base + o_co);
+  w->kr = (int*)(base + o_kr);
+  w->bdev = (double2*)(base + o_bd);
+  w->xdev = (double2*)(base + o_xd);
+  if (cudaMemset(lz.count, 0, (size_t)nrhs * 4) != cudaSuccess) {
+    free_direct_ws(w);
+    set_error("apply_sign: cudaMemset failed");
+    return OVL_ECUDA;
+  }
+  // pinned mirrors: alpha, beta (16 B), delta, vnorm, sv (8 B), beta0, j, status
+  size_t hb = (size_t)nrhs * ks * (16 + 16 + 8 + 8 + 8) + nrhs * (8 + 4 + 4) + 64;
+  char* hp = nullptr;
+  if (cudaMallocHost(&hp, 2 * hb) != cudaSuccess) {
+    free_direct_ws(w);
+    set_error("apply_sign: cannot allocate pinned host memory");
+    return OVL_ENOMEM;
+  }
+  w->h_block = hp;
+  for (int q = 0; q < 2; ++q) {
+    DirectWS::Mirror& h = w->h[q];
+    h.alpha = (double2*)(hp + q * hb);
+    h.beta = h.alpha + (size_t)nrhs * ks;
+    h.delta = (double*)(h.beta + (size_t)nrhs * ks);
+    h.vnorm = h.delta + (size_t)nrhs * ks;
+    h.sv = h.vnorm + (size_t)nrhs * ks;
+    h.beta0 = h.sv + (size_t)nrhs * ks;
+    h.j = (int*)(h.beta0 + nrhs);
+    h.status = h.j + nrhs;
+  }
+  if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming) != cudaSuccess) {
+    free_direct_ws(w);
+    set_error("apply_sign: cannot create stream/event");
+    return OVL_ECUDA;
+  }
+  lat->dws = w;
+  return OVL_OK;
+}
+
+// queue copies of the scalar arrays to the pinned mirrors
+static cudaError_t queue_scalar_copies(DirectWS* w, int q, cudaStream_t st) {
+  const size_t ks = (size_t)w->kmax + 2, nr = (size_t)w->nrhs;
+  const LzDev& lz = w->lz;
+  DirectWS::Mirror& h = w->h[q];
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(h.alpha, lz.alpha, nr * ks * 16, cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaMemcpyAsync(h.beta, lz.beta, nr * ks * 16, cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaMemcpyAsync(h.delta, lz.delta, nr * ks * 8, cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaMemcpyAsync(h.vnorm, lz.vnorm, nr * ks * 8, cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaMemcpyAsync(h.sv, lz.sv, nr * ks * 8, cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaMemcpyAsync(h.beta0, lz.beta0, nr * 8, cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaMemcpyAsync(h.j, lz.j, nr * 4, cudaMemcpyDeviceToHost, st))) return e;
+  return cudaMemcpyAsync(h.status, lz.status, nr * 4, cudaMemcpyDeviceToHost, st);
+}
+
+struct RhsState {
+  int k = 0;                       // Krylov dimension of y
+  std::vector<std::complex<double>> y, yprev;
+  double est = 1e300;
+  int status = OVL_PENDING;        // OK / ENOCONV / EBREAKDOWN / EILLPOSED once final
+  bool done = false;
+};
+
+// Snapshot of rhs r from the pinned mirrors: H_k, y = sign(H_k) e_1, error estimate.
+static ovl_status evaluate_rhs(DirectWS* w, int q, int r, RhsState& rs, double* t_small) {
+  const size_t ks = (size_t)w->kmax + 2;
+  const DirectWS::Mirror& h = w->h[q];
+  int j = h.j[r];
+  int st = h.status[r];
+  int k = (st == 1) ? j : j - 1;  // after a breakdown alpha_j exists but no beta_j
+  if (st == 3) k = 0;              // empty Krylov part: x = x_P
+  if (k < 1) {
+    rs.k = 0;
+    rs.y.clear();
+    rs.est = 0;
+    return OVL_OK;
+  }
+  std::vector<std::complex<double>> al(k), be(k), de(k);
+  for (int i = 0; i < k; ++i) {
+    double2 a = h.alpha[r * ks + i + 1];
+    al[i] = {a.x, a.y};
+    if (i + 1 < k) {
+      double2 b = h.beta[r * ks + i + 1];
+      be[i] = {b.x, b.y};
+      de[i] = h.delta[r * ks + i + 1];
+    }
+  }
+  std::vector<std::complex<double>> y(k);
+  auto t0 = std::chrono::steady_clock::now();
+  ovl_status s = small_sign(k, al.data(), be.data(), de.data(), y.data(), 0);
+  *t_small += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (s != OVL_OK) return s;
+  double ny = 0, dif = 0;
+  for (int i = 0; i < k; ++i) {
+    ny += std::norm(y[i]);
+    std::complex<double> p = (i < (int)rs.y.size()) ? rs.y[i] : 0.0;
+    dif += std::abs(y[i] - p) * h.vnorm[r * ks + i + 1];
+  }
+  rs.est = rs.y.empty() ? 1e300 : dif / std::sqrt(ny);
+  rs.yprev.swap(rs.y);
+  rs.y.swap(y);
+  rs.k = k;
+  return OVL_OK;
+}
+
+ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, const double2* b, double2* x,
+                        ovl_sign_info* info, cudaStream_t user_stream) {
+  auto t_start = std::chrono::steady_clock::now();
+  const bool f64 = p->precision == OVL_PREC_F64;
+  const int lf = p->precision == OVL_PREC_F32_F16LINKS ? LINK_F16R12 : (f64 ? LINK_F64 : LINK_F32);
+  OVL_REQUIRE(p->k_max >= 1 && p->k_max <= 100000, "apply_sign: k_max must be in [1, 100000]");
+  OVL_REQUIRE(lat->u64, "apply_sign: links not set");
+  OVL_REQUIRE(f64 || (lf == LINK_F32 ? lat->u32 != nullptr : lat->u16 != nullptr),
+              "apply_sign: links not set in the format this precision needs (ovl_set_links formats)");
+  int m = 0;
+  if (p->use_deflation) {
+    OVL_REQUIRE(lat->defl.m > 0, "apply_sign: use_deflation but no deflation set");
+    OVL_REQUIRE(lat->defl.m_w == p->m_W && lat->defl.mu == p->mu,
+                "apply_sign: deflation set was computed for (m_W, mu) = (%g, %g)", lat->defl.m_w, lat->defl.mu);
+    m = lat->defl.m;
+  }
+  const int kmax = p->fixed_k > 0 ? p->fixed_k : p->k_max;
+  OVL_TRY(ensure_ws(lat, nrhs, kmax, f64, m));
+  DirectWS* w = lat->dws;
+  cudaStream_t st = w->stream;
+  const Geom& g = lat->g;
+  const size_t n = (size_t)12 * g.vol;
+  // order after the caller's stream
+  OVL_CHECK_CUDA(cudaEventRecord(w->ev, user_stream));
+  OVL_CHECK_CUDA(cudaStreamWaitEvent(st, w->ev, 0));
+  const double2* bd = b;
+  if (p->host_io) {
+    OVL_CHECK_CUDA(cudaMemcpyAsync(w->bdev, b, (size_t)nrhs * n * 16, cudaMemcpyHostToDevice, st));
+    bd = w->bdev;
+  }
+  // start: deflation split and first vectors
+  if (m > 0) {
+    std::vector<double> ls(m);
+    for (int i = 0; i < m; ++i) ls[i] = lat->defl.lam[2 * i] >= 0 ? 1.0 : -1.0;
+    OVL_CHECK_CUDA(cudaMemcpyAsync(w->lam_sign, ls.data(), m * 8, cudaMemcpyHostToDevice, st));
+  }
+  LzVecs vec = w->vec;
+  if (m == 0) vec.xp = nullptr;
+  OVL_CHECK_CUDA(launch_lanczos_start(g, f64, w->lz, vec, bd, m, lat->defl.R, lat->defl.L, w->lam_sign, w->dots, st));
+  const Links U = lat->links();
+  const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 20, kmax));
+  // graph of `chunk` steps (re-captured when the step's parameters change)
+  bool use_graph = p->use_graphs != 0;
+  if (use_graph && !(w->graph && w->gchunk == chunk && w->g_mw == p->m_W && w->g_mu == p->mu && w->g_lf == lf)) {
+    if (w->graph) cudaGraphExecDestroy(w->graph);
+    w->graph = nullptr;
+    cudaGraph_t gr;
+    OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < chunk; ++i) {
+      cudaError_t e = launch_lanczos_step(g, U, lf, f64, p->m_W, p->mu, w->lz, vec, st);
+      if (e != cudaSuccess) {
+        cudaStreamEndCapture(st, &gr);
+        set_error("apply_sign: capture failed: %s", cudaGetErrorString(e));
+        return OVL_ECUDA;
+      }
+    }
+    OVL_CHECK_CUDA(cudaStreamEndCapture(st, &gr));
+    cudaError_t e = cudaGraphInstantiate(&w->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    OVL_CHECK_CUDA(e);
+    w->gchunk = chunk;
+    w->g_mw = p->m_W;
+    w->g_mu = p->mu;
+    w->g_lf = lf;
+  }
+  auto run_steps = [&](int nsteps) -> cudaError_t {
+    if (use_graph && nsteps == chunk) return cudaGraphLaunch(w->graph, st);
+    for (int i = 0; i < nsteps; ++i) {
+      cudaError_t e = launch_lanczos_step(g, U, lf, f64, p->m_W, p->mu, w->lz, vec, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  std::vector<RhsState> rs(nrhs);
+  double t_small = 0;
+  int queued = 0;  // steps queued on the device
+  cudaEvent_t evc[2];
+  OVL_CHECK_CUDA(cudaEventCreateWithFlags(&evc[0], cudaEventDisableTiming));
+  OVL_CHECK_CUDA(cudaEventCreateWithFlags(&evc[1], cudaEventDisableTiming));
+  int evq[2] = {0, 0};  // steps covered by the snapshot in each mirror slot
+  int next_slot = 0;
+  std::vector<int> pending;  // slots whose copies are in flight, oldest first
+  const bool fixed = p->fixed_k > 0;
+  auto launch_chunk = [&]() -> cudaError_t {
+    int ns = std::min(chunk, kmax - queued);
+    cudaError_t e = run_steps(ns);
+    if (e) return e;
+    queued += ns;
+    int q = next_slot;
+    next_slot ^= 1;
+    if ((e = queue_scalar_copies(w, q, st))) return e;
+    evq[q] = queued;
+    if ((e = cudaEventRecord(evc[q], st))) return e;
+    pending.push_back(q);
+    return cudaSuccess;
+  };
+  ovl_status result = OVL_OK;
+  cudaError_t ce = cudaSuccess;
+  int qlast = 0;
+  if (fixed) {
+    while (queued < kmax && ce == cudaSuccess) {
+      int ns = std::min(chunk, kmax - queued);
+      ce = run_steps(ns);
+      queued += ns;
+    }
+    if (ce == cudaSuccess) ce = queue_scalar_copies(w, 0, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    for (int r = 0; r < nrhs && ce == cudaSuccess; ++r) {
+      ovl_status s = evaluate_rhs(w, 0, r, rs[r], &t_small);
+      rs[r].status = s != OVL_OK ? s : (w->h[0].status[r] == 1 && rs[r].k < kmax ? OVL_EBREAKDOWN : OVL_OK);
+      rs[r].est = 0;
+      rs[r].done = true;
+    }
+  } else {
+    ce = launch_chunk();
+    while (ce == cudaSuccess) {
+      // keep one more chunk queued while the host evaluates the oldest snapshot
+      if (queued < kmax && pending.size() < 2) {
+        ce = launch_chunk();
+        if (ce) break;
+      }
+      int q = pending.front();
+      pending.erase(pending.begin());
+      ce = cudaEventSynchronize(evc[q]);
+      if (ce) break;
+      qlast = q;
+      const bool final_snapshot = evq[q] >= kmax;
+      bool all_done = true;
+      for (int r = 0; r < nrhs; ++r) {
+        RhsState& s = rs[r];
+        if (s.done) continue;
+        ovl_status es = evaluate_rhs(w, q, r, s, &t_small);
+        if (es != OVL_OK) {
+          s.status = es;
+          s.done = true;
+        } else if (w->h[q].status[r] == 3) {
+          s.status = OVL_OK;
+          s.done = true;
+        } else if (w->h[q].status[r] == 1) {
+          s.status = OVL_EBREAKDOWN;
+          s.done = true;
+        } else if (s.est <= p->tol) {
+          s.status = OVL_OK;
+          s.done = true;
+        } else if (final_snapshot) {
+          s.status = OVL_ENOCONV;
+          s.done = true;
+        }
+        if (s.done && w->h[q].status[r] == 0) {
+          // retire this right-hand side: later steps skip it (any nonzero status)
+          ce = cudaMemsetAsync(w->lz.status + r, 2, sizeof(int), st);
+          if (ce) break;
+        }
+        all_done = all_done && s.done;
+      }
+      if (all_done || ce) break;
+    }
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  cudaEventDestroy(evc[0]);
+  cudaEventDestroy(evc[1]);
+  if (ce != cudaSuccess) {
+    set_error("apply_sign: CUDA error in the Lanczos loop: %s", cudaGetErrorString(ce));
+    return OVL_ECUDA;
+  }
+  const DirectWS::Mirror& hm = w->h[qlast];
+  // combine: x = x_P + beta V_k y with coef_j = beta0 y_j sv_j
+  std::vector<double2> coef((size_t)nrhs * kmax, make_double2(0, 0));
+  const size_t ks = (size_t)kmax + 2;
+  lat->last_alpha.assign(nrhs, {});
+  lat->last_beta.assign(nrhs, {});
+  lat->last_delta.assign(nrhs, {});
+  for (int r = 0; r < nrhs; ++r) {
+    RhsState& s = rs[r];
+    double b0 = hm.beta0[r];
+    for (int i = 0; i < s.k; ++i) {
+      std::complex<double> c = b0 * s.y[i] * hm.sv[r * ks + i + 1];
+      coef[(size_t)r * kmax + i] = make_double2(c.real(), c.imag());
+    }
+    for (int i = 0; i < s.k; ++i) {
+      double2 a = hm.alpha[r * ks + i + 1];
+      lat->last_alpha[r].push_back(a.x);
+      lat->last_alpha[r].push_back(a.y);
+      if (i + 1 < s.k) {
+        double2 bb = hm.beta[r * ks + i + 1];
+        lat->last_beta[r].push_back(bb.x);
+        lat->last_beta[r].push_back(bb.y);
+        lat->last_delta[r].push_back(hm.delta[r * ks + i + 1]);
+        lat->last_delta[r].push_back(0.0);
+      }
+    }
+    if (s.status != OVL_OK && result == OVL_OK) result = s.status;
+  }
+  // coefficients and per-rhs k travel in one pinned upload
+  std::vector<int> kr(nrhs);
+  for (int r = 0; r < nrhs; ++r) kr[r] = rs[r].k;
+  OVL_CHECK_CUDA(cudaMemcpyAsync(w->coef, coef.data(), coef.size() * 16, cudaMemcpyHostToDevice, st));
+  OVL_CHECK_CUDA(cudaMemcpyAsync(w->kr, kr.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+  double2* xd = p->host_io ? w->xdev : x;
+  OVL_CHECK_CUDA(launch_lanczos_combine(g, f64, w->lz, vec, w->kr, w->coef, kmax, xd, st));
+  if (p->host_io) OVL_CHECK_CUDA(cudaMemcpyAsync(x, w->xdev, (size_t)nrhs * n * 16, cudaMemcpyDeviceToHost, st));
+  OVL_CHECK_CUDA(cudaStreamSynchronize(st));
+  double t_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (info) {
+    for (int r = 0; r < nrhs; ++r) {
+      info[r].status = rs[r].status;
+      info[r].iterations = rs[r].k;
+      info[r].matvecs = 2 * rs[r].k;
+      info[r].poles = 0;
+      info[r].est_error = rs[r].est;
+      info[r].t_total_ms = t_total;
+      info[r].t_small_ms = t_small;
+      info[r].residual = 0;
+    }
+  }
+  if (result != OVL_OK) set_error("apply_sign: at least one right-hand side ended with status %d", result);
+  return result;
+}
+
+}  // namespace ovl

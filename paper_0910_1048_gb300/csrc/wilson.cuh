@@ -1,0 +1,217 @@
+// Site-level Wilson hop arithmetic shared by the stencil kernels.
+//
+// (D_W psi)(x) = psi(x) - kappa sum_nu [ e^{+mu d_nu,t} (1 - g_nu) U_nu(x) psi(x+nu)
+//                                      + e^{-mu d_nu,t} (1 + g_nu) U_nu(x-nu)^H psi(x-nu) ]
+// (the reading of the paper's H_W = gamma5 D_W, Section 1, with the notation of its
+// reference [Bloch:2006cd]); t hops that wrap the time boundary carry t_bc.
+//
+// Chiral basis: g_k = [[0, -i s_k], [i s_k, 0]], g_4 = [[0, 1], [1, 0]]. Writing
+// g_nu = [[0, M], [N, 0]] on (upper, lower) spin pairs, (1 -/+ g_nu) psi is determined by
+// the half spinor h = upper -/+ M lower: (1 - g) psi = (h, -N h), (1 + g) psi = (h, N h).
+// Only h (2 spins x 3 colours) is multiplied by the link.
+#pragma once
+
+#include "common.h"
+
+#if defined(__CUDACC__)
+#include <cuda_fp16.h>
+#endif
+
+namespace ovl {
+
+template <class R> struct Spin { cplx<R> c[4][3]; };
+template <class R> struct Half { cplx<R> c[2][3]; };
+template <class R> struct Mat3 { cplx<R> m[3][3]; };
+
+// Half spinor h of (1 - g_mu) p (FWD) or (1 + g_mu) p (!FWD).
+template <int MU, bool FWD, class R>
+OVL_HD void project(const Spin<R>& p, Half<R>& h) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (MU == 0) {  // M l = (-i p3, -i p2)
+      h.c[0][a] = FWD ? p.c[0][a] + times_i(p.c[3][a]) : p.c[0][a] + times_mi(p.c[3][a]);
+      h.c[1][a] = FWD ? p.c[1][a] + times_i(p.c[2][a]) : p.c[1][a] + times_mi(p.c[2][a]);
+    } else if (MU == 1) {  // M l = (-p3, p2)
+      h.c[0][a] = FWD ? p.c[0][a] + p.c[3][a] : p.c[0][a] - p.c[3][a];
+      h.c[1][a] = FWD ? p.c[1][a] - p.c[2][a] : p.c[1][a] + p.c[2][a];
+    } else if (MU == 2) {  // M l = (-i p2, i p3)
+      h.c[0][a] = FWD ? p.c[0][a] + times_i(p.c[2][a]) : p.c[0][a] + times_mi(p.c[2][a]);
+      h.c[1][a] = FWD ? p.c[1][a] + times_mi(p.c[3][a]) : p.c[1][a] + times_i(p.c[3][a]);
+    } else {  // M l = (p2, p3)
+      h.c[0][a] = FWD ? p.c[0][a] - p.c[2][a] : p.c[0][a] + p.c[2][a];
+      h.c[1][a] = FWD ? p.c[1][a] - p.c[3][a] : p.c[1][a] + p.c[3][a];
+    }
+  }
+}
+
+// acc += (h, -/+ N h): the full spinor of the projected hop.
+template <int MU, bool FWD, class R>
+OVL_HD void reconstruct_add(Spin<R>& acc, const Half<R>& h) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    acc.c[0][a] = acc.c[0][a] + h.c[0][a];
+    acc.c[1][a] = acc.c[1][a] + h.c[1][a];
+    if (MU == 0) {  // N h = (i h1, i h0)
+      acc.c[2][a] = acc.c[2][a] + (FWD ? times_mi(h.c[1][a]) : times_i(h.c[1][a]));
+      acc.c[3][a] = acc.c[3][a] + (FWD ? times_mi(h.c[0][a]) : times_i(h.c[0][a]));
+    } else if (MU == 1) {  // N h = (h1, -h0)
+      acc.c[2][a] = FWD ? acc.c[2][a] - h.c[1][a] : acc.c[2][a] + h.c[1][a];
+      acc.c[3][a] = FWD ? acc.c[3][a] + h.c[0][a] : acc.c[3][a] - h.c[0][a];
+    } else if (MU == 2) {  // N h = (i h0, -i h1)
+      acc.c[2][a] = acc.c[2][a] + (FWD ? times_mi(h.c[0][a]) : times_i(h.c[0][a]));
+      acc.c[3][a] = acc.c[3][a] + (FWD ? times_i(h.c[1][a]) : times_mi(h.c[1][a]));
+    } else {  // N h = (h0, h1)
+      acc.c[2][a] = FWD ? acc.c[2][a] - h.c[0][a] : acc.c[2][a] + h.c[0][a];
+      acc.c[3][a] = FWD ? acc.c[3][a] - h.c[1][a] : acc.c[3][a] + h.c[1][a];
+    }
+  }
+}
+
+// out = U h (DAG false) or U^H h (DAG true), colour multiply of both half-spinor rows.
+template <bool DAG, class R>
+OVL_HD void su3_mul(const Mat3<R>& u, const Half<R>& h, Half<R>& out) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cplx<R> acc = mk<R>(0, 0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) acc = acc + (DAG ? cdot(u.m[b][a], h.c[s][b]) : u.m[a][b] * h.c[s][b]);
+      out.c[s][a] = acc;
+    }
+  }
+}
+
+template <class R>
+OVL_HD void scale_half(Half<R>& h, R f) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) h.c[s][a] = f * h.c[s][a];
+}
+
+// ------------------------------------------------------------------ link loads
+template <int LF, class R>
+OVL_HD void load_link(const Links& U, int mu, int site, int vol, Mat3<R>& u) {
+  if (LF == LINK_F64) {
+    const double2* p = U.f64 + (size_t)mu * 9 * vol + site;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double2 v = p[(size_t)k * vol];
+      u.m[k / 3][k % 3] = mk<R>((R)v.x, (R)v.y);
+    }
+  } else if (LF == LINK_F32) {
+    const float2* p = U.f32 + (size_t)mu * 9 * vol + site;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      float2 v = p[(size_t)k * vol];
+      u.m[k / 3][k % 3] = mk<R>((R)v.x, (R)v.y);
+    }
+  } else {
+#if defined(__CUDA_ARCH__)
+    const uint32_t* p = U.f16 + (size_t)mu * 6 * vol + site;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      uint32_t bits = p[(size_t)k * vol];
+      __half2 hv = *reinterpret_cast<__half2*>(&bits);
+      float2 f = __half22float2(hv);
+      u.m[k / 3][k % 3] = mk<R>((R)f.x, (R)f.y);
+    }
+    // third row of an SU(3) matrix: conj(row0 x row1)
+    u.m[2][0] = conj(u.m[0][1] * u.m[1][2] - u.m[0][2] * u.m[1][1]);
+    u.m[2][1] = conj(u.m[0][2] * u.m[1][0] - u.m[0][0] * u.m[1][2]);
+    u.m[2][2] = conj(u.m[0][0] * u.m[1][1] - u.m[0][1] * u.m[1][0]);
+#endif
+  }
+}
+
+// ------------------------------------------------------------------ neighbours
+struct Nbr {
+  int f[4], b[4];  // forward / backward neighbour site per direction
+  int t;           // time coordinate (for the boundary sign)
+};
+
+OVL_HD void neighbours(const Geom& g, int s, Nbr& n) {
+  int x = s % g.lx;
+  int r = s / g.lx;
+  int y = r % g.ly;
+  r /= g.ly;
+  int z = r % g.lz;
+  int t = r / g.lz;
+  n.t = t;
+  n.f[0] = (x == g.lx - 1) ? s - (g.lx - 1) : s + 1;
+  n.b[0] = (x == 0) ? s + (g.lx - 1) : s - 1;
+  n.f[1] = (y == g.ly - 1) ? s - (g.ly - 1) * g.sy : s + g.sy;
+  n.b[1] = (y == 0) ? s + (g.ly - 1) * g.sy : s - g.sy;
+  n.f[2] = (z == g.lz - 1) ? s - (g.lz - 1) * g.sz : s + g.sz;
+  n.b[2] = (z == 0) ? s + (g.lz - 1) * g.sz : s - g.sz;
+  n.f[3] = (t == g.lt - 1) ? s - (g.lt - 1) * g.st : s + g.st;
+  n.b[3] = (t == 0) ? s + (g.lt - 1) * g.st : s - g.st;
+}
+
+// Hop coefficients: spatial -kappa; time forward -kappa e^{mu}, backward -kappa e^{-mu},
+// each times t_bc where the hop wraps the time boundary.
+template <class R>
+struct HopCoef {
+  R ks, ktf, ktb;
+};
+
+// acc += hop terms for one direction (forward and backward), input p loaded by `ld`.
+template <int MU, int LF, class R, class Load>
+OVL_HD void hop_dir(const Geom& g, const Links& U, int s, const Nbr& n, R kf, R kb, Load ld, Spin<R>& acc) {
+  Mat3<R> u;
+  Half<R> h, hu;
+  {
+    Spin<R> p;
+    ld(n.f[MU], p);
+    project<MU, true>(p, h);
+    load_link<LF>(U, MU, s, g.vol, u);
+    su3_mul<false>(u, h, hu);
+    scale_half(hu, kf);
+    reconstruct_add<MU, true>(acc, hu);
+  }
+  {
+    Spin<R> p;
+    ld(n.b[MU], p);
+    project<MU, false>(p, h);
+    load_link<LF>(U, MU, n.b[MU], g.vol, u);
+    su3_mul<true>(u, h, hu);
+    scale_half(hu, kb);
+    reconstruct_add<MU, false>(acc, hu);
+  }
+}
+
+// out = D_W psi at site s (psi loaded through `ld`), coefficients c.
+template <int LF, class R, class Load>
+OVL_HD void dslash_site(const Geom& g, const Links& U, int s, const HopCoef<R>& c, Load ld, Spin<R>& out) {
+  Nbr n;
+  neighbours(g, s, n);
+  ld(s, out);
+  hop_dir<0, LF>(g, U, s, n, c.ks, c.ks, ld, out);
+  hop_dir<1, LF>(g, U, s, n, c.ks, c.ks, ld, out);
+  hop_dir<2, LF>(g, U, s, n, c.ks, c.ks, ld, out);
+  R ktf = (n.t == g.lt - 1) ? (R)g.t_bc * c.ktf : c.ktf;
+  R ktb = (n.t == 0) ? (R)g.t_bc * c.ktb : c.ktb;
+  hop_dir<3, LF>(g, U, s, n, ktf, ktb, ld, out);
+}
+
+template <class R>
+OVL_HD void gamma5_inplace(Spin<R>& p) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    p.c[2][a] = -p.c[2][a];
+    p.c[3][a] = -p.c[3][a];
+  }
+}
+
+template <class R>
+OVL_HD HopCoef<R> hop_coef(double m_w, double mu) {
+  double kap = 1.0 / (2.0 * m_w + 8.0);
+  HopCoef<R> c;
+  c.ks = (R)(-kap);
+  c.ktf = (R)(-kap * std::exp(mu));
+  c.ktb = (R)(-kap * std::exp(-mu));
+  return c;
+}
+
+}  // namespace ovl

@@ -1,0 +1,244 @@
+"""GPU parity of x = sign(H_W(mu)) b by direct two-sided Lanczos-LR (Algorithm 4).
+
+- equal-k parity: the GPU's H_k (ovl_get_tridiag) and x_k against the oracle's Algorithm 4
+  at the same k (FP64: 1e-10; FP32 with FP64 scalars: 1e-4 on H_k, a stated bound);
+- against the definition x* = R sign(Lambda) R^-1 b: 4^4, mu = 0.3 at rel.err 1e-10 (plain
+  two-sided Lanczos, k <= 1200) and with 16 deflated eigenpairs; k = n exactness on 2^4;
+  free field at 8^4 against the closed form; the mu = 0 Hermitian case;
+- properties at sizes without a dense oracle (8^4): sign^2 b = b (the paper's accuracy
+  measure, Section 6), gauge covariance, <w, sign(H(mu)) v> = <sign(H(-mu)) w, v>;
+- edge cases: b in the deflated space (x = x_P exactly), k_max too small (ENOCONV with the
+  best iterate), host buffers, batches of right-hand sides equal to single solves.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import deflation, freefield, lanczos, matsign, wilson
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ovl():
+    import paper_0910_1048_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(ovl):
+    c = ovl.ovl_ctx_create(0)
+    yield c
+    ovl.ovl_ctx_destroy(c)
+
+
+def _lat(ovl, ctx, dims, links, formats=None):
+    lat = ovl.ovl_create_lattice(ctx, dims, -1)
+    ovl.ovl_set_links(lat, links, formats or (ovl.OVL_F64 | ovl.OVL_F32 | ovl.OVL_F16R12))
+    return lat
+
+
+def _solve(ovl, lat, b, **kw):
+    p = ovl.ovl_sign_params_default(**kw)
+    bt = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+    xt = torch.empty_like(bt)
+    st, info = ovl.ovl_apply_sign(lat, p, bt, xt)
+    return st, info, xt.cpu().numpy()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _oracle_ops(u, dims, mu):
+    a = deflation.sparse_hw(u, dims, -2.0, mu)
+    ah = deflation.sparse_hw(u, dims, -2.0, -mu)
+    return (lambda v: (a @ v.ravel()).reshape(v.shape)), (lambda w: (ah @ w.ravel()).reshape(w.shape))
+
+
+@pytest.mark.parametrize("dims,k", [((4, 4, 4, 4), 40), ((2, 4, 6, 4), 25), ((6, 6, 6, 6), 60)])
+def test_equal_k_parity_f64(ovl, ctx, dims, k):
+    u = synth.gauge_links(dims, 2)
+    b = synth.gaussian_source(dims, 3)
+    lat = _lat(ovl, ctx, dims, u)
+    st, info, x = _solve(ovl, lat, b, mu=0.3, fixed_k=k, check_every=7)
+    assert st == ovl.OVL_OK and info[0]["iterations"] == k
+    al, be, de = ovl.ovl_get_tridiag(lat, 0)
+    fa, fah = _oracle_ops(u, dims, 0.3)
+    xo, sto = lanczos.direct_lanczos_lr(fa, fah, b, k)
+    assert np.abs(al - sto["alpha"]).max() < 1e-10 * np.abs(sto["alpha"]).max()
+    assert np.abs(be - sto["beta"]).max() < 1e-10 * np.abs(sto["beta"]).max()
+    assert np.abs(de - sto["delta"]).max() < 1e-10 * np.abs(sto["delta"]).max()
+    assert _rel(x, xo) < 1e-10
+    ovl.ovl_destroy_lattice(lat)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_equal_k_parity_f32(ovl, ctx, prec):
+    dims = (4, 4, 4, 4)
+    u = synth.gauge_links(dims, 2)
+    b = synth.gaussian_source(dims, 3)
+    lat = _lat(ovl, ctx, dims, u)
+    pr = ovl.OVL_PREC_F32 if prec == "f32" else ovl.OVL_PREC_F32_F16LINKS
+    st, info, x = _solve(ovl, lat, b, mu=0.3, fixed_k=20, precision=pr)
+    al, be, de = ovl.ovl_get_tridiag(lat, 0)
+    fa, fah = _oracle_ops(u, dims, 0.3)
+    xo, sto = lanczos.direct_lanczos_lr(fa, fah, b, 20)
+    tol = 1e-4 if prec == "f32" else 2e-2
+    assert np.abs(al - sto["alpha"]).max() < tol * np.abs(sto["alpha"]).max()
+    assert _rel(x, xo) < tol
+    ovl.ovl_destroy_lattice(lat)
+
+
+@pytest.fixture(scope="module")
+def p4(problem_4444):
+    return problem_4444
+
+
+def test_c1_plain_lanczos_vs_dense(ovl, ctx, p4):
+    """4^4, mu = 0.3, FP64, no deflation: rel.err <= 1e-10 against the eigendecomposition."""
+    lat = _lat(ovl, ctx, p4["dims"], p4["links"], ovl.OVL_F64)
+    st, info, x = _solve(ovl, lat, p4["b"], mu=0.3, tol=1e-11, k_max=1200, check_every=25)
+    assert st == ovl.OVL_OK, info
+    assert _rel(x, p4["xstar"]) < 1e-10
+    ovl.ovl_destroy_lattice(lat)
+
+
+def test_lr_deflation_vs_dense(ovl, ctx, p4):
+    """Algorithm 4 with m = 16 critical eigenpairs (LR deflation, Section 3)."""
+    n = p4["b"].size
+    lat = _lat(ovl, ctx, p4["dims"], p4["links"], ovl.OVL_F64)
+    ovl.ovl_set_deflation(lat, -2.0, 0.3, p4["R16"].T.copy(), p4["L16"].T.copy(), p4["lam16"])
+    st, info, x = _solve(ovl, lat, p4["b"], mu=0.3, tol=1e-11, k_max=900, use_deflation=1)
+    assert st == ovl.OVL_OK, info
+    assert _rel(x, p4["xstar"]) < 1e-10
+    # deflation shortens the Krylov space needed (gap 0.063 -> 0.105)
+    st2, info2, _ = _solve(ovl, lat, p4["b"], mu=0.3, tol=1e-9, k_max=1200)
+    st3, info3, _ = _solve(ovl, lat, p4["b"], mu=0.3, tol=1e-9, k_max=1200, use_deflation=1)
+    assert info3[0]["iterations"] < info2[0]["iterations"]
+    # b = right eigenvector: Krylov part vanishes and x = x_P = sign(Re lambda) r exactly
+    r3 = p4["R16"][:, 3].reshape(p4["b"].shape)
+    st, info, x = _solve(ovl, lat, r3, mu=0.3, tol=1e-10, k_max=200, use_deflation=1)
+    assert np.abs(x - np.sign(p4["lam16"][3].real) * r3).max() < 1e-10
+    # mismatched (m_W, mu) is refused
+    p = ovl.ovl_sign_params_default(mu=0.2, use_deflation=1)
+    bt = torch.from_numpy(p4["b"]).cuda()
+    with pytest.raises(ovl.OvlError):
+        ovl.ovl_apply_sign(lat, p, bt, torch.empty_like(bt))
+    with pytest.raises(ovl.OvlError):  # not biorthonormal
+        ovl.ovl_set_deflation(lat, -2.0, 0.3, p4["R16"].T.copy(), 2 * p4["L16"].T.copy(), p4["lam16"])
+    ovl.ovl_destroy_lattice(lat)
+    del n
+
+
+def test_exact_at_k_equal_n(ovl, ctx):
+    dims = (2, 2, 2, 2)
+    u = synth.gauge_links(dims, 35, 0.2)
+    b = synth.gaussian_source(dims, 36)
+    xs = matsign.sign_eig(wilson.dense_hw(u, dims, -2.0, 0.3), b.ravel()).reshape(b.shape)
+    lat = _lat(ovl, ctx, dims, u, ovl.OVL_F64)
+    st, info, x = _solve(ovl, lat, b, mu=0.3, fixed_k=b.size)
+    assert st == ovl.OVL_OK
+    assert _rel(x, xs) < 1e-11
+    ovl.ovl_destroy_lattice(lat)
+
+
+def test_mu0_hermitian(ovl, ctx):
+    dims = (4, 4, 2, 4)
+    u = synth.gauge_links(dims, 37)
+    b = synth.gaussian_source(dims, 38)
+    xs = matsign.sign_hermitian(wilson.dense_hw(u, dims, -2.0, 0.0), b.ravel()).reshape(b.shape)
+    lat = _lat(ovl, ctx, dims, u, ovl.OVL_F64)
+    st, info, x = _solve(ovl, lat, b, mu=0.0, tol=1e-11, k_max=b.size)
+    assert _rel(x, xs) < 1e-9, info
+    ovl.ovl_destroy_lattice(lat)
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.3])
+def test_free_field_closed_form_8888(ovl, ctx, mu):
+    dims = (8, 8, 8, 8)
+    u = synth.unit_links(dims)
+    b = synth.gaussian_source(dims, 39)
+    xs = freefield.sign_hw_free(b, dims, -2.0, mu)
+    lat = _lat(ovl, ctx, dims, u, ovl.OVL_F64)
+    st, info, x = _solve(ovl, lat, b, mu=mu, tol=1e-11, k_max=600)
+    assert st == ovl.OVL_OK, info
+    assert _rel(x, xs) < 1e-10
+    ovl.ovl_destroy_lattice(lat)
+
+
+@pytest.fixture(scope="module")
+def lat8(ovl, ctx):
+    dims = (8, 8, 8, 8)
+    u = synth.gauge_links(dims, 0)
+    lat = _lat(ovl, ctx, dims, u)
+    yield dims, u, lat
+    ovl.ovl_destroy_lattice(lat)
+
+
+def test_sign_squared_8888(ovl, lat8):
+    """The paper's accuracy measure: 0.5 ||sign(A)^2 b - b|| / ||b|| (Section 6)."""
+    dims, u, lat = lat8
+    b = synth.gaussian_source(dims, 1000)
+    st, info, x = _solve(ovl, lat, b, mu=0.3, tol=1e-8, k_max=1500, check_every=25)
+    st2, info2, x2 = _solve(ovl, lat, x, mu=0.3, tol=1e-8, k_max=1500, check_every=25)
+    acc = 0.5 * np.linalg.norm(x2 - b) / np.linalg.norm(b)
+    assert acc < 1e-7, (acc, info, info2)
+
+
+def test_adjoint_relation_8888(ovl, lat8):
+    """sign(H(mu))^H = sign(H(-mu)): <w, sign(H(mu)) v> = <sign(H(-mu)) w, v>."""
+    dims, u, lat = lat8
+    v = synth.gaussian_source(dims, 41)
+    w = synth.gaussian_source(dims, 42)
+    _, _, sv = _solve(ovl, lat, v, mu=0.3, tol=1e-10, k_max=1500, check_every=25)
+    _, _, sw = _solve(ovl, lat, w, mu=-0.3, tol=1e-10, k_max=1500, check_every=25)
+    lhs = np.vdot(w, sv)
+    rhs = np.vdot(sw, v)
+    assert abs(lhs - rhs) < 1e-8 * np.linalg.norm(v) * np.linalg.norm(w)
+
+
+def test_gauge_covariance_sign(ovl, ctx):
+    dims = (4, 4, 4, 4)
+    u = synth.gauge_links(dims, 43)
+    g = synth.random_su3_field(dims, 44)
+    b = synth.gaussian_source(dims, 45)
+    lat1 = _lat(ovl, ctx, dims, u, ovl.OVL_F64)
+    lat2 = _lat(ovl, ctx, dims, wilson.gauge_transform(u, g), ovl.OVL_F64)
+    _, _, x1 = _solve(ovl, lat1, b, mu=0.3, tol=1e-11, k_max=1500)
+    _, _, x2 = _solve(ovl, lat2, wilson.gauge_transform_spinor(b, g), mu=0.3, tol=1e-11, k_max=1500)
+    assert _rel(x2, wilson.gauge_transform_spinor(x1, g)) < 1e-9
+    ovl.ovl_destroy_lattice(lat1)
+    ovl.ovl_destroy_lattice(lat2)
+
+
+def test_enoconv_returns_best_iterate(ovl, ctx):
+    dims = (4, 4, 4, 4)
+    u = synth.gauge_links(dims, 0)
+    b = synth.gaussian_source(dims, 1000)
+    lat = _lat(ovl, ctx, dims, u, ovl.OVL_F64)
+    st, info, x = _solve(ovl, lat, b, mu=0.3, tol=1e-14, k_max=40, check_every=10)
+    assert st == ovl.OVL_ENOCONV and info[0]["status"] == ovl.OVL_ENOCONV
+    assert info[0]["iterations"] == 40 and np.all(np.isfinite(x))
+    fa, fah = _oracle_ops(u, dims, 0.3)
+    xo, _ = lanczos.direct_lanczos_lr(fa, fah, b, 40)
+    assert _rel(x, xo) < 1e-10
+    ovl.ovl_destroy_lattice(lat)
+
+
+def test_host_io_and_batch(ovl, ctx):
+    dims = (4, 4, 4, 4)
+    u = synth.gauge_links(dims, 0)
+    b3 = synth.gaussian_source(dims, 50, nrhs=3)
+    lat = _lat(ovl, ctx, dims, u, ovl.OVL_F64)
+    p = ovl.ovl_sign_params_default(mu=0.3, tol=1e-9, k_max=1200)
+    xh = np.zeros_like(b3)
+    st, info = ovl.ovl_apply_sign(lat, p, b3, xh)
+    assert st == ovl.OVL_OK
+    for r in range(3):
+        st1, info1, x1 = _solve(ovl, lat, b3[r], mu=0.3, tol=1e-9, k_max=1200)
+        assert info1[0]["iterations"] == info[r]["iterations"]
+        assert np.array_equal(x1, xh[r])  # per-rhs arithmetic is independent of the batch
+    ovl.ovl_destroy_lattice(lat)
