@@ -49,6 +49,10 @@ struct LzVecs {
   double2* xp = nullptr;    // [nrhs][12][V] FP64 deflated part x_P (nullptr without deflation)
 };
 
+// c_i = l_i^H b, d_i = r_i^H b (dots[rhs][0..m) = c, [m..2m) = d); part >= nrhs*m*ceil(V/128)*4.
+cudaError_t launch_defl_dots(const Geom& g, int nrhs, int m, const double2* b, const double2* R, const double2* L,
+                             double* part, unsigned* count, double2* dots, cudaStream_t st);
+
 // Start: from b (canonical complex128, device) build vhat_1 = r, what_1 = r~ and the scales.
 // With m > 0 deflation vectors R, L (native FP64 [m][12][V]) and lam (host, 2m doubles):
 // x_P = R sign(Lambda) L^H b, r = b - R L^H b, r~ = b - L R^H b (Algorithm 4, first lines).
@@ -62,5 +66,45 @@ cudaError_t launch_lanczos_step(const Geom& g, const Links& U, int lf, bool f64,
 // kr [nrhs] (device) the Krylov dimension of each rhs.
 cudaError_t launch_lanczos_combine(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, const int* kr,
                                    const double2* coef, int kcoef, double2* x, cudaStream_t st);
+
+}  // namespace ovl
+
+namespace ovl {
+
+// ---- multishift BiCG on M = A^2 (Algorithm 3 with Section 5's g(t) = t sum w_i/(t^2 - s_i))
+// Seed system (M - sigma_1) x = r, sigma_1 the shift closest to 0; shifted systems
+// (M - sigma_i) x = r share its Krylov space with residuals zeta^i_k r_k (collinear).
+// Status: 0 running, 1 breakdown, 2 converged, 3 empty (r = 0), 4 final update pending.
+constexpr int kMaxShifts = 128;
+struct MsDev {
+  int nrhs = 0, s = 0, nblk = 0;
+  int* k = nullptr;           // [nrhs] iterations done
+  int* status = nullptr;      // [nrhs]
+  double2* seed = nullptr;    // [nrhs][8]: rho, alpha_k, alpha_{k-1}, beta_{k-1}, (|r0|,|r|), beta_k
+  double2* zeta = nullptr;    // [nrhs][s][3]: zeta_{k-1}, zeta_k, zeta_{k+1}
+  double2* ash = nullptr;     // [nrhs][s] alpha^i_k
+  double2* bsh = nullptr;     // [nrhs][s] beta^i_k
+  int* active = nullptr;      // [nrhs][s] 1 running, 2 last update pending, 0 done
+  const double* omega = nullptr;  // [s]
+  const double* dsig = nullptr;   // [s] sigma_i - sigma_1
+  double sigma1 = 0, tol = 0;
+  double* part = nullptr;     // [nrhs][nblk][4]
+  unsigned* count = nullptr;  // [nrhs]
+};
+
+struct MsVecs {
+  void *r = nullptr, *rt = nullptr, *p = nullptr, *pt = nullptr;  // [nrhs][12][V]
+  void *t = nullptr, *tt = nullptr, *q = nullptr, *qt = nullptr;  // [nrhs][12][V]
+  void* ps = nullptr;          // [nrhs][s][12][V] shifted directions
+  double2* X = nullptr;        // [nrhs][12][V] FP64 sum_i omega_i x^(i)
+  double2* xp = nullptr;       // [nrhs][12][V] FP64 x_P (nullptr without deflation)
+};
+
+cudaError_t launch_ms_start(const Geom& g, bool f64, const MsDev& ms, const MsVecs& v, const double2* b, int m,
+                            const double2* R, const double2* L, const double* lam_sign, double2* dots, cudaStream_t st);
+cudaError_t launch_ms_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, const MsDev& ms,
+                           const MsVecs& v, cudaStream_t st);
+// x (canonical complex128) = x_P + AX (AX native FP64, = H_W(mu) X)
+cudaError_t launch_ms_finish(const Geom& g, int nrhs, const double2* ax, const double2* xp, double2* x, cudaStream_t st);
 
 }  // namespace ovl

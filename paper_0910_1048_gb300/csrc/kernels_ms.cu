@@ -1,0 +1,360 @@
+// Multishift BiCG kernels (Algorithm 3 on M = A^2, A = H_W(mu); Section 5's rational sign).
+//
+// One iteration k is four launches:
+//   pair1:  t = A p,  t~ = A^H p~                                   (A^H = H_W(-mu))
+//   pair2:  q = A t - s1 p = (M - s1) p,  q~ = A^H t~ - s1 p~;  alpha_k = rho / (p~^H q);
+//           last block: zeta^i_{k+1}, alpha^i_k for every live shift
+//   update: r -= alpha_k q,  r~ -= conj(alpha_k) q~;  rho' = r~^H r, |r|;
+//           last block: beta_k = rho'/rho, beta^i_k = beta_k (zeta^i_{k+1}/zeta^i_k)^2,
+//           shifts with |zeta^i_{k+1}| |r| <= tol |r_0| are retired after this step
+//   dirs:   X += sum_i omega_i alpha^i_k p^i;  p^i = zeta^i_{k+1} r + beta^i_k p^i;
+//           p = r + beta_k p,  p~ = r~ + conj(beta_k) p~
+// The shifted recurrences follow from the BiCG residual polynomials: r_k = R_k(M0) r_0 with
+// R_{k+1}(t) = (1 + a_k b_{k-1}/a_{k-1} - a_k t) R_k(t) - (a_k b_{k-1}/a_{k-1}) R_{k-1}(t), and the
+// residual of (M0 - d) x = r_0 in the same Krylov space is R_k(d)^-1 r_k, i.e. zeta = 1/R_k(d).
+#include "devutil.cuh"
+#include "kernels.h"
+
+namespace ovl {
+
+template <class R>
+__device__ __forceinline__ size_t voff(int rhs, size_t n) { return (size_t)rhs * n; }
+
+// start: r = b - R L^H b, r~ = b - L R^H b, x_P; p = r, p~ = r~, p^i = r, X = 0
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_ms_start(Geom g, MsDev ms, MsVecs v, const double2* b, int m,
+                                                     const double2* Rv, const double2* Lv, const double* lam_sign,
+                                                     const double2* dots) {
+  using T = typename V2<R>::T;
+  const int rhs = blockIdx.y;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t n = (size_t)12 * g.vol;
+  double acc[4] = {0, 0, 0, 0};
+  if (s < g.vol) {
+    const double2* dr = dots + (size_t)rhs * 2 * m;
+    for (int c = 0; c < 12; ++c) {
+      zd bv = ldc<double>(b, (size_t)rhs * n + (size_t)s * 12 + c);
+      zd r = bv, rt = bv, x = mk(0.0, 0.0);
+      for (int i = 0; i < m; ++i) {
+        zd ci = ldc<double>(dr, i), di = ldc<double>(dr, m + i);
+        zd ri = ldc<double>(Rv, (size_t)i * n + (size_t)c * g.vol + s);
+        zd li = ldc<double>(Lv, (size_t)i * n + (size_t)c * g.vol + s);
+        r = r - ci * ri;
+        x = x + lam_sign[i] * (ci * ri);
+        rt = rt - di * li;
+      }
+      const size_t e = voff<R>(rhs, n) + (size_t)c * g.vol + s;
+      if (v.xp) stc<double>(v.xp, e, x);
+      stc<double>(v.X, e, mk(0.0, 0.0));
+      cplx<R> rr = mk<R>((R)r.re, (R)r.im), rtt = mk<R>((R)rt.re, (R)rt.im);
+      stc<R>((T*)v.r, e, rr);
+      stc<R>((T*)v.p, e, rr);
+      stc<R>((T*)v.rt, e, rtt);
+      stc<R>((T*)v.pt, e, rtt);
+      for (int i = 0; i < ms.s; ++i) stc<R>((T*)v.ps, ((size_t)rhs * ms.s + i) * n + (size_t)c * g.vol + s, rr);
+      // rho and |r| from the stored (rounded) vectors, so the recurrences start consistent
+      zd rd = mk((double)rr.re, (double)rr.im), rtd = mk((double)rtt.re, (double)rtt.im);
+      zd ip = cdot(rtd, rd);
+      acc[0] += ip.re;
+      acc[1] += ip.im;
+      acc[2] += norm2(rd);
+    }
+  }
+  block_sum<4>(acc);
+  double* part = ms.part + (size_t)rhs * ms.nblk * 4;
+  if (publish_partials<4>(acc, part, ms.count + rhs)) {
+    reduce_partials<4>(part, gridDim.x, acc);
+    const int t = lin_tid();
+    double2* sd = ms.seed + (size_t)rhs * 8;
+    if (t == 0) {
+      double rn = sqrt(acc[2]);
+      sd[0] = make_double2(acc[0], acc[1]);  // rho
+      sd[1] = make_double2(0, 0);
+      sd[2] = make_double2(1, 0);  // alpha_{-1}
+      sd[3] = make_double2(0, 0);  // beta_{-1}
+      sd[4] = make_double2(rn, rn);
+      sd[5] = make_double2(0, 0);
+      ms.k[rhs] = 0;
+      ms.status[rhs] = acc[2] == 0.0 ? 3 : ((acc[0] != 0.0 || acc[1] != 0.0) ? 0 : 1);
+    }
+    for (int i = t; i < ms.s; i += lin_nthreads()) {
+      double2* z = ms.zeta + ((size_t)rhs * ms.s + i) * 3;
+      z[0] = z[1] = z[2] = make_double2(1, 0);
+      ms.active[(size_t)rhs * ms.s + i] = 1;
+      ms.ash[(size_t)rhs * ms.s + i] = make_double2(0, 0);
+      ms.bsh[(size_t)rhs * ms.s + i] = make_double2(0, 0);
+    }
+  }
+}
+
+// pair1 (MODE 0): t = A p, t~ = A^H p~.  pair2 (MODE 1): q = A t - s1 p, q~ = A^H t~ - s1 p~, p~^H q.
+template <class R, int LF, int MODE>
+__global__ void __launch_bounds__(2 * kPairSites) k_ms_pair(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm, MsDev ms,
+                                                            MsVecs v) {
+  using T = typename V2<R>::T;
+  const int rhs = blockIdx.y;
+  if (MODE == 0 && blockIdx.x == 0 && lin_tid() == 0 && ms.status[rhs] == 4) ms.status[rhs] = 2;
+  if (ms.status[rhs] != 0) return;
+  const size_t n = (size_t)12 * g.vol;
+  const int s = blockIdx.x * kPairSites + threadIdx.x;
+  const bool is_t = threadIdx.y == 1;
+  const T* in = (const T*)(MODE == 0 ? (is_t ? v.pt : v.p) : (is_t ? v.tt : v.t)) + voff<R>(rhs, n);
+  T* out = (T*)(MODE == 0 ? (is_t ? v.tt : v.t) : (is_t ? v.qt : v.q)) + voff<R>(rhs, n);
+  double acc[2] = {0, 0};
+  if (s < g.vol) {
+    Spin<R> o;
+    dslash_site<LF, R>(g, U, s, is_t ? cm : cp, Loader<R, true>{in, g.vol, false}, o);
+    const R s1 = (R)ms.sigma1;
+    const T* pp = (const T*)(is_t ? v.pt : v.p) + voff<R>(rhs, n);
+    const T* ptl = (const T*)v.pt + voff<R>(rhs, n);
+    cplx<R> a = mk<R>(0, 0);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      cplx<R> x = o.c[c / 3][c % 3];
+      if (c >= 6) x = -x;  // gamma5
+      if (MODE == 1) {
+        x = x - s1 * ldc<R>(pp, (size_t)c * g.vol + s);
+        if (!is_t) a = a + cdot(ldc<R>(ptl, (size_t)c * g.vol + s), x);
+      }
+      stc<R>(out, (size_t)c * g.vol + s, x);
+    }
+    acc[0] = (double)a.re;
+    acc[1] = (double)a.im;
+  }
+  if (MODE == 0) return;
+  block_sum<2>(acc);
+  double* part = ms.part + (size_t)rhs * ms.nblk * 4;
+  double pv[4] = {acc[0], acc[1], 0, 0};
+  if (publish_partials<4>(pv, part, ms.count + rhs)) {
+    reduce_partials<4>(part, gridDim.x, pv);
+    __shared__ zd alpha_sh;
+    __shared__ int bad;
+    const int t = lin_tid();
+    double2* sd = ms.seed + (size_t)rhs * 8;
+    if (t == 0) {
+      zd den = mk(pv[0], pv[1]);
+      zd rho = ldc<double>(sd, 0);
+      double dd = norm2(den);
+      bad = !(dd > 0.0) || !(dd < 1e300);
+      zd alpha = bad ? mk(0.0, 0.0) : (1.0 / dd) * (rho * conj(den));
+      alpha_sh = alpha;
+      if (bad) ms.status[rhs] = 1;
+      sd[1] = make_double2(alpha.re, alpha.im);
+    }
+    __syncthreads();
+    if (bad) return;
+    const zd ak = alpha_sh, akm = ldc<double>(sd, 2), bkm = ldc<double>(sd, 3);
+    for (int i = t; i < ms.s; i += lin_nthreads()) {
+      const size_t si = (size_t)rhs * ms.s + i;
+      int act = ms.active[si];
+      if (act == 2) ms.active[si] = act = 0;  // its final update happened last step
+      if (!act) continue;
+      double2* z = ms.zeta + si * 3;
+      zd zm = ldc<double>(z, 0), z0 = ldc<double>(z, 1);
+      // zeta_{k+1} = z0 zm a_{k-1} / (a_{k-1} zm (1 - a_k d) + a_k b_{k-1} (zm - z0))
+      zd d1 = mk(1.0 - ak.re * ms.dsig[i], -ak.im * ms.dsig[i]);
+      zd den = akm * zm * d1 + ak * bkm * (zm - z0);
+      zd num = z0 * zm * akm;
+      double dn = norm2(den);
+      zd zp = dn > 0 ? (1.0 / dn) * (num * conj(den)) : mk(0.0, 0.0);
+      z[2] = make_double2(zp.re, zp.im);
+      double z0n = norm2(z0);
+      zd ratio = z0n > 0 ? (1.0 / z0n) * (zp * conj(z0)) : mk(0.0, 0.0);
+      zd ai = ak * ratio;
+      ms.ash[si] = make_double2(ai.re, ai.im);
+    }
+  }
+}
+
+// update: r -= alpha q, r~ -= conj(alpha) q~; rho' = r~^H r, |r|^2
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_ms_update(Geom g, MsDev ms, MsVecs v) {
+  using T = typename V2<R>::T;
+  const int rhs = blockIdx.y;
+  if (ms.status[rhs] != 0) return;
+  const size_t n = (size_t)12 * g.vol;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  double2* sd = ms.seed + (size_t)rhs * 8;
+  const zd ak = ldc<double>(sd, 1);
+  const cplx<R> a = mk<R>((R)ak.re, (R)ak.im), ac = mk<R>((R)ak.re, (R)-ak.im);
+  double acc[4] = {0, 0, 0, 0};
+  if (s < g.vol) {
+    T* r = (T*)v.r + voff<R>(rhs, n);
+    T* rt = (T*)v.rt + voff<R>(rhs, n);
+    const T* q = (const T*)v.q + voff<R>(rhs, n);
+    const T* qt = (const T*)v.qt + voff<R>(rhs, n);
+    R ipr = 0, ipi = 0, nr = 0;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      size_t e = (size_t)c * g.vol + s;
+      cplx<R> x = ldc<R>(r, e) - a * ldc<R>(q, e);
+      cplx<R> y = ldc<R>(rt, e) - ac * ldc<R>(qt, e);
+      stc<R>(r, e, x);
+      stc<R>(rt, e, y);
+      cplx<R> ip = cdot(y, x);
+      ipr += ip.re;
+      ipi += ip.im;
+      nr += norm2(x);
+    }
+    acc[0] = ipr;
+    acc[1] = ipi;
+    acc[2] = nr;
+  }
+  block_sum<4>(acc);
+  double* part = ms.part + (size_t)rhs * ms.nblk * 4;
+  if (publish_partials<4>(acc, part, ms.count + rhs)) {
+    reduce_partials<4>(part, gridDim.x, acc);
+    __shared__ zd beta_sh;
+    __shared__ double rn_sh;
+    __shared__ int live;
+    const int t = lin_tid();
+    if (t == 0) {
+      zd rho = ldc<double>(sd, 0), rhon = mk(acc[0], acc[1]);
+      double rr = norm2(rho);
+      zd beta = rr > 0 ? (1.0 / rr) * (rhon * conj(rho)) : mk(0.0, 0.0);
+      double rn = sqrt(acc[2]);
+      beta_sh = beta;
+      rn_sh = rn;
+      live = 0;
+      sd[0] = make_double2(rhon.re, rhon.im);
+      sd[2] = sd[1];  // alpha_{k-1} <- alpha_k
+      sd[3] = make_double2(beta.re, beta.im);
+      sd[5] = make_double2(beta.re, beta.im);
+      sd[4].y = rn;
+      ms.k[rhs] += 1;
+      // breakdown of the BiCG recurrence (rho' = 0 while r is not small) or non-finite values
+      if (!(rn < 1e300) || !(norm2(rhon) < 1e300) || (norm2(rhon) == 0.0 && rn > ms.tol * sd[4].x))
+        ms.status[rhs] = 1;
+    }
+    __syncthreads();
+    const zd beta = beta_sh;
+    const double rn = rn_sh, r0 = sd[4].x;
+    int mylive = 0;
+    for (int i = t; i < ms.s; i += lin_nthreads()) {
+      const size_t si = (size_t)rhs * ms.s + i;
+      if (!ms.active[si]) continue;
+      double2* z = ms.zeta + si * 3;
+      zd z0 = ldc<double>(z, 1), zp = ldc<double>(z, 2);
+      double z0n = norm2(z0);
+      zd ratio = z0n > 0 ? (1.0 / z0n) * (zp * conj(z0)) : mk(0.0, 0.0);
+      zd bi = beta * (ratio * ratio);
+      ms.bsh[si] = make_double2(bi.re, bi.im);
+      z[0] = z[1];
+      z[1] = z[2];
+      if (sqrt(norm2(zp)) * rn <= ms.tol * r0)
+        ms.active[si] = 2;  // this step's direction update is its last
+      else
+        mylive = 1;
+    }
+    if (mylive) atomicOr(&live, 1);
+    __syncthreads();
+    if (t == 0 && !live && ms.status[rhs] == 0) ms.status[rhs] = 4;
+  }
+}
+
+// dirs: X += sum_i omega_i alpha^i p^i (FP64); p^i = zeta^i r + beta^i p^i; p, p~ updates
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs v) {
+  using T = typename V2<R>::T;
+  const int rhs = blockIdx.y;
+  const int st = ms.status[rhs];
+  if (st != 0 && st != 4) return;
+  const size_t n = (size_t)12 * g.vol;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double2 coefx[kMaxShifts], coefz[kMaxShifts], coefb[kMaxShifts];
+  __shared__ int act[kMaxShifts];
+  for (int i = threadIdx.x; i < ms.s; i += blockDim.x) {
+    const size_t si = (size_t)rhs * ms.s + i;
+    act[i] = ms.active[si];
+    zd ai = ldc<double>(ms.ash, si);
+    coefx[i] = make_double2(ms.omega[i] * ai.re, ms.omega[i] * ai.im);
+    coefz[i] = ms.zeta[si * 3 + 1];  // zeta_{k+1} after the rotation in update
+    coefb[i] = ms.bsh[si];
+  }
+  __syncthreads();
+  if (s >= g.vol) return;
+  const zd bk = ldc<double>(ms.seed + (size_t)rhs * 8, 5);
+  const cplx<R> b = mk<R>((R)bk.re, (R)bk.im), bc = mk<R>((R)bk.re, (R)-bk.im);
+  const T* r = (const T*)v.r + voff<R>(rhs, n);
+  const T* rt = (const T*)v.rt + voff<R>(rhs, n);
+  T* p = (T*)v.p + voff<R>(rhs, n);
+  T* pt = (T*)v.pt + voff<R>(rhs, n);
+  T* ps = (T*)v.ps + (size_t)rhs * ms.s * n;
+  double2* X = v.X + voff<R>(rhs, n);
+  for (int c = 0; c < 12; ++c) {
+    const size_t e = (size_t)c * g.vol + s;
+    const cplx<R> rv = ldc<R>(r, e);
+    zd xa = ldc<double>(X, e);
+    for (int i = 0; i < ms.s; ++i) {
+      if (!act[i]) continue;
+      T* pi = ps + (size_t)i * n;
+      cplx<R> pv = ldc<R>(pi, e);
+      double2 cx = coefx[i];
+      xa = xa + mk(cx.x, cx.y) * mk((double)pv.re, (double)pv.im);
+      if (act[i] == 1) {
+        double2 cz = coefz[i], cb = coefb[i];
+        cplx<R> nv = mk<R>((R)cz.x, (R)cz.y) * rv + mk<R>((R)cb.x, (R)cb.y) * pv;
+        stc<R>(pi, e, nv);
+      }
+    }
+    stc<double>(X, e, xa);
+    if (st == 0) {
+      stc<R>(p, e, rv + b * ldc<R>(p, e));
+      stc<R>(pt, e, ldc<R>(rt, e) + bc * ldc<R>(pt, e));
+    }
+  }
+}
+
+cudaError_t launch_ms_start(const Geom& g, bool f64, const MsDev& ms, const MsVecs& v, const double2* b, int m,
+                            const double2* R, const double2* L, const double* lam_sign, double2* dots, cudaStream_t st) {
+  dim3 grid((g.vol + kBlock - 1) / kBlock, ms.nrhs);
+  if (m > 0) {
+    cudaError_t e = launch_defl_dots(g, ms.nrhs, m, b, R, L, ms.part, ms.count, dots, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (f64)
+    k_ms_start<double><<<grid, kBlock, 0, st>>>(g, ms, v, b, m, R, L, lam_sign, dots);
+  else
+    k_ms_start<float><<<grid, kBlock, 0, st>>>(g, ms, v, b, m, R, L, lam_sign, dots);
+  return cudaGetLastError();
+}
+
+template <class R, int LF>
+static cudaError_t ms_step_t(const Geom& g, const Links& U, double m_w, double mu, const MsDev& ms, const MsVecs& v,
+                             cudaStream_t st) {
+  dim3 grid((g.vol + kBlock - 1) / kBlock, ms.nrhs);
+  dim3 pgrid((g.vol + kPairSites - 1) / kPairSites, ms.nrhs), pblock(kPairSites, 2);
+  HopCoef<R> cp = hop_coef<R>(m_w, mu), cm = hop_coef<R>(m_w, -mu);
+  k_ms_pair<R, LF, 0><<<pgrid, pblock, 0, st>>>(g, U, cp, cm, ms, v);
+  k_ms_pair<R, LF, 1><<<pgrid, pblock, 0, st>>>(g, U, cp, cm, ms, v);
+  k_ms_update<R><<<grid, kBlock, 0, st>>>(g, ms, v);
+  k_ms_dirs<R><<<grid, kBlock, 0, st>>>(g, ms, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ms_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, const MsDev& ms,
+                           const MsVecs& v, cudaStream_t st) {
+  if (f64) return ms_step_t<double, LINK_F64>(g, U, m_w, mu, ms, v, st);
+  if (lf == LINK_F16R12) return ms_step_t<float, LINK_F16R12>(g, U, m_w, mu, ms, v, st);
+  return ms_step_t<float, LINK_F32>(g, U, m_w, mu, ms, v, st);
+}
+
+__global__ void k_ms_finish(int vol, const double2* ax, const double2* xp, double2* x) {
+  const size_t n = (size_t)12 * vol;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int rhs = blockIdx.y;
+  if (e >= n) return;
+  zd a = ldc<double>(ax, (size_t)rhs * n + e);
+  if (xp) a = a + ldc<double>(xp, (size_t)rhs * n + e);
+  int c = (int)(e / vol), s = (int)(e % vol);
+  x[(size_t)rhs * n + (size_t)s * 12 + c] = make_double2(a.re, a.im);
+}
+
+cudaError_t launch_ms_finish(const Geom& g, int nrhs, const double2* ax, const double2* xp, double2* x, cudaStream_t st) {
+  size_t n = (size_t)12 * g.vol;
+  dim3 grid((unsigned)((n + 255) / 256), nrhs);
+  k_ms_finish<<<grid, 256, 0, st>>>(g.vol, ax, xp, x);
+  return cudaGetLastError();
+}
+
+}  // namespace ovl

@@ -1,15 +1,341 @@
-// Multishift BiCG on A^2 with a rational sign approximation (Algorithm 3 + Section 5).
+// Host driver of BiCG-LR(m) with a rational sign approximation (Algorithm 3, Section 5):
+//   x_P = R f(Lambda) L^H b;  r = (I - P) b;  shadow r~ = b - L R^H b;
+//   multishift BiCG for (A^2 - sigma_i) x^(i) = r, i = 1..s (all systems share one Krylov
+//   space of M = A^2; footnote of Section 6: FOM/BiCG on Eq. pfe_s works with A^2);
+//   x = x_P + A sum_i omega_i x^(i)   (g(A) r with g(t) = t sum_i omega_i / (t^2 - sigma_i)).
+// Stopping rule (Section 6): every shifted residual below tol relative to |r|; shifts are
+// retired individually. Coefficients: Neuberger (Eq. pfe_s; s and c from Eq. no_of_poles with
+// the circle through spec_lo, spec_hi), Zolotarev on [spec_lo, spec_hi], or caller-given.
+#include <algorithm>
+#include <chrono>
+
 #include "kernels.h"
 
 namespace ovl {
 
-struct MultiWS {};
-void free_multi_ws(MultiWS* w) { delete w; }
+void neuberger(int s, double c, double* omega, double* sigma);
+void neuberger_for_spectrum(double lo, double hi, double eps, int* s_out, double* c_out, double* d_out);
+double neuberger_bound(int s, double d);
+double zolotarev(int n, double lo, double hi, double* omega, double* sigma);
 
-ovl_status solve_multishift(ovl_lattice*, const ovl_sign_params*, int, const double2*, double2*, ovl_sign_info*,
-                            cudaStream_t) {
-  set_error("apply_sign: multishift method not available in this build");
+struct MultiWS {
+  int nrhs = 0, s = 0, f64 = -1, vol = 0, m = 0;
+  MsDev ms;
+  MsVecs v;
+  char* dev = nullptr;
+  double2* dots = nullptr;
+  double* lam_sign = nullptr;
+  double* omega = nullptr;
+  double* dsig = nullptr;
+  double2* ax = nullptr;
+  double2* bdev = nullptr;
+  double2* xdev = nullptr;
+  int* h_status = nullptr;  // pinned [2][nrhs] status + [2][nrhs] k
+  cudaGraphExec_t graph = nullptr;
+  int gchunk = 0, g_lf = -1;
+  double g_mw = 0, g_mu = 0, g_s1 = 0, g_tol = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+void free_multi_ws(MultiWS* w) {
+  if (!w) return;
+  if (w->graph) cudaGraphExecDestroy(w->graph);
+  if (w->dev) cudaFree(w->dev);
+  if (w->h_status) cudaFreeHost(w->h_status);
+  if (w->stream) cudaStreamDestroy(w->stream);
+  for (auto e : w->ev)
+    if (e) cudaEventDestroy(e);
+  delete w;
+}
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m) {
+  MultiWS* w = lat->mws;
+  const int vol = lat->g.vol;
+  if (w && w->nrhs == nrhs && w->s == s && w->f64 == (int)f64 && w->vol == vol && w->m >= m) return OVL_OK;
+  free_multi_ws(w);
+  lat->mws = nullptr;
+  w = new MultiWS();
+  w->nrhs = nrhs;
+  w->s = s;
+  w->f64 = f64;
+  w->vol = vol;
+  w->m = m;
+  const size_t n = (size_t)12 * vol, elt = f64 ? 16 : 8;
+  const int nblk = (vol + kPairSites - 1) / kPairSites;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off += al256(b);
+    return o;
+  };
+  size_t o_vec[8];
+  for (int i = 0; i < 8; ++i) o_vec[i] = take((size_t)nrhs * n * elt);
+  size_t o_ps = take((size_t)nrhs * s * n * elt);
+  size_t o_X = take((size_t)nrhs * n * 16);
+  size_t o_xp = take((size_t)nrhs * n * 16);
+  size_t o_ax = take((size_t)nrhs * n * 16);
+  size_t o_bd = take((size_t)nrhs * n * 16);
+  size_t o_xd = take((size_t)nrhs * n * 16);
+  size_t o_k = take((size_t)nrhs * 4);
+  size_t o_st = take((size_t)nrhs * 4);
+  size_t o_seed = take((size_t)nrhs * 8 * 16);
+  size_t o_z = take((size_t)nrhs * s * 3 * 16);
+  size_t o_a = take((size_t)nrhs * s * 16);
+  size_t o_b = take((size_t)nrhs * s * 16);
+  size_t o_act = take((size_t)nrhs * s * 4);
+  size_t o_om = take((size_t)s * 8);
+  size_t o_ds = take((size_t)s * 8);
+  size_t o_pa = take((size_t)nrhs * std::max(m, 1) * nblk * 4 * 8);
+  size_t o_cn = take((size_t)nrhs * 4);
+  size_t o_do = take((size_t)nrhs * 2 * std::max(m, 1) * 16);
+  size_t o_ls = take((size_t)std::max(m, 1) * 8);
+  cudaError_t e = cudaMalloc(&w->dev, off);
+  if (e != cudaSuccess) {
+    delete w;
+    set_error("apply_sign: cannot allocate %zu bytes of device workspace: %s", off, cudaGetErrorString(e));
+    return OVL_ENOMEM;
+  }
+  char* b = w->dev;
+  void** vp[8] = {&w->v.r, &w->v.rt, &w->v.p, &w->v.pt, &w->v.t, &w->v.tt, &w->v.q, &w->v.qt};
+  for (int i = 0; i < 8; ++i) *vp[i] = b + o_vec[i];
+  w->v.ps = b + o_ps;
+  w->v.X = (double2*)(b + o_X);
+  w->v.xp = (double2*)(b + o_xp);
+  w->ax = (double2*)(b + o_ax);
+  w->bdev = (double2*)(b + o_bd);
+  w->xdev = (double2*)(b + o_xd);
+  MsDev& ms = w->ms;
+  ms.nrhs = nrhs;
+  ms.s = s;
+  ms.nblk = nblk;
+  ms.k = (int*)(b + o_k);
+  ms.status = (int*)(b + o_st);
+  ms.seed = (double2*)(b + o_seed);
+  ms.zeta = (double2*)(b + o_z);
+  ms.ash = (double2*)(b + o_a);
+  ms.bsh = (double2*)(b + o_b);
+  ms.active = (int*)(b + o_act);
+  w->omega = (double*)(b + o_om);
+  w->dsig = (double*)(b + o_ds);
+  ms.omega = w->omega;
+  ms.dsig = w->dsig;
+  ms.part = (double*)(b + o_pa);
+  ms.count = (unsigned*)(b + o_cn);
+  w->dots = (double2*)(b + o_do);
+  w->lam_sign = (double*)(b + o_ls);
+  if (cudaMemset(ms.count, 0, (size_t)nrhs * 4) != cudaSuccess ||
+      cudaMallocHost(&w->h_status, (size_t)4 * nrhs * sizeof(int)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w->ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    free_multi_ws(w);
+    set_error("apply_sign: cannot set up the multishift workspace");
+    return OVL_ECUDA;
+  }
+  lat->mws = w;
+  return OVL_OK;
+}
+
+// Rational coefficients for the call; returns the approximation's own error bound.
+static ovl_status coefficients(const ovl_sign_params* p, std::vector<double>& om, std::vector<double>& sg, double* bound) {
+  if (p->rational_kind == OVL_RAT_CUSTOM) {
+    OVL_REQUIRE(p->s >= 1 && p->s <= kMaxShifts && p->omega && p->sigma, "apply_sign: custom rational needs s, omega, sigma");
+    om.assign(p->omega, p->omega + p->s);
+    sg.assign(p->sigma, p->sigma + p->s);
+    for (double x : sg) OVL_REQUIRE(x <= 0, "apply_sign: shifts must satisfy sigma_i <= 0");
+    *bound = 0;
+    return OVL_OK;
+  }
+  OVL_REQUIRE(p->spec_lo > 0 && p->spec_hi > p->spec_lo,
+              "apply_sign: the rational variant needs spectrum bounds 0 < spec_lo < spec_hi");
+  if (p->rational_kind == OVL_RAT_NEUBERGER) {
+    int s;
+    double c, d;
+    neuberger_for_spectrum(p->spec_lo, p->spec_hi, std::max(p->tol, 1e-15), &s, &c, &d);
+    if (p->s > 0) s = p->s;
+    OVL_REQUIRE(s <= kMaxShifts, "apply_sign: %d poles needed (max %d)", s, kMaxShifts);
+    om.resize(s);
+    sg.resize(s);
+    neuberger(s, c, om.data(), sg.data());
+    *bound = neuberger_bound(s, d);
+    return OVL_OK;
+  }
+  if (p->rational_kind == OVL_RAT_ZOLOTAREV) {
+    OVL_REQUIRE(p->s >= 1 && p->s <= kMaxShifts, "apply_sign: Zolotarev needs 1 <= s <= %d", kMaxShifts);
+    om.resize(p->s);
+    sg.resize(p->s);
+    *bound = zolotarev(p->s, p->spec_lo, p->spec_hi, om.data(), sg.data());
+    return OVL_OK;
+  }
+  set_error("apply_sign: unknown rational_kind %d", p->rational_kind);
   return OVL_EINVAL;
+}
+
+ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, const double2* b, double2* x,
+                            ovl_sign_info* info, cudaStream_t user_stream) {
+  auto t0 = std::chrono::steady_clock::now();
+  const bool f64 = p->precision == OVL_PREC_F64;
+  const int lf = p->precision == OVL_PREC_F32_F16LINKS ? LINK_F16R12 : (f64 ? LINK_F64 : LINK_F32);
+  OVL_REQUIRE(lat->u64, "apply_sign: links not set");
+  OVL_REQUIRE(f64 || (lf == LINK_F32 ? lat->u32 != nullptr : lat->u16 != nullptr),
+              "apply_sign: links not set in the format this precision needs (ovl_set_links formats)");
+  OVL_REQUIRE(p->k_max >= 1 && p->k_max <= 1000000, "apply_sign: k_max must be in [1, 1e6]");
+  std::vector<double> om, sg;
+  double bound = 0;
+  OVL_TRY(coefficients(p, om, sg, &bound));
+  const int s = (int)om.size();
+  int m = 0;
+  if (p->use_deflation) {
+    OVL_REQUIRE(lat->defl.m > 0, "apply_sign: use_deflation but no deflation set");
+    OVL_REQUIRE(lat->defl.m_w == p->m_W && lat->defl.mu == p->mu,
+                "apply_sign: deflation set was computed for (m_W, mu) = (%g, %g)", lat->defl.m_w, lat->defl.mu);
+    m = lat->defl.m;
+  }
+  OVL_TRY(ensure_mws(lat, nrhs, s, f64, m));
+  MultiWS* w = lat->mws;
+  cudaStream_t st = w->stream;
+  const Geom& g = lat->g;
+  const size_t n = (size_t)12 * g.vol;
+  // seed shift: the one closest to 0 (the hardest system); others relative to it
+  double s1 = *std::max_element(sg.begin(), sg.end());
+  std::vector<double> ds(s);
+  for (int i = 0; i < s; ++i) ds[i] = sg[i] - s1;
+  MsDev ms = w->ms;
+  ms.sigma1 = s1;
+  ms.tol = p->tol;
+  OVL_CHECK_CUDA(cudaEventRecord(w->ev[0], user_stream));
+  OVL_CHECK_CUDA(cudaStreamWaitEvent(st, w->ev[0], 0));
+  OVL_CHECK_CUDA(cudaMemcpyAsync(w->omega, om.data(), s * 8, cudaMemcpyHostToDevice, st));
+  OVL_CHECK_CUDA(cudaMemcpyAsync(w->dsig, ds.data(), s * 8, cudaMemcpyHostToDevice, st));
+  const double2* bd = b;
+  if (p->host_io) {
+    OVL_CHECK_CUDA(cudaMemcpyAsync(w->bdev, b, (size_t)nrhs * n * 16, cudaMemcpyHostToDevice, st));
+    bd = w->bdev;
+  }
+  std::vector<double> ls(std::max(m, 1));
+  for (int i = 0; i < m; ++i) ls[i] = lat->defl.lam[2 * i] >= 0 ? 1.0 : -1.0;
+  if (m > 0) OVL_CHECK_CUDA(cudaMemcpyAsync(w->lam_sign, ls.data(), m * 8, cudaMemcpyHostToDevice, st));
+  MsVecs v = w->v;
+  if (m == 0) v.xp = nullptr;
+  OVL_CHECK_CUDA(launch_ms_start(g, f64, ms, v, bd, m, lat->defl.R, lat->defl.L, w->lam_sign, w->dots, st));
+  const Links U = lat->links();
+  const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 20, p->k_max));
+  const bool use_graph = p->use_graphs != 0;
+  if (use_graph && !(w->graph && w->gchunk == chunk && w->g_lf == lf && w->g_mw == p->m_W && w->g_mu == p->mu &&
+                     w->g_s1 == s1 && w->g_tol == p->tol)) {
+    if (w->graph) cudaGraphExecDestroy(w->graph);
+    w->graph = nullptr;
+    cudaGraph_t gr;
+    OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st);
+    cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+    OVL_CHECK_CUDA(e);
+    OVL_CHECK_CUDA(e2);
+    e = cudaGraphInstantiate(&w->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    OVL_CHECK_CUDA(e);
+    w->gchunk = chunk;
+    w->g_lf = lf;
+    w->g_mw = p->m_W;
+    w->g_mu = p->mu;
+    w->g_s1 = s1;
+    w->g_tol = p->tol;
+  }
+  auto run_chunk = [&](int ns) -> cudaError_t {
+    if (use_graph && ns == chunk) return cudaGraphLaunch(w->graph, st);
+    for (int i = 0; i < ns; ++i) {
+      cudaError_t e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  // chunks with status snapshots; one chunk stays queued while the host looks at the last
+  int queued = 0, slot = 0;
+  std::vector<int> pend;
+  cudaError_t ce = cudaSuccess;
+  auto launch = [&]() -> cudaError_t {
+    int ns = std::min(chunk, p->k_max - queued);
+    cudaError_t e = run_chunk(ns);
+    if (e) return e;
+    queued += ns;
+    int* hs = w->h_status + (size_t)slot * 2 * nrhs;
+    if ((e = cudaMemcpyAsync(hs, ms.status, nrhs * 4, cudaMemcpyDeviceToHost, st))) return e;
+    if ((e = cudaMemcpyAsync(hs + nrhs, ms.k, nrhs * 4, cudaMemcpyDeviceToHost, st))) return e;
+    if ((e = cudaEventRecord(w->ev[slot], st))) return e;
+    pend.push_back(slot);
+    slot ^= 1;
+    return cudaSuccess;
+  };
+  ce = launch();
+  bool done = false;
+  while (ce == cudaSuccess && !done) {
+    if (queued < p->k_max && pend.size() < 2) {
+      ce = launch();
+      if (ce) break;
+    }
+    int q = pend.front();
+    pend.erase(pend.begin());
+    ce = cudaEventSynchronize(w->ev[q]);
+    if (ce) break;
+    const int* hs = w->h_status + (size_t)q * 2 * nrhs;
+    done = true;
+    for (int r = 0; r < nrhs; ++r)
+      if (hs[r] == 0) done = false;
+    if (pend.empty() && queued >= p->k_max) done = true;
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) {
+    set_error("apply_sign: CUDA error in the multishift loop: %s", cudaGetErrorString(ce));
+    return OVL_ECUDA;
+  }
+  // final state, per-shift residual estimates
+  std::vector<int> hst(nrhs), hk(nrhs), act((size_t)nrhs * s);
+  std::vector<double2> seed((size_t)nrhs * 8), zeta((size_t)nrhs * s * 3);
+  OVL_CHECK_CUDA(cudaMemcpy(hst.data(), ms.status, nrhs * 4, cudaMemcpyDeviceToHost));
+  OVL_CHECK_CUDA(cudaMemcpy(hk.data(), ms.k, nrhs * 4, cudaMemcpyDeviceToHost));
+  OVL_CHECK_CUDA(cudaMemcpy(act.data(), ms.active, act.size() * 4, cudaMemcpyDeviceToHost));
+  OVL_CHECK_CUDA(cudaMemcpy(seed.data(), ms.seed, seed.size() * 16, cudaMemcpyDeviceToHost));
+  OVL_CHECK_CUDA(cudaMemcpy(zeta.data(), ms.zeta, zeta.size() * 16, cudaMemcpyDeviceToHost));
+  // x = x_P + A X (FP64 stencil, native layout)
+  OVL_CHECK_CUDA(launch_dslash(g, U, LINK_F64, true, p->m_W, p->mu, false, true, true, true, nrhs, v.X, w->ax, st));
+  double2* xd = p->host_io ? w->xdev : x;
+  OVL_CHECK_CUDA(launch_ms_finish(g, nrhs, w->ax, v.xp, xd, st));
+  if (p->host_io) OVL_CHECK_CUDA(cudaMemcpyAsync(x, w->xdev, (size_t)nrhs * n * 16, cudaMemcpyDeviceToHost, st));
+  OVL_CHECK_CUDA(cudaStreamSynchronize(st));
+  double t_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  ovl_status result = OVL_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    int stt = hst[r];
+    double r0 = seed[(size_t)r * 8 + 4].x, rn = seed[(size_t)r * 8 + 4].y;
+    double worst = 0;
+    for (int i = 0; i < s; ++i) {
+      double2 z = zeta[((size_t)r * s + i) * 3 + 1];
+      if (r0 > 0) worst = std::max(worst, std::sqrt(z.x * z.x + z.y * z.y) * rn / r0);
+    }
+    ovl_status rs = (stt == 2 || stt == 3 || stt == 4) ? OVL_OK : (stt == 1 ? OVL_EBREAKDOWN : OVL_ENOCONV);
+    if (stt == 0) {
+      bool all = true;
+      for (int i = 0; i < s; ++i) all = all && act[(size_t)r * s + i] != 1;
+      if (all) rs = OVL_OK;
+    }
+    if (rs != OVL_OK && result == OVL_OK) result = rs;
+    if (info) {
+      info[r].status = rs;
+      info[r].iterations = hk[r];
+      info[r].matvecs = 4 * hk[r] + 1;
+      info[r].poles = s;
+      info[r].est_error = (stt == 3 ? 0.0 : worst) + bound;
+      info[r].t_total_ms = t_total;
+      info[r].t_small_ms = 0;
+      info[r].residual = worst;
+    }
+  }
+  if (result != OVL_OK) set_error("apply_sign: at least one right-hand side ended with status %d", result);
+  return result;
 }
 
 }  // namespace ovl
