@@ -157,7 +157,12 @@ typedef struct {
   double est_error;       /* the solver's own error estimate (relative) */
   double t_total_ms;      /* wall time of the call (shared by all rhs of the call) */
   double t_small_ms;      /* host time in sign(H_k) e_1 */
-  double residual;        /* multishift: max relative true residual over shifts (FP64) */
+  double residual;        /* multishift: max recursive shifted residual |zeta_i r| / |r_0| */
+  double t_kernel_ms;     /* mean device time of the sampled launches of the dominant kernel (the
+                             pair stencil), timed with events on the stream that launched it */
+  double t_update_ms;     /* the same for the vector-update kernel of a step */
+  int32_t kernel_samples; /* launches behind t_kernel_ms (and t_update_ms) */
+  int32_t kernel_launches;/* all library kernel launches of the call (shared by its rhs) */
 } ovl_sign_info;
 
 /* Fill p with defaults: DIRECT_2SL, F64, m_W = -2, mu = 0, tol = 1e-10, k_max = 600,

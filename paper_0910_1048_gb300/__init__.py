@@ -53,7 +53,8 @@ class ovl_sign_info(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("matvecs", ctypes.c_int32),
         ("poles", ctypes.c_int32), ("est_error", ctypes.c_double), ("t_total_ms", ctypes.c_double),
-        ("t_small_ms", ctypes.c_double), ("residual", ctypes.c_double),
+        ("t_small_ms", ctypes.c_double), ("residual", ctypes.c_double), ("t_kernel_ms", ctypes.c_double),
+        ("t_update_ms", ctypes.c_double), ("kernel_samples", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
     ]
 
     def as_dict(self):

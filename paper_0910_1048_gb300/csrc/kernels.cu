@@ -397,29 +397,40 @@ __global__ void __launch_bounds__(kBlock) k_lz_update(Geom g, LzDev lz, typename
   }
 }
 
-cudaError_t launch_lanczos_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, const LzDev& lz,
-                                const LzVecs& vec, cudaStream_t st) {
-  dim3 grid((g.vol + kBlock - 1) / kBlock, lz.nrhs);
+cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
+                                const LzDev& lz, const LzVecs& vec, cudaStream_t st) {
   dim3 pgrid((g.vol + kPairSites - 1) / kPairSites, lz.nrhs), pblock(kPairSites, 2);
-  if (f64) {
+  if (f64)
     k_lz_pair<double, LINK_F64><<<pgrid, pblock, 0, st>>>(g, U, hop_coef<double>(m_w, mu), hop_coef<double>(m_w, -mu),
-                                                          lz, (const double2*)vec.vh, (const double2*)vec.wh,
-                                                          (double2*)vec.av, (double2*)vec.aw);
+                                                           lz, (const double2*)vec.vh, (const double2*)vec.wh,
+                                                           (double2*)vec.av, (double2*)vec.aw);
+  else if (lf == LINK_F16R12)
+    k_lz_pair<float, LINK_F16R12><<<pgrid, pblock, 0, st>>>(g, U, hop_coef<float>(m_w, mu), hop_coef<float>(m_w, -mu),
+                                                             lz, (const float2*)vec.vh, (const float2*)vec.wh,
+                                                             (float2*)vec.av, (float2*)vec.aw);
+  else
+    k_lz_pair<float, LINK_F32><<<pgrid, pblock, 0, st>>>(g, U, hop_coef<float>(m_w, mu), hop_coef<float>(m_w, -mu),
+                                                          lz, (const float2*)vec.vh, (const float2*)vec.wh,
+                                                          (float2*)vec.av, (float2*)vec.aw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_update(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, cudaStream_t st) {
+  dim3 grid((g.vol + kBlock - 1) / kBlock, lz.nrhs);
+  if (f64)
     k_lz_update<double><<<grid, kBlock, 0, st>>>(g, lz, (double2*)vec.vh, (double2*)vec.wh, (const double2*)vec.av,
                                                   (const double2*)vec.aw);
-  } else {
-    if (lf == LINK_F16R12)
-      k_lz_pair<float, LINK_F16R12><<<pgrid, pblock, 0, st>>>(g, U, hop_coef<float>(m_w, mu),
-                                                              hop_coef<float>(m_w, -mu), lz, (const float2*)vec.vh,
-                                                              (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
-    else
-      k_lz_pair<float, LINK_F32><<<pgrid, pblock, 0, st>>>(g, U, hop_coef<float>(m_w, mu), hop_coef<float>(m_w, -mu),
-                                                           lz, (const float2*)vec.vh, (const float2*)vec.wh,
-                                                           (float2*)vec.av, (float2*)vec.aw);
+  else
     k_lz_update<float><<<grid, kBlock, 0, st>>>(g, lz, (float2*)vec.vh, (float2*)vec.wh, (const float2*)vec.av,
                                                  (const float2*)vec.aw);
-  }
   return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, const LzDev& lz,
+                                const LzVecs& vec, cudaStream_t st) {
+  cudaError_t e = launch_lanczos_pair(g, U, lf, f64, m_w, mu, lz, vec, st);
+  if (e != cudaSuccess) return e;
+  return launch_lanczos_update(g, f64, lz, vec, st);
 }
 
 // ------------------------------------------------------------------ combine

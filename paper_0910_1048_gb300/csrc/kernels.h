@@ -59,6 +59,10 @@ cudaError_t launch_defl_dots(const Geom& g, int nrhs, int m, const double2* b, c
 cudaError_t launch_lanczos_start(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, const double2* b,
                                  int m, const double2* R, const double2* L, const double* lam_sign,
                                  double2* dots, cudaStream_t st);
+// The two launches of step j (read from lz.j): pair stencil + alpha, biorthogonal update.
+cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
+                                const LzDev& lz, const LzVecs& vec, cudaStream_t st);
+cudaError_t launch_lanczos_update(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, cudaStream_t st);
 // One step j (read from lz.j): pair stencil + alpha, then the biorthogonal update.
 cudaError_t launch_lanczos_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
                                 const LzDev& lz, const LzVecs& vec, cudaStream_t st);
@@ -102,8 +106,10 @@ struct MsVecs {
 
 cudaError_t launch_ms_start(const Geom& g, bool f64, const MsDev& ms, const MsVecs& v, const double2* b, int m,
                             const double2* R, const double2* L, const double* lam_sign, double2* dots, cudaStream_t st);
+// One iteration (four launches). With timing events (may be null): ev[0] before the first
+// pair stencil, ev[1] after it, ev[2] before the direction update, ev[3] after it.
 cudaError_t launch_ms_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, const MsDev& ms,
-                           const MsVecs& v, cudaStream_t st);
+                           const MsVecs& v, cudaStream_t st, cudaEvent_t* ev = nullptr);
 // x (canonical complex128) = x_P + AX (AX native FP64, = H_W(mu) X)
 cudaError_t launch_ms_finish(const Geom& g, int nrhs, const double2* ax, const double2* xp, double2* x, cudaStream_t st);
 

@@ -321,22 +321,26 @@ cudaError_t launch_ms_start(const Geom& g, bool f64, const MsDev& ms, const MsVe
 
 template <class R, int LF>
 static cudaError_t ms_step_t(const Geom& g, const Links& U, double m_w, double mu, const MsDev& ms, const MsVecs& v,
-                             cudaStream_t st) {
+                             cudaStream_t st, cudaEvent_t* ev) {
   dim3 grid((g.vol + kBlock - 1) / kBlock, ms.nrhs);
   dim3 pgrid((g.vol + kPairSites - 1) / kPairSites, ms.nrhs), pblock(kPairSites, 2);
   HopCoef<R> cp = hop_coef<R>(m_w, mu), cm = hop_coef<R>(m_w, -mu);
+  if (ev) cudaEventRecord(ev[0], st);
   k_ms_pair<R, LF, 0><<<pgrid, pblock, 0, st>>>(g, U, cp, cm, ms, v);
+  if (ev) cudaEventRecord(ev[1], st);
   k_ms_pair<R, LF, 1><<<pgrid, pblock, 0, st>>>(g, U, cp, cm, ms, v);
   k_ms_update<R><<<grid, kBlock, 0, st>>>(g, ms, v);
+  if (ev) cudaEventRecord(ev[2], st);
   k_ms_dirs<R><<<grid, kBlock, 0, st>>>(g, ms, v);
+  if (ev) cudaEventRecord(ev[3], st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ms_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, const MsDev& ms,
-                           const MsVecs& v, cudaStream_t st) {
-  if (f64) return ms_step_t<double, LINK_F64>(g, U, m_w, mu, ms, v, st);
-  if (lf == LINK_F16R12) return ms_step_t<float, LINK_F16R12>(g, U, m_w, mu, ms, v, st);
-  return ms_step_t<float, LINK_F32>(g, U, m_w, mu, ms, v, st);
+                           const MsVecs& v, cudaStream_t st, cudaEvent_t* ev) {
+  if (f64) return ms_step_t<double, LINK_F64>(g, U, m_w, mu, ms, v, st, ev);
+  if (lf == LINK_F16R12) return ms_step_t<float, LINK_F16R12>(g, U, m_w, mu, ms, v, st, ev);
+  return ms_step_t<float, LINK_F32>(g, U, m_w, mu, ms, v, st, ev);
 }
 
 __global__ void k_ms_finish(int vol, const double2* ax, const double2* xp, double2* x) {

@@ -2,7 +2,9 @@
 //
 // Algorithm 4 ends with x = x_P + beta V_k f(H_k) e_1; Section 2 evaluates f on the small
 // projected matrix by an eigendecomposition or Roberts' Newton iteration, an O(k^3) term
-// (Proposition 2). Here the default route is O(k^2):
+// (Proposition 2). Two faster routes are implemented here.
+//
+// Eigenvector route (O(k^2), accurate to about cond(Z)^2 u):
 //  1. Diagonal similarity S = D^-1 H_k D with d_1 = 1, d_{j+1} = d_j delta_j / gamma_j,
 //     gamma_j = sqrt(beta_j delta_j), makes S complex symmetric (S^T = S) with diagonal
 //     alpha and off-diagonal gamma. sign(H_k) e_1 = D sign(S) e_1.
@@ -14,6 +16,15 @@
 // Complex orthogonal rotations are not unitary; the result is therefore checked
 // (sign(S)^2 e_1 = e_1 and H_k y = sign(H_k) H_k e_1) and, if a check fails, recomputed
 // by scaled Newton on the dense k x k matrix (the paper's Roberts iteration, O(k^3)).
+//
+// Rational route, the default (more accurate; O(k^2) for the Ritz values, O(s k) per evaluation): Roberts'
+// unscaled Newton iterate is exactly the Kenney-Laub function g_s of Section 5, whose
+// partial fractions (Eq. pfe_s) give
+//     sign(H_k) e_1 ~ g_s(c H_k) e_1 = c H_k sum_i omega_i (c^2 H_k^2 - sigma_i)^-1 e_1,
+// s solves with the pentadiagonal H_k^2 (banded LU with partial pivoting). c and s are chosen
+// from the Ritz values mu (right half plane representatives) so that every Ritz value meets
+//     2 |(c mu - 1)/(c mu + 1)|^{2s} <= eps      (the proof of Theorem 1),
+// and the result is accepted when the involution residual |g(cH) y - e_1| is small.
 #include <algorithm>
 #include <complex>
 #include <vector>
@@ -261,8 +272,202 @@ ovl_status small_sign_ql(int k, const cz* al, const cz* be, const cz* de, cz* y,
   return OVL_OK;
 }
 
-// method 0 auto (QL, Newton on failure), 1 QL only, 2 Newton only
-ovl_status small_sign(int k, const cz* al, const cz* be, const cz* de, cz* y, int method) {
+namespace {
+
+// Eigenvalues only of the complex symmetric tridiagonal (same sweeps as cs_qr, no rotations kept).
+bool cs_eigs(std::vector<cz> d, std::vector<cz> e, std::vector<cz>& lam) {
+  const int k = (int)d.size();
+  const double eps = 1e-15;
+  long long budget = 60LL * k + 100;
+  auto negligible = [&](int i) { return std::abs(e[i]) <= eps * (std::abs(d[i]) + std::abs(d[i + 1])); };
+  int hi = k - 1;
+  while (hi > 0) {
+    if (negligible(hi - 1)) {
+      e[hi - 1] = 0;
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && !negligible(lo - 1)) --lo;
+    if (lo > 0) e[lo - 1] = 0;
+    if (--budget < 0) return false;
+    cz a = d[hi - 1], b = d[hi], ee = e[hi - 1];
+    cz half = 0.5 * (a - b);
+    cz disc = std::sqrt(half * half + ee * ee);
+    cz m1 = 0.5 * (a + b) + disc, m2 = 0.5 * (a + b) - disc;
+    cz shift = std::abs(m1 - b) < std::abs(m2 - b) ? m1 : m2;
+    cz x = d[lo] - shift, z = e[lo];
+    for (int p = lo; p < hi; ++p) {
+      const int q = p + 1;
+      cz rho = std::sqrt(x * x + z * z);
+      double scale = std::sqrt(std::norm(x) + std::norm(z));
+      if (!(std::abs(rho) > 1e-8 * scale) || scale == 0.0) return false;
+      cz c = x / rho, s = -z / rho;
+      if (p > lo) e[p - 1] = rho;
+      cz dp = d[p], dq = d[q], ep = e[p];
+      cz c2 = c * c, s2 = s * s, cs = c * s;
+      d[p] = dp * c2 - 2.0 * ep * cs + dq * s2;
+      d[q] = dp * s2 + 2.0 * ep * cs + dq * c2;
+      e[p] = cs * (dp - dq) + ep * (c2 - s2);
+      if (q < hi) {
+        z = -s * e[q];
+        e[q] = c * e[q];
+        x = e[p];
+      }
+    }
+  }
+  lam = d;
+  return true;
+}
+
+// Ritz values of H_k (via its complex symmetric similar S).
+bool ritz_values(int k, const cz* al, const cz* be, const cz* de, std::vector<cz>& lam) {
+  std::vector<cz> dg(al, al + k), gm(k - 1);
+  for (int i = 0; i + 1 < k; ++i) {
+    gm[i] = std::sqrt(be[i] * de[i]);
+    if (gm[i] == cz(0)) return false;
+  }
+  return cs_eigs(dg, gm, lam);
+}
+
+// (c, s): fewest poles with 2 |(c mu - 1)/(c mu + 1)|^{2s} <= eps over the Ritz values.
+bool choose_scale(const std::vector<cz>& lam, double eps, int s_max, double* c_out, int* s_out) {
+  std::vector<cz> mu;
+  double amin = 1e300, amax = 0;
+  for (cz l : lam) {
+    cz m = l.real() >= 0 ? l : -l;
+    if (!(m.real() > 0)) return false;
+    mu.push_back(m);
+    amin = std::min(amin, std::abs(m));
+    amax = std::max(amax, std::abs(m));
+  }
+  double best_q = 1.0, best_c = 1.0;
+  const int ng = 160;
+  for (int t = 0; t <= ng; ++t) {
+    double c = std::exp(std::log(1.0 / amax) + (std::log(1.0 / amin) - std::log(1.0 / amax)) * t / ng);
+    double q = 0;
+    for (cz m : mu) q = std::max(q, std::abs((c * m - 1.0) / (c * m + 1.0)));
+    if (q < best_q) best_q = q, best_c = c;
+  }
+  if (!(best_q < 1.0)) return false;
+  double sr = std::log(eps / 2.0) / (2.0 * std::log(best_q));
+  int s = std::max(1, (int)std::ceil(sr));
+  if (s > s_max) return false;
+  *c_out = best_c;
+  *s_out = s;
+  return true;
+}
+
+// out = g_s(c H) v = c H sum_i omega_i (c^2 H^2 - sigma_i)^-1 v (Eq. pfe_s), banded solves.
+void rational_apply(int k, const cz* al, const cz* be, const cz* de, double c, int s, const cz* v, cz* out) {
+  // H^2 bands: d0 main, u1/u2 upper, l1/l2 lower
+  std::vector<cz> d0(k), u1(k, 0.0), u2(k, 0.0), l1(k, 0.0), l2(k, 0.0);
+  for (int i = 0; i < k; ++i) {
+    cz t = al[i] * al[i];
+    if (i > 0) t += de[i - 1] * be[i - 1];
+    if (i + 1 < k) t += be[i] * de[i];
+    d0[i] = t;
+    if (i + 1 < k) {
+      u1[i] = al[i] * be[i] + be[i] * al[i + 1];
+      l1[i] = de[i] * al[i] + al[i + 1] * de[i];
+    }
+    if (i + 2 < k) {
+      u2[i] = be[i] * be[i + 1];
+      l2[i] = de[i + 1] * de[i];
+    }
+  }
+  const double c2 = c * c;
+  std::vector<cz> acc(k, 0.0);
+  // band storage for LU with partial pivoting: row i holds columns i-2..i+4 (7 entries)
+  const int W = 7, OFF = 2;
+  std::vector<cz> a((size_t)k * W), rhs(k);
+  for (int sh = 1; sh <= s; ++sh) {
+    const double th = 3.14159265358979323846 / (2.0 * s) * (sh - 0.5);
+    const double om = 1.0 / (s * std::cos(th) * std::cos(th));
+    const double sg = -std::tan(th) * std::tan(th);
+    std::fill(a.begin(), a.end(), cz(0));
+    for (int i = 0; i < k; ++i) {
+      cz* r = &a[(size_t)i * W];
+      if (i >= 2) r[OFF - 2] = c2 * l2[i - 2];
+      if (i >= 1) r[OFF - 1] = c2 * l1[i - 1];
+      r[OFF] = c2 * d0[i] - sg;
+      if (i + 1 < k) r[OFF + 1] = c2 * u1[i];
+      if (i + 2 < k) r[OFF + 2] = c2 * u2[i];
+      rhs[i] = v[i];
+    }
+    auto at = [&](int i, int j) -> cz& { return a[(size_t)i * W + (j - i + OFF)]; };
+    for (int col = 0; col < k; ++col) {
+      int last = std::min(k - 1, col + 2);
+      int piv = col;
+      double best = std::abs(at(col, col));
+      for (int r = col + 1; r <= last; ++r)
+        if (std::abs(at(r, col)) > best) best = std::abs(at(r, col)), piv = r;
+      int cend = std::min(k - 1, col + 4);
+      if (piv != col) {
+        for (int j = col; j <= cend; ++j) std::swap(at(piv, j), at(col, j));
+        std::swap(rhs[piv], rhs[col]);
+      }
+      cz pinv = 1.0 / at(col, col);
+      for (int r = col + 1; r <= last; ++r) {
+        cz f = at(r, col) * pinv;
+        if (f == cz(0)) continue;
+        for (int j = col; j <= cend; ++j) at(r, j) -= f * at(col, j);
+        rhs[r] -= f * rhs[col];
+      }
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      cz t = rhs[i];
+      int cend = std::min(k - 1, i + 4);
+      for (int j = i + 1; j <= cend; ++j) t -= at(i, j) * rhs[j];
+      rhs[i] = t / at(i, i);
+    }
+    for (int i = 0; i < k; ++i) acc[i] += om * rhs[i];
+  }
+  for (int i = 0; i < k; ++i) {
+    cz t = al[i] * acc[i];
+    if (i > 0) t += de[i - 1] * acc[i - 1];
+    if (i + 1 < k) t += be[i] * acc[i + 1];
+    out[i] = c * t;
+  }
+}
+
+}  // namespace
+
+// Rational route with a (c, s) hint; hint->s == 0 means "compute from the Ritz values".
+// Returns OVL_OK when the involution residual is below tol_inv.
+ovl_status small_sign_rational(int k, const cz* al, const cz* be, const cz* de, cz* y, double* hint_c, int* hint_s,
+                               double* inv_res) {
+  const double eps = 1e-15, tol_inv = 1e-11;
+  const int s_max = 4000;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (*hint_s <= 0 || attempt == 1) {
+      std::vector<cz> lam;
+      if (!ritz_values(k, al, be, de, lam)) return OVL_ENOCONV;
+      double lmax = 0;
+      for (cz l : lam) lmax = std::max(lmax, std::abs(l));
+      for (cz l : lam)
+        if (std::abs(l.real()) <= 1e-14 * lmax) {
+          set_error("small_sign: Ritz value on the imaginary axis");
+          return OVL_EILLPOSED;
+        }
+      if (!choose_scale(lam, eps, s_max, hint_c, hint_s)) return OVL_ENOCONV;
+    }
+    std::vector<cz> e1(k, 0.0), chk(k);
+    e1[0] = 1.0;
+    rational_apply(k, al, be, de, *hint_c, *hint_s, e1.data(), y);
+    rational_apply(k, al, be, de, *hint_c, *hint_s, y, chk.data());
+    double r = std::abs(chk[0] - 1.0);
+    for (int i = 1; i < k; ++i) r = std::max(r, std::abs(chk[i]));
+    if (inv_res) *inv_res = r;
+    if (r <= tol_inv) return OVL_OK;
+  }
+  return OVL_ENOCONV;
+}
+
+// method 0 auto (rational, then QL eigenvectors, then Newton), 1 QL only, 2 Newton only,
+// 3 rational only. hint_c/hint_s (may be null) carry (c, s) between calls on growing H_k.
+ovl_status small_sign(int k, const cz* al, const cz* be, const cz* de, cz* y, int method, double* hint_c = nullptr,
+                      int* hint_s = nullptr) {
   if (k < 1) {
     set_error("small_sign: k < 1");
     return OVL_EINVAL;
@@ -274,6 +479,14 @@ ovl_status small_sign(int k, const cz* al, const cz* be, const cz* de, cz* y, in
     }
     y[0] = al[0].real() > 0 ? 1.0 : -1.0;
     return OVL_OK;
+  }
+  if (method == 0 || method == 3) {
+    double c = hint_c ? *hint_c : 0.0;
+    int sp = hint_s ? *hint_s : 0;
+    ovl_status s = small_sign_rational(k, al, be, de, y, &c, &sp, nullptr);
+    if (hint_c && s == OVL_OK) *hint_c = c;
+    if (hint_s) *hint_s = s == OVL_OK ? sp : 0;
+    if (s == OVL_OK || method == 3 || s == OVL_EILLPOSED) return s;
   }
   if (method != 2) {
     double chk = 0;
@@ -288,7 +501,7 @@ ovl_status small_sign(int k, const cz* al, const cz* be, const cz* de, cz* y, in
 extern "C" ovl_status ovl_small_sign(int32_t k, const void* alpha, const void* beta, const void* delta, void* y,
                                      int32_t method) {
   ovl::clear_error();
-  if (k < 1 || !alpha || !y || (k > 1 && (!beta || !delta)) || method < 0 || method > 2) {
+  if (k < 1 || !alpha || !y || (k > 1 && (!beta || !delta)) || method < 0 || method > 3) {
     ovl::set_error("ovl_small_sign: invalid arguments");
     return OVL_EINVAL;
   }

@@ -15,7 +15,8 @@
 namespace ovl {
 
 ovl_status small_sign(int k, const std::complex<double>* al, const std::complex<double>* be,
-                      const std::complex<double>* de, std::complex<double>* y, int method);
+                      const std::complex<double>* de, std::complex<double>* y, int method, double* hint_c,
+                      int* hint_s);
 
 struct DirectWS {
   int nrhs = 0, kmax = 0, f64 = -1, m = 0, vol = 0;
@@ -42,8 +43,10 @@ struct DirectWS {
     int* status = nullptr;
   } h[2];
   void* h_block = nullptr;
-  // graph of `gchunk` steps
-  cudaGraphExec_t graph = nullptr;
+  // two graphs of `gchunk` steps (alternating chunks); each records timing events around
+  // its first step's pair stencil (tev[q][0..1]) and update (tev[q][2..3])
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaEvent_t tev[2][4] = {};
   int gchunk = 0;
   double g_mw = 0, g_mu = 0;
   int g_lf = -1;
@@ -53,7 +56,11 @@ struct DirectWS {
 
 void free_direct_ws(DirectWS* w) {
   if (!w) return;
-  if (w->graph) cudaGraphExecDestroy(w->graph);
+  for (int q = 0; q < 2; ++q) {
+    if (w->graph[q]) cudaGraphExecDestroy(w->graph[q]);
+    for (auto e : w->tev[q])
+      if (e) cudaEventDestroy(e);
+  }
   if (w->dev_block) cudaFree(w->dev_block);
   if (w->h_block) cudaFreeHost(w->h_block);
   if (w->stream) cudaStreamDestroy(w->stream);
@@ -168,7 +175,10 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
     h.j = (int*)(h.beta0 + nrhs);
     h.status = h.j + nrhs;
   }
-  if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess ||
+  bool ev_ok = true;
+  for (int q = 0; q < 2; ++q)
+    for (int i = 0; i < 4; ++i) ev_ok = ev_ok && cudaEventCreate(&w->tev[q][i]) == cudaSuccess;
+  if (!ev_ok || cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming) != cudaSuccess) {
     free_direct_ws(w);
     set_error("apply_sign: cannot create stream/event");
@@ -200,6 +210,8 @@ struct RhsState {
   double est = 1e300;
   int status = OVL_PENDING;        // OK / ENOCONV / EBREAKDOWN / EILLPOSED once final
   bool done = false;
+  double hint_c = 0;               // (c, s) of the rational small sign, reused between checks
+  int hint_s = 0;
 };
 
 // Snapshot of rhs r from the pinned mirrors: H_k, y = sign(H_k) e_1, error estimate.
@@ -228,7 +240,7 @@ static ovl_status evaluate_rhs(DirectWS* w, int q, int r, RhsState& rs, double* 
   }
   std::vector<std::complex<double>> y(k);
   auto t0 = std::chrono::steady_clock::now();
-  ovl_status s = small_sign(k, al.data(), be.data(), de.data(), y.data(), 0);
+  ovl_status s = small_sign(k, al.data(), be.data(), de.data(), y.data(), 0, &rs.hint_c, &rs.hint_s);
   *t_small += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (s != OVL_OK) return s;
   double ny = 0, dif = 0;
@@ -285,37 +297,64 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   OVL_CHECK_CUDA(launch_lanczos_start(g, f64, w->lz, vec, bd, m, lat->defl.R, lat->defl.L, w->lam_sign, w->dots, st));
   const Links U = lat->links();
   const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 20, kmax));
-  // graph of `chunk` steps (re-captured when the step's parameters change)
+  // one step, with timing events around its two launches when `tev` is given
+  auto step = [&](cudaEvent_t* tev) -> cudaError_t {
+    cudaError_t e;
+    if (tev && (e = cudaEventRecord(tev[0], st))) return e;
+    if ((e = launch_lanczos_pair(g, U, lf, f64, p->m_W, p->mu, w->lz, vec, st))) return e;
+    if (tev && (e = cudaEventRecord(tev[1], st))) return e;
+    if (tev && (e = cudaEventRecord(tev[2], st))) return e;
+    if ((e = launch_lanczos_update(g, f64, w->lz, vec, st))) return e;
+    if (tev && (e = cudaEventRecord(tev[3], st))) return e;
+    return cudaSuccess;
+  };
+  // graphs of `chunk` steps (re-captured when the step's parameters change)
   bool use_graph = p->use_graphs != 0;
-  if (use_graph && !(w->graph && w->gchunk == chunk && w->g_mw == p->m_W && w->g_mu == p->mu && w->g_lf == lf)) {
-    if (w->graph) cudaGraphExecDestroy(w->graph);
-    w->graph = nullptr;
-    cudaGraph_t gr;
-    OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < chunk; ++i) {
-      cudaError_t e = launch_lanczos_step(g, U, lf, f64, p->m_W, p->mu, w->lz, vec, st);
+  if (use_graph && !(w->graph[0] && w->gchunk == chunk && w->g_mw == p->m_W && w->g_mu == p->mu && w->g_lf == lf)) {
+    for (int q = 0; q < 2; ++q) {
+      if (w->graph[q]) cudaGraphExecDestroy(w->graph[q]);
+      w->graph[q] = nullptr;
+    }
+    for (int q = 0; q < 2; ++q) {
+      cudaGraph_t gr;
+      OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = step(i == 0 ? w->tev[q] : nullptr);
+      cudaError_t e2 = cudaStreamEndCapture(st, &gr);
       if (e != cudaSuccess) {
-        cudaStreamEndCapture(st, &gr);
         set_error("apply_sign: capture failed: %s", cudaGetErrorString(e));
         return OVL_ECUDA;
       }
+      OVL_CHECK_CUDA(e2);
+      e = cudaGraphInstantiate(&w->graph[q], gr, 0);
+      cudaGraphDestroy(gr);
+      OVL_CHECK_CUDA(e);
     }
-    OVL_CHECK_CUDA(cudaStreamEndCapture(st, &gr));
-    cudaError_t e = cudaGraphInstantiate(&w->graph, gr, 0);
-    cudaGraphDestroy(gr);
-    OVL_CHECK_CUDA(e);
     w->gchunk = chunk;
     w->g_mw = p->m_W;
     w->g_mu = p->mu;
     w->g_lf = lf;
   }
-  auto run_steps = [&](int nsteps) -> cudaError_t {
-    if (use_graph && nsteps == chunk) return cudaGraphLaunch(w->graph, st);
+  int launches = 1 + (m > 0 ? 1 : 0) + 1;  // start (+ deflation dots) and the combine
+  auto run_steps = [&](int nsteps, int q) -> cudaError_t {
+    launches += 2 * nsteps;
+    if (use_graph && nsteps == chunk) return cudaGraphLaunch(w->graph[q], st);
     for (int i = 0; i < nsteps; ++i) {
-      cudaError_t e = launch_lanczos_step(g, U, lf, f64, p->m_W, p->mu, w->lz, vec, st);
+      cudaError_t e = step(i == 0 && q >= 0 ? w->tev[q] : nullptr);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+  };
+  double t_pair = 0, t_upd = 0;
+  int nsamp = 0;
+  auto sample = [&](int q) {  // durations of the first step of the chunk behind slot q
+    float a = 0, b = 0;
+    if (cudaEventElapsedTime(&a, w->tev[q][0], w->tev[q][1]) == cudaSuccess &&
+        cudaEventElapsedTime(&b, w->tev[q][2], w->tev[q][3]) == cudaSuccess) {
+      t_pair += a;
+      t_upd += b;
+      ++nsamp;
+    }
   };
   std::vector<RhsState> rs(nrhs);
   double t_small = 0;
@@ -329,11 +368,11 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   const bool fixed = p->fixed_k > 0;
   auto launch_chunk = [&]() -> cudaError_t {
     int ns = std::min(chunk, kmax - queued);
-    cudaError_t e = run_steps(ns);
-    if (e) return e;
-    queued += ns;
     int q = next_slot;
     next_slot ^= 1;
+    cudaError_t e = run_steps(ns, q);
+    if (e) return e;
+    queued += ns;
     if ((e = queue_scalar_copies(w, q, st))) return e;
     evq[q] = queued;
     if ((e = cudaEventRecord(evc[q], st))) return e;
@@ -343,12 +382,15 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   ovl_status result = OVL_OK;
   cudaError_t ce = cudaSuccess;
   int qlast = 0;
+  bool any_running = true;  // a chunk launched while some rhs ran did real work
   if (fixed) {
     while (queued < kmax && ce == cudaSuccess) {
       int ns = std::min(chunk, kmax - queued);
-      ce = run_steps(ns);
+      ce = run_steps(ns, 0);
       queued += ns;
     }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce == cudaSuccess) sample(0);
     if (ce == cudaSuccess) ce = queue_scalar_copies(w, 0, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     for (int r = 0; r < nrhs && ce == cudaSuccess; ++r) {
@@ -369,6 +411,7 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
       pending.erase(pending.begin());
       ce = cudaEventSynchronize(evc[q]);
       if (ce) break;
+      if (any_running) sample(q);
       qlast = q;
       const bool final_snapshot = evq[q] >= kmax;
       bool all_done = true;
@@ -399,6 +442,8 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
         }
         all_done = all_done && s.done;
       }
+      any_running = false;
+      for (int r = 0; r < nrhs; ++r) any_running = any_running || w->h[q].status[r] == 0;
       if (all_done || ce) break;
     }
   }
@@ -457,6 +502,10 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
       info[r].t_total_ms = t_total;
       info[r].t_small_ms = t_small;
       info[r].residual = 0;
+      info[r].t_kernel_ms = nsamp ? t_pair / nsamp : 0;
+      info[r].t_update_ms = nsamp ? t_upd / nsamp : 0;
+      info[r].kernel_samples = nsamp;
+      info[r].kernel_launches = launches;
     }
   }
   if (result != OVL_OK) set_error("apply_sign: at least one right-hand side ended with status %d", result);

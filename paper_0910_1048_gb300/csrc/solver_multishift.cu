@@ -31,7 +31,8 @@ struct MultiWS {
   double2* bdev = nullptr;
   double2* xdev = nullptr;
   int* h_status = nullptr;  // pinned [2][nrhs] status + [2][nrhs] k
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // alternating chunks, each with its events
+  cudaEvent_t tev[2][4] = {};
   int gchunk = 0, g_lf = -1;
   double g_mw = 0, g_mu = 0, g_s1 = 0, g_tol = 0;
   cudaStream_t stream = nullptr;
@@ -40,7 +41,11 @@ struct MultiWS {
 
 void free_multi_ws(MultiWS* w) {
   if (!w) return;
-  if (w->graph) cudaGraphExecDestroy(w->graph);
+  for (int q = 0; q < 2; ++q) {
+    if (w->graph[q]) cudaGraphExecDestroy(w->graph[q]);
+    for (auto e : w->tev[q])
+      if (e) cudaEventDestroy(e);
+  }
   if (w->dev) cudaFree(w->dev);
   if (w->h_status) cudaFreeHost(w->h_status);
   if (w->stream) cudaStreamDestroy(w->stream);
@@ -126,7 +131,10 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m)
   ms.count = (unsigned*)(b + o_cn);
   w->dots = (double2*)(b + o_do);
   w->lam_sign = (double*)(b + o_ls);
-  if (cudaMemset(ms.count, 0, (size_t)nrhs * 4) != cudaSuccess ||
+  bool ev_ok = true;
+  for (int q = 0; q < 2; ++q)
+    for (int i = 0; i < 4; ++i) ev_ok = ev_ok && cudaEventCreate(&w->tev[q][i]) == cudaSuccess;
+  if (!ev_ok || cudaMemset(ms.count, 0, (size_t)nrhs * 4) != cudaSuccess ||
       cudaMallocHost(&w->h_status, (size_t)4 * nrhs * sizeof(int)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&w->ev[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -224,20 +232,25 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
   const Links U = lat->links();
   const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 20, p->k_max));
   const bool use_graph = p->use_graphs != 0;
-  if (use_graph && !(w->graph && w->gchunk == chunk && w->g_lf == lf && w->g_mw == p->m_W && w->g_mu == p->mu &&
+  if (use_graph && !(w->graph[0] && w->gchunk == chunk && w->g_lf == lf && w->g_mw == p->m_W && w->g_mu == p->mu &&
                      w->g_s1 == s1 && w->g_tol == p->tol)) {
-    if (w->graph) cudaGraphExecDestroy(w->graph);
-    w->graph = nullptr;
-    cudaGraph_t gr;
-    OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st);
-    cudaError_t e2 = cudaStreamEndCapture(st, &gr);
-    OVL_CHECK_CUDA(e);
-    OVL_CHECK_CUDA(e2);
-    e = cudaGraphInstantiate(&w->graph, gr, 0);
-    cudaGraphDestroy(gr);
-    OVL_CHECK_CUDA(e);
+    for (int q = 0; q < 2; ++q) {
+      if (w->graph[q]) cudaGraphExecDestroy(w->graph[q]);
+      w->graph[q] = nullptr;
+    }
+    for (int q = 0; q < 2; ++q) {
+      cudaGraph_t gr;
+      OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      for (int i = 0; i < chunk && e == cudaSuccess; ++i)
+        e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st, i == 0 ? w->tev[q] : nullptr);
+      cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+      OVL_CHECK_CUDA(e);
+      OVL_CHECK_CUDA(e2);
+      e = cudaGraphInstantiate(&w->graph[q], gr, 0);
+      cudaGraphDestroy(gr);
+      OVL_CHECK_CUDA(e);
+    }
     w->gchunk = chunk;
     w->g_lf = lf;
     w->g_mw = p->m_W;
@@ -245,13 +258,26 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
     w->g_s1 = s1;
     w->g_tol = p->tol;
   }
-  auto run_chunk = [&](int ns) -> cudaError_t {
-    if (use_graph && ns == chunk) return cudaGraphLaunch(w->graph, st);
+  int launches = 1 + (m > 0 ? 1 : 0) + 2;  // start (+ deflation dots), final stencil and finish
+  auto run_chunk = [&](int ns, int q) -> cudaError_t {
+    launches += 4 * ns;
+    if (use_graph && ns == chunk) return cudaGraphLaunch(w->graph[q], st);
     for (int i = 0; i < ns; ++i) {
-      cudaError_t e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st);
+      cudaError_t e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st, i == 0 ? w->tev[q] : nullptr);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+  };
+  double t_pair = 0, t_upd = 0;
+  int nsamp = 0;
+  auto sample = [&](int q) {
+    float a = 0, b = 0;
+    if (cudaEventElapsedTime(&a, w->tev[q][0], w->tev[q][1]) == cudaSuccess &&
+        cudaEventElapsedTime(&b, w->tev[q][2], w->tev[q][3]) == cudaSuccess) {
+      t_pair += a;
+      t_upd += b;
+      ++nsamp;
+    }
   };
   // chunks with status snapshots; one chunk stays queued while the host looks at the last
   int queued = 0, slot = 0;
@@ -259,7 +285,7 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
   cudaError_t ce = cudaSuccess;
   auto launch = [&]() -> cudaError_t {
     int ns = std::min(chunk, p->k_max - queued);
-    cudaError_t e = run_chunk(ns);
+    cudaError_t e = run_chunk(ns, slot);
     if (e) return e;
     queued += ns;
     int* hs = w->h_status + (size_t)slot * 2 * nrhs;
@@ -271,7 +297,7 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
     return cudaSuccess;
   };
   ce = launch();
-  bool done = false;
+  bool done = false, any_running = true;
   while (ce == cudaSuccess && !done) {
     if (queued < p->k_max && pend.size() < 2) {
       ce = launch();
@@ -281,10 +307,12 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
     pend.erase(pend.begin());
     ce = cudaEventSynchronize(w->ev[q]);
     if (ce) break;
+    if (any_running) sample(q);
     const int* hs = w->h_status + (size_t)q * 2 * nrhs;
     done = true;
     for (int r = 0; r < nrhs; ++r)
       if (hs[r] == 0) done = false;
+    any_running = !done;
     if (pend.empty() && queued >= p->k_max) done = true;
   }
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
@@ -332,6 +360,10 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
       info[r].t_total_ms = t_total;
       info[r].t_small_ms = 0;
       info[r].residual = worst;
+      info[r].t_kernel_ms = nsamp ? t_pair / nsamp : 0;
+      info[r].t_update_ms = nsamp ? t_upd / nsamp : 0;
+      info[r].kernel_samples = nsamp;
+      info[r].kernel_launches = launches;
     }
   }
   if (result != OVL_OK) set_error("apply_sign: at least one right-hand side ended with status %d", result);

@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU: the library loads, exports every function declared in
 include/ovl.h, and its host-side pieces agree with the oracle:
-  - ovl_small_sign (sign(H_k) e_1, Section 2 / Algorithm 4's last line) vs eigendecomposition;
+  - ovl_small_sign (sign(H_k) e_1, Section 2 / Algorithm 4's last line) vs eigendecomposition,
+    for each route (rational g_s(cH) e_1, complex-symmetric eigenvectors, dense Newton);
   - ovl_rational_coeffs (Eq. pfe_s with Eq. no_of_poles; Zolotarev) vs the oracle's coefficients;
   - argument errors come back as EINVAL with a message, not a crash.
 """
@@ -46,7 +47,7 @@ def _lanczos_t(mu, k, seed=51, dims=(2, 2, 4, 4)):
 
 
 @pytest.mark.parametrize("mu,k", [(0.0, 30), (0.3, 10), (0.3, 60), (0.3, 150), (1.0, 80)])
-@pytest.mark.parametrize("method", [0, 1, 2])
+@pytest.mark.parametrize("method", [0, 1, 2, 3])
 def test_small_sign_matches_eig(ovl, mu, k, method):
     al, be, de = _lanczos_t(mu, k)
     ref = lanczos.sign_tridiag_e1(al, be, de)
@@ -54,7 +55,9 @@ def test_small_sign_matches_eig(ovl, mu, k, method):
     if method == 1 and st != ovl.OVL_OK:
         pytest.skip("QL route declined (checked fallback exists): status %d" % st)
     assert st == ovl.OVL_OK
-    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-9
+    # the eigenvector route is limited by cond(Z)^2 u; the rational and Newton routes are not
+    tol = 1e-9 if method == 1 else 1e-11
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < tol
 
 
 def test_small_sign_closed_forms(ovl):
