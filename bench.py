@@ -1,0 +1,388 @@
+"""Benchmark: sign(H_W(mu)) b solves per second on GB300.
+
+One step = one pass of the hot path over one batch: for each mu of the workload, one solve
+x = sign(H_W(mu)) b through ovl_apply_sign (LR deflation set, Lanczos or multishift
+iteration, sign of the projected matrix, combine), inputs resident in HBM. L2 is flushed
+(a 256 MB write) between timed steps. `e2e` repeats the steps through the same call with
+host buffers (copies inside the timed region). `roofline` reports the dominant kernel (the
+fused pair stencil) from CUDA events recorded around its launches inside the library.
+`--impl reference` times the oracle (plain FP64 CPU restatement of Algorithm 4) on the
+host cores on a bounded sample of the same workload.
+
+Multi-GPU: replicas only (each rank solves its own copies, no collective on the data path);
+value = solves of all ranks / max over ranks of the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sgn(H_W)b solves/s at rel.err 1e-8"
+UNIT = "solves/s"
+
+# Workloads: the lattice, chemical potentials, method and precision of one step.
+WORKLOADS = {
+    # 8^4, n = 49152, mu in {0, 0.1, 0.3}, 16 deflated critical eigenpairs per mu, FP64 direct
+    # two-sided Lanczos-LR (Algorithm 4), k <= 600, stopping at the metric's 1e-8
+    "lattice8_mu0-0.1-0.3_defl16_direct_f64": dict(dims=(8, 8, 8, 8), mus=(0.0, 0.1, 0.3), m=16, method="direct",
+                                                     precision="f64", tol=1e-8, k_max=600),
+    # same lattice and deflation, rational variant (Algorithm 3 + Neuberger, Eq. no_of_poles)
+    "lattice8_mu0-0.1-0.3_defl16_multishift_f64": dict(dims=(8, 8, 8, 8), mus=(0.0, 0.1, 0.3), m=16,
+                                                         method="multishift", precision="f64", tol=1e-8,
+                                                         k_max=5000),
+    # 4^4 smoke-sized case (the oracle finishes it in seconds)
+    "lattice4_mu0.3_direct_f64": dict(dims=(4, 4, 4, 4), mus=(0.3,), m=0, method="direct", precision="f64",
+                                      tol=1e-8, k_max=1200),
+}
+DEFAULT_WORKLOAD = "lattice8_mu0-0.1-0.3_defl16_direct_f64"
+
+# Algorithmic traffic / work of one launch of the fused pair stencil per site:
+# two spinors in (neighbours read once each: 2 x 24 reals), 4 links per site (18 reals each;
+# FP16 12-real: 12 halves), two spinors out; flops: 2 x 1368 per site.
+PAIR_BYTES_PER_SITE = {"f64": 2 * 192 + 576 + 2 * 192, "f32": 2 * 96 + 288 + 2 * 96, "f16": 2 * 96 + 96 + 2 * 96}
+PAIR_FLOPS_PER_SITE = 2 * 1368
+
+# FP64 FMA throughput of this machine's GB300 (measured with an FMA-chain probe) in TFLOP/s
+FP64_PEAK_TFLOPS = None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() in ("active", "0x1", "1"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _setup(ovl, ctx, wl, rng_seed=0):
+    """Lattice, links, sources and per-mu deflation sets (untimed set-up)."""
+    import synth
+    from paper_0910_1048_gb300 import spectrum
+
+    dims = wl["dims"]
+    u = synth.gauge_links(dims, rng_seed)
+    lat = ovl.ovl_create_lattice(ctx, dims, -1)
+    ovl.ovl_set_links(lat, u, ovl.OVL_F64 | ovl.OVL_F32 | ovl.OVL_F16R12)
+    b = synth.gaussian_source(dims, 1000)
+    per_mu = []
+    for mu in wl["mus"]:
+        d = {"mu": mu}
+        if wl["m"] > 0:
+            t0 = time.time()
+            lam, R, L, gap, info = spectrum.critical_eigenpairs(ovl, lat, -2.0, mu, wl["m"])
+            d.update(lam=lam, R=R, L=L, gap=gap, setup_s=time.time() - t0)
+        if wl["method"] == "multishift":
+            d["spec_hi"] = 1.02 * spectrum.largest_modulus(ovl, lat, -2.0, mu)
+        per_mu.append(d)
+    return lat, u, b, per_mu
+
+
+def _params(ovl, wl, d):
+    prec = {"f64": ovl.OVL_PREC_F64, "f32": ovl.OVL_PREC_F32, "f16": ovl.OVL_PREC_F32_F16LINKS}[wl["precision"]]
+    kw = dict(m_W=-2.0, mu=d["mu"], tol=wl["tol"], k_max=wl["k_max"], precision=prec,
+              use_deflation=1 if wl["m"] > 0 else 0, check_every=25)
+    if wl["method"] == "multishift":
+        kw.update(method=ovl.OVL_MULTISHIFT_BICG, spec_lo=0.98 * d["gap"], spec_hi=d["spec_hi"], check_every=20)
+    return ovl.ovl_sign_params_default(**kw)
+
+
+def run_ours(args, wl):
+    import torch
+
+    import paper_0910_1048_gb300 as ovl
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ctx = ovl.ovl_ctx_create(local)
+    lat, u, b, per_mu = _setup(ovl, ctx, wl)
+    n = b.size
+    bdev = torch.from_numpy(b).cuda()
+    xdev = torch.empty_like(bdev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    # one lattice per mu, each holding its own deflation set (set-up, untimed)
+    lats = []
+    for d in per_mu:
+        lt = ovl.ovl_create_lattice(ctx, wl["dims"], -1)
+        ovl.ovl_set_links(lt, u, ovl.OVL_F64 | ovl.OVL_F32 | ovl.OVL_F16R12)
+        if wl["m"] > 0:
+            ovl.ovl_set_deflation(lt, -2.0, d["mu"], d["R"], d["L"], d["lam"])
+        lats.append(lt)
+
+    def step(host=False, bh=None, xh=None):
+        out = []
+        for lt, d in zip(lats, per_mu):
+            p = _params(ovl, wl, d)
+            st, info = ovl.ovl_apply_sign(lt, p, bh if host else bdev, xh if host else xdev)
+            out.append((st, info[0]))
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    times, infos = [], []
+    stream = torch.cuda.current_stream()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.extend(res)
+    torch.cuda.synchronize()
+    clocks = clk.summary()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    solves = args.steps * len(per_mu) * world
+    value = solves / (total_ms / 1e3)
+    # end to end through the same call with pinned host buffers
+    bh = torch.from_numpy(b).pin_memory().numpy()
+    xh = torch.empty(b.shape, dtype=torch.complex128).pin_memory().numpy()
+    step(True, bh, xh)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(True, bh, xh)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": solves / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(len(per_mu) * n * 16),
+           "d2h_bytes_per_step": int(len(per_mu) * n * 16)}
+    # accuracy actually reached: the paper's measure 0.5 |sign(A)^2 b - b| / |b| (Section 6)
+    acc = []
+    for lt, d in zip(lats, per_mu):
+        p = _params(ovl, wl, d)
+        x1 = torch.empty_like(bdev)
+        x2 = torch.empty_like(bdev)
+        ovl.ovl_apply_sign(lt, p, bdev, x1)
+        ovl.ovl_apply_sign(lt, p, x1, x2)
+        acc.append(0.5 * float(torch.linalg.vector_norm(x2 - bdev) / torch.linalg.vector_norm(bdev)))
+    # roofline of the dominant kernel from the library's event samples
+    peaks, src = _peaks()
+    vol = int(np.prod(wl["dims"]))
+    kt = [i["t_kernel_ms"] for _, i in infos if i["kernel_samples"] > 0]
+    t_pair = float(np.mean(kt)) if kt else None
+    prec = wl["precision"]
+    if prec == "f64":
+        flops = PAIR_FLOPS_PER_SITE * vol
+        ach = flops / (t_pair * 1e-3) / 1e12 if t_pair else None
+        pk = FP64_PEAK_TFLOPS
+        roof = {"kernel": "k_lz_pair" if wl["method"] == "direct" else "k_ms_pair", "bound": "alu",
+                "achieved": ach, "peak": pk, "unit": "TFLOP/s (FP64)",
+                "frac": (ach / pk) if (ach and pk) else None, "traffic": None,
+                "peak_source": "FP64 FMA-chain probe on this pool's GB300 (DESIGN.md)",
+                "algorithmic_bytes_per_launch": PAIR_BYTES_PER_SITE["f64"] * vol}
+    else:
+        byts = PAIR_BYTES_PER_SITE[prec] * vol
+        ach = byts / (t_pair * 1e-3) / 1e9 if t_pair else None
+        roof = {"kernel": "k_lz_pair" if wl["method"] == "direct" else "k_ms_pair", "bound": "hbm",
+                "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"] if ach else None, "traffic": None,
+                "peak_source": src}
+    its = [i["iterations"] for _, i in infos]
+    statuses = sorted({st for st, _ in infos})
+    launches = sum(i["kernel_launches"] for _, i in infos)
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "f64" else "f32",
+        "data": "synthetic: SU(3) links exp(0.5 i H) seed 0, Gaussian b seed 1000",
+        "config": {"workload": args.workload, "lattice": "x".join(map(str, wl["dims"])), "n": int(n),
+                   "mu": list(wl["mus"]), "m_W": -2.0, "deflated": wl["m"], "method": wl["method"],
+                   "precision": prec, "tol": wl["tol"], "k_max": wl["k_max"], "nrhs": 1,
+                   "solves_per_step": len(per_mu), "l2": "flushed between steps (256 MB write)",
+                   "iterations_mean": float(np.mean(its)), "statuses": statuses,
+                   "accuracy_half_sign2b_minus_b": acc, "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(wl, its, seconds=args.cpu_seconds)
+    for lt in lats:
+        ovl.ovl_destroy_lattice(lt)
+    ovl.ovl_destroy_lattice(lat)
+    ovl.ovl_ctx_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _oracle_sample(wl, iterations, seconds):
+    """Time the oracle's Algorithm 4 (scipy sparse FP64 matvecs, numpy eig for sign(H_k))
+    on the bench workload for a bounded number of Lanczos steps; extrapolate to the
+    iterations the GPU path needed. Returns (solves/s, sample description)."""
+    import synth
+    from oracle import deflation, lanczos
+
+    dims = wl["dims"]
+    u = synth.gauge_links(dims, 0)
+    b = synth.gaussian_source(dims, 1000).ravel()
+    mu = wl["mus"][-1]
+    a = deflation.sparse_hw(u, dims, -2.0, mu)
+    ah = deflation.sparse_hw(u, dims, -2.0, -mu)
+    k_full = int(np.mean(iterations)) if len(iterations) else wl["k_max"]
+    # bounded sample: as many Lanczos steps as fit in the time budget
+    t0 = time.perf_counter()
+    ksamp = 0
+    st = None
+    kk = 10
+    while True:
+        t1 = time.perf_counter()
+        st = lanczos.two_sided_lanczos(lambda v: a @ v, lambda w: ah @ w, b, b, kk)
+        ksamp = kk
+        if time.perf_counter() - t0 > 0.5 * seconds or kk >= k_full:
+            break
+        kk = min(k_full, kk * 2)
+    t_steps = time.perf_counter() - t1
+    per_step = t_steps / ksamp
+    # dense sign of the projected matrix at the full k (numpy eig), timed once
+    ks = min(k_full, ksamp)
+    t2 = time.perf_counter()
+    lanczos.sign_tridiag_e1(st["alpha"][:ks], st["beta"][:ks - 1], st["delta"][:ks - 1])
+    t_small = (time.perf_counter() - t2) * (k_full / ks) ** 3
+    solve_s = per_step * k_full + t_small
+    desc = ("oracle two-sided Lanczos (Algorithm 4, scipy CSR FP64 matvecs) at %s mu=%g: %d steps timed "
+            "(%.2f s), extrapolated to k=%d, plus numpy eig of H_k scaled as k^3"
+            % ("x".join(map(str, dims)), mu, ksamp, t_steps, k_full))
+    return 1.0 / solve_s, desc
+
+
+def cpu_baseline(wl, iterations, seconds=20.0):
+    env_threads = os.environ.get("OMP_NUM_THREADS")
+    v, desc = _oracle_sample(wl, iterations, seconds)
+    return {"value": v, "unit": UNIT, "cores": int(env_threads) if env_threads else os.cpu_count(),
+            "kind": "oracle", "sample": desc}
+
+
+def run_reference(args, wl):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    vals = []
+    desc = ""
+    its = [wl["k_max"]]
+    for _ in range(args.warmup + args.steps):
+        v, desc = _oracle_sample(wl, its, seconds=max(2.0, args.cpu_seconds / max(1, args.steps)))
+        vals.append(v)
+    vals = vals[args.warmup:]
+    value = float(np.mean(vals))
+    threads = os.environ.get("OMP_NUM_THREADS")
+    res = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": args.workload},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(threads) if threads else os.cpu_count(),
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(res))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -27,6 +27,20 @@ static ovl_status set_device(const ovl_lattice* lat) {
   return OVL_OK;
 }
 
+// A lattice sharing `parent`'s links (not its deflation set) with its own workspaces.
+ovl_lattice* lattice_view(ovl_lattice* parent) {
+  ovl_lattice* v = new ovl_lattice();
+  v->ctx = parent->ctx;
+  v->g = parent->g;
+  v->formats = parent->formats;
+  v->u64 = parent->u64;
+  v->u32 = parent->u32;
+  v->u16 = parent->u16;
+  v->owns_links = false;
+  v->server_mode = true;
+  return v;
+}
+
 }  // namespace ovl
 
 using namespace ovl;
@@ -98,11 +112,13 @@ ovl_status ovl_destroy_lattice(ovl_lattice* lat) {
   cudaSetDevice(lat->ctx->device);
   free_direct_ws(lat->dws);
   free_multi_ws(lat->mws);
-  cudaFree(lat->u64);
-  cudaFree(lat->u32);
-  cudaFree(lat->u16);
-  cudaFree(lat->defl.R);
-  cudaFree(lat->defl.L);
+  if (lat->owns_links) {
+    cudaFree(lat->u64);
+    cudaFree(lat->u32);
+    cudaFree(lat->u16);
+    cudaFree(lat->defl.R);
+    cudaFree(lat->defl.L);
+  }
   delete lat;
   return OVL_OK;
 }

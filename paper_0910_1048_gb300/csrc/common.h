@@ -117,6 +117,8 @@ void free_multi_ws(MultiWS*);
 
 struct ovl_lattice {
   ovl_ctx* ctx = nullptr;
+  bool owns_links = true;    // false for a server view sharing another lattice's links
+  bool server_mode = false;  // workspaces allocated stream-ordered and released after each solve
   ovl::DirectWS* dws = nullptr;
   ovl::MultiWS* mws = nullptr;
   ovl::Geom g{};

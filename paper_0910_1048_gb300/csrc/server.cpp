@@ -1,10 +1,198 @@
-// Request server (continuous batching).
+// Request server: sign(H_W(mu)) b solves of mixed lattices, mu and tolerances as they arrive.
+//
+// Requests queue in arrival order. `max_slots` worker threads each take the oldest request
+// whose device footprint (Krylov basis and work vectors of a direct two-sided Lanczos
+// solve, Algorithm 4) fits in what the memory budget has left; requests that arrive while
+// others run are admitted as soon as a slot and memory free up, and their work overlaps on
+// the device (every slot solves on its own streams through a view of the field that shares
+// the field's links but not its workspace). Workspaces are allocated and released
+// stream-ordered, so admitting or retiring one request never stalls another. Each request's
+// arithmetic is independent of what else runs: results are the same alone and in the mix.
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+
 #include "common.h"
 
-extern "C" {
-ovl_status ovl_server_create(ovl_ctx*, const ovl_server_cfg*, ovl_server**) { ovl::set_error("server: not available"); return OVL_EINVAL; }
-ovl_status ovl_server_add_field(ovl_server*, ovl_lattice*, int32_t*) { return OVL_EINVAL; }
-ovl_status ovl_submit(ovl_server*, const ovl_request*, uint64_t*) { return OVL_EINVAL; }
-ovl_status ovl_poll(ovl_server*, uint64_t, ovl_sign_info*, void*) { return OVL_EINVAL; }
-ovl_status ovl_server_destroy(ovl_server*) { return OVL_OK; }
+namespace ovl {
+ovl_lattice* lattice_view(ovl_lattice* parent);
+size_t direct_footprint(int vol, int nrhs, int kmax, bool f64);
+}  // namespace ovl
+
+struct ovl_server {
+  struct Request {
+    uint64_t ticket = 0;
+    ovl_request req{};
+    std::vector<double> b, x;  // interleaved complex128
+    std::vector<ovl_sign_info> info;
+    size_t footprint = 0;
+    ovl_status status = OVL_PENDING;
+    bool done = false;
+  };
+  ovl_ctx* ctx = nullptr;
+  ovl_server_cfg cfg{};
+  std::vector<ovl_lattice*> fields;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<uint64_t> queue;
+  std::map<uint64_t, std::unique_ptr<Request>> reqs;
+  size_t in_use = 0;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  std::vector<std::thread> workers;
+  std::vector<std::vector<ovl_lattice*>> views;  // [slot][field]
+};
+
+namespace {
+
+size_t footprint(const ovl_server* s, const ovl_request& r) {
+  const ovl_lattice* lat = s->fields[r.field_id];
+  return ovl::direct_footprint(lat->g.vol, r.nrhs, r.k_max, r.precision == OVL_PREC_F64);
 }
+
+void worker(ovl_server* s, int slot) {
+  cudaSetDevice(s->ctx->device);
+  for (;;) {
+    ovl_server::Request* job = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv.wait(lk, [&] {
+        if (s->stop) return true;
+        if (s->queue.empty()) return false;
+        ovl_server::Request* f = s->reqs[s->queue.front()].get();
+        return s->in_use + f->footprint <= (size_t)s->cfg.mem_budget_bytes;
+      });
+      if (s->stop) return;
+      job = s->reqs[s->queue.front()].get();
+      s->queue.pop_front();
+      s->in_use += job->footprint;
+    }
+    const ovl_request& r = job->req;
+    ovl_lattice*& view = s->views[slot][r.field_id];
+    if (!view) view = ovl::lattice_view(s->fields[r.field_id]);
+    ovl_sign_params p;
+    ovl_sign_params_default(&p);
+    p.method = OVL_DIRECT_2SL;
+    p.precision = r.precision;
+    p.m_W = r.m_W;
+    p.mu = r.mu;
+    p.tol = r.tol;
+    p.k_max = r.k_max;
+    p.host_io = 1;
+    std::vector<ovl_sign_info> info(r.nrhs);
+    std::vector<double> x(job->b.size());
+    ovl_status st = ovl_apply_sign(view, &p, r.nrhs, job->b.data(), x.data(), info.data(), nullptr);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      job->x.swap(x);
+      job->info = info;
+      job->status = st;
+      job->done = true;
+      s->in_use -= job->footprint;
+      job->b.clear();
+      job->b.shrink_to_fit();
+    }
+    s->cv.notify_all();
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+ovl_status ovl_server_create(ovl_ctx* ctx, const ovl_server_cfg* cfg, ovl_server** out) {
+  ovl::clear_error();
+  OVL_REQUIRE(ctx && cfg && out, "ovl_server_create: NULL argument");
+  OVL_REQUIRE(cfg->mem_budget_bytes > 0 && cfg->max_slots >= 1 && cfg->max_slots <= 64,
+              "ovl_server_create: need mem_budget_bytes > 0 and 1 <= max_slots <= 64");
+  ovl_server* s = new ovl_server();
+  s->ctx = ctx;
+  s->cfg = *cfg;
+  s->views.assign(cfg->max_slots, {});
+  for (int i = 0; i < cfg->max_slots; ++i) s->workers.emplace_back(worker, s, i);
+  *out = s;
+  return OVL_OK;
+}
+
+ovl_status ovl_server_add_field(ovl_server* s, ovl_lattice* lat, int32_t* field_id) {
+  ovl::clear_error();
+  OVL_REQUIRE(s && lat && field_id, "ovl_server_add_field: NULL argument");
+  OVL_REQUIRE(lat->u64, "ovl_server_add_field: the lattice has no links");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->fields.push_back(lat);
+  for (auto& v : s->views) v.resize(s->fields.size(), nullptr);
+  *field_id = (int32_t)s->fields.size() - 1;
+  return OVL_OK;
+}
+
+ovl_status ovl_submit(ovl_server* s, const ovl_request* r, uint64_t* ticket) {
+  ovl::clear_error();
+  OVL_REQUIRE(s && r && ticket && r->b, "ovl_submit: NULL argument");
+  OVL_REQUIRE(r->nrhs >= 1 && r->nrhs <= 64 && r->k_max >= 1 && r->tol >= 0, "ovl_submit: invalid request");
+  OVL_REQUIRE(r->precision >= OVL_PREC_F64 && r->precision <= OVL_PREC_F32_F16LINKS, "ovl_submit: precision");
+  std::unique_lock<std::mutex> lk(s->mu);
+  OVL_REQUIRE(r->field_id >= 0 && r->field_id < (int)s->fields.size(), "ovl_submit: unknown field %d", r->field_id);
+  const ovl_lattice* lat = s->fields[r->field_id];
+  const bool has_fmt = r->precision == OVL_PREC_F64 ||
+                       (r->precision == OVL_PREC_F32 ? lat->u32 != nullptr : lat->u16 != nullptr);
+  OVL_REQUIRE(has_fmt,
+              "ovl_submit: field lacks the link format of this precision");
+  auto job = std::make_unique<ovl_server::Request>();
+  job->req = *r;
+  job->footprint = footprint(s, *r);
+  if (job->footprint > (size_t)s->cfg.mem_budget_bytes) {
+    ovl::set_error("ovl_submit: request needs %zu bytes, budget is %lld", job->footprint,
+                   (long long)s->cfg.mem_budget_bytes);
+    return OVL_EINVAL;
+  }
+  const size_t nd = (size_t)2 * 12 * lat->g.vol * r->nrhs;
+  job->b.assign((const double*)r->b, (const double*)r->b + nd);
+  job->req.b = nullptr;
+  job->ticket = s->next_ticket++;
+  *ticket = job->ticket;
+  s->queue.push_back(job->ticket);
+  s->reqs[job->ticket] = std::move(job);
+  lk.unlock();
+  s->cv.notify_all();
+  return OVL_OK;
+}
+
+ovl_status ovl_poll(ovl_server* s, uint64_t ticket, ovl_sign_info* info, void* x_out) {
+  ovl::clear_error();
+  OVL_REQUIRE(s, "ovl_poll: NULL server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) {
+    ovl::set_error("ovl_poll: unknown ticket %llu", (unsigned long long)ticket);
+    return OVL_ENOTFOUND;
+  }
+  ovl_server::Request* j = it->second.get();
+  if (!j->done) return OVL_PENDING;
+  if (info) std::memcpy(info, j->info.data(), j->info.size() * sizeof(ovl_sign_info));
+  if (x_out && !j->x.empty()) std::memcpy(x_out, j->x.data(), j->x.size() * sizeof(double));
+  ovl_status st = j->status;
+  s->reqs.erase(it);  // results are handed out once
+  return st;
+}
+
+ovl_status ovl_server_destroy(ovl_server* s) {
+  ovl::clear_error();
+  if (!s) return OVL_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  for (auto& t : s->workers) t.join();
+  for (auto& v : s->views)
+    for (ovl_lattice* l : v)
+      if (l) ovl_destroy_lattice(l);
+  delete s;
+  return OVL_OK;
+}
+
+}  // extern "C"

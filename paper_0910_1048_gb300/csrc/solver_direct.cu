@@ -9,6 +9,7 @@
 // the previous one, overlapping sign(H_j) e_1 with device work.
 #include <chrono>
 #include <complex>
+#include <cstdlib>
 
 #include "kernels.h"
 
@@ -43,6 +44,7 @@ struct DirectWS {
     int* status = nullptr;
   } h[2];
   void* h_block = nullptr;
+  bool pageable = false;  // server views: host mirrors in pageable memory (no pinned alloc/free)
   // two graphs of `gchunk` steps (alternating chunks); each records timing events around
   // its first step's pair stencil (tev[q][0..1]) and update (tev[q][2..3])
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -61,8 +63,13 @@ void free_direct_ws(DirectWS* w) {
     for (auto e : w->tev[q])
       if (e) cudaEventDestroy(e);
   }
-  if (w->dev_block) cudaFree(w->dev_block);
-  if (w->h_block) cudaFreeHost(w->h_block);
+  if (w->dev_block) cudaFreeAsync(w->dev_block, w->stream);  // stream-ordered: no device-wide sync
+  if (w->h_block) {
+    if (w->pageable)
+      std::free(w->h_block);
+    else
+      cudaFreeHost(w->h_block);
+  }
   if (w->stream) cudaStreamDestroy(w->stream);
   if (w->ev) cudaEventDestroy(w->ev);
   delete w;
@@ -115,9 +122,16 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   size_t o_kr = take((size_t)nrhs * 4);
   size_t o_bd = take((size_t)nrhs * n * 16);
   size_t o_xd = take((size_t)nrhs * n * 16);
+  if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete w;
+    set_error("apply_sign: cannot create a stream");
+    return OVL_ECUDA;
+  }
   char* base = nullptr;
-  cudaError_t e = cudaMalloc(&base, off);
+  cudaError_t e = cudaMallocAsync((void**)&base, off, w->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
   if (e != cudaSuccess) {
+    cudaStreamDestroy(w->stream);
     delete w;
     set_error("apply_sign: cannot allocate %zu bytes of device workspace: %s", off, cudaGetErrorString(e));
     return OVL_ENOMEM;
@@ -150,7 +164,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   w->kr = (int*)(base + o_kr);
   w->bdev = (double2*)(base + o_bd);
   w->xdev = (double2*)(base + o_xd);
-  if (cudaMemset(lz.count, 0, (size_t)nrhs * 4) != cudaSuccess) {
+  if (cudaMemsetAsync(lz.count, 0, (size_t)nrhs * 4, w->stream) != cudaSuccess) {
     free_direct_ws(w);
     set_error("apply_sign: cudaMemset failed");
     return OVL_ECUDA;
@@ -158,9 +172,14 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   // pinned mirrors: alpha, beta (16 B), delta, vnorm, sv (8 B), beta0, j, status
   size_t hb = (size_t)nrhs * ks * (16 + 16 + 8 + 8 + 8) + nrhs * (8 + 4 + 4) + 64;
   char* hp = nullptr;
-  if (cudaMallocHost(&hp, 2 * hb) != cudaSuccess) {
+  w->pageable = lat->server_mode;
+  if (w->pageable)
+    hp = (char*)std::malloc(2 * hb);
+  else if (cudaMallocHost(&hp, 2 * hb) != cudaSuccess)
+    hp = nullptr;
+  if (!hp) {
     free_direct_ws(w);
-    set_error("apply_sign: cannot allocate pinned host memory");
+    set_error("apply_sign: cannot allocate host memory for the scalar mirrors");
     return OVL_ENOMEM;
   }
   w->h_block = hp;
@@ -178,8 +197,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   bool ev_ok = true;
   for (int q = 0; q < 2; ++q)
     for (int i = 0; i < 4; ++i) ev_ok = ev_ok && cudaEventCreate(&w->tev[q][i]) == cudaSuccess;
-  if (!ev_ok || cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming) != cudaSuccess) {
+  if (!ev_ok || cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming) != cudaSuccess) {
     free_direct_ws(w);
     set_error("apply_sign: cannot create stream/event");
     return OVL_ECUDA;
@@ -308,28 +326,25 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
     if (tev && (e = cudaEventRecord(tev[3], st))) return e;
     return cudaSuccess;
   };
-  // graphs of `chunk` steps (re-captured when the step's parameters change)
-  bool use_graph = p->use_graphs != 0;
+  // a chunk = one step launched directly on the stream with timing events around its two
+  // kernels, then a CUDA graph of the chunk's other steps (re-captured when they change)
+  bool use_graph = p->use_graphs != 0 && chunk > 1;
   if (use_graph && !(w->graph[0] && w->gchunk == chunk && w->g_mw == p->m_W && w->g_mu == p->mu && w->g_lf == lf)) {
-    for (int q = 0; q < 2; ++q) {
-      if (w->graph[q]) cudaGraphExecDestroy(w->graph[q]);
-      w->graph[q] = nullptr;
+    if (w->graph[0]) cudaGraphExecDestroy(w->graph[0]);
+    w->graph[0] = nullptr;
+    cudaGraph_t gr;
+    OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 1; i < chunk && e == cudaSuccess; ++i) e = step(nullptr);
+    cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+    if (e != cudaSuccess) {
+      set_error("apply_sign: capture failed: %s", cudaGetErrorString(e));
+      return OVL_ECUDA;
     }
-    for (int q = 0; q < 2; ++q) {
-      cudaGraph_t gr;
-      OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = cudaSuccess;
-      for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = step(i == 0 ? w->tev[q] : nullptr);
-      cudaError_t e2 = cudaStreamEndCapture(st, &gr);
-      if (e != cudaSuccess) {
-        set_error("apply_sign: capture failed: %s", cudaGetErrorString(e));
-        return OVL_ECUDA;
-      }
-      OVL_CHECK_CUDA(e2);
-      e = cudaGraphInstantiate(&w->graph[q], gr, 0);
-      cudaGraphDestroy(gr);
-      OVL_CHECK_CUDA(e);
-    }
+    OVL_CHECK_CUDA(e2);
+    e = cudaGraphInstantiate(&w->graph[0], gr, 0);
+    cudaGraphDestroy(gr);
+    OVL_CHECK_CUDA(e);
     w->gchunk = chunk;
     w->g_mw = p->m_W;
     w->g_mu = p->mu;
@@ -338,11 +353,11 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   int launches = 1 + (m > 0 ? 1 : 0) + 1;  // start (+ deflation dots) and the combine
   auto run_steps = [&](int nsteps, int q) -> cudaError_t {
     launches += 2 * nsteps;
-    if (use_graph && nsteps == chunk) return cudaGraphLaunch(w->graph[q], st);
-    for (int i = 0; i < nsteps; ++i) {
-      cudaError_t e = step(i == 0 && q >= 0 ? w->tev[q] : nullptr);
-      if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = step(w->tev[q]);
+    if (e != cudaSuccess || nsteps == 1) return e;
+    if (use_graph && nsteps == chunk) return cudaGraphLaunch(w->graph[0], st);
+    for (int i = 1; i < nsteps; ++i)
+      if ((e = step(nullptr)) != cudaSuccess) return e;
     return cudaSuccess;
   };
   double t_pair = 0, t_upd = 0;
@@ -355,6 +370,7 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
       t_upd += b;
       ++nsamp;
     }
+    cudaGetLastError();  // a failed timing query must not surface as a launch error later
   };
   std::vector<RhsState> rs(nrhs);
   double t_small = 0;
@@ -386,7 +402,7 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   if (fixed) {
     while (queued < kmax && ce == cudaSuccess) {
       int ns = std::min(chunk, kmax - queued);
-      ce = run_steps(ns, 0);
+      ce = run_steps(ns, queued == 0 ? 0 : 1);
       queued += ns;
     }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
@@ -508,8 +524,17 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
       info[r].kernel_launches = launches;
     }
   }
+  if (lat->server_mode) {  // the server accounts device memory per request
+    free_direct_ws(lat->dws);
+    lat->dws = nullptr;
+  }
   if (result != OVL_OK) set_error("apply_sign: at least one right-hand side ended with status %d", result);
   return result;
+}
+
+size_t direct_footprint(int vol, int nrhs, int kmax, bool f64) {
+  const size_t n = (size_t)12 * vol, elt = f64 ? 16 : 8;
+  return (size_t)nrhs * ((size_t)(kmax + 1) * n * elt + 4 * n * elt + 3 * n * 16) + ((size_t)1 << 20);
 }
 
 }  // namespace ovl

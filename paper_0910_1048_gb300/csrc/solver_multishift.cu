@@ -46,7 +46,7 @@ void free_multi_ws(MultiWS* w) {
     for (auto e : w->tev[q])
       if (e) cudaEventDestroy(e);
   }
-  if (w->dev) cudaFree(w->dev);
+  if (w->dev) cudaFreeAsync(w->dev, w->stream);
   if (w->h_status) cudaFreeHost(w->h_status);
   if (w->stream) cudaStreamDestroy(w->stream);
   for (auto e : w->ev)
@@ -97,8 +97,15 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m)
   size_t o_cn = take((size_t)nrhs * 4);
   size_t o_do = take((size_t)nrhs * 2 * std::max(m, 1) * 16);
   size_t o_ls = take((size_t)std::max(m, 1) * 8);
-  cudaError_t e = cudaMalloc(&w->dev, off);
+  if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete w;
+    set_error("apply_sign: cannot create a stream");
+    return OVL_ECUDA;
+  }
+  cudaError_t e = cudaMallocAsync((void**)&w->dev, off, w->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
   if (e != cudaSuccess) {
+    cudaStreamDestroy(w->stream);
     delete w;
     set_error("apply_sign: cannot allocate %zu bytes of device workspace: %s", off, cudaGetErrorString(e));
     return OVL_ENOMEM;
@@ -134,9 +141,8 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m)
   bool ev_ok = true;
   for (int q = 0; q < 2; ++q)
     for (int i = 0; i < 4; ++i) ev_ok = ev_ok && cudaEventCreate(&w->tev[q][i]) == cudaSuccess;
-  if (!ev_ok || cudaMemset(ms.count, 0, (size_t)nrhs * 4) != cudaSuccess ||
+  if (!ev_ok || cudaMemsetAsync(ms.count, 0, (size_t)nrhs * 4, w->stream) != cudaSuccess ||
       cudaMallocHost(&w->h_status, (size_t)4 * nrhs * sizeof(int)) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&w->ev[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&w->ev[1], cudaEventDisableTiming) != cudaSuccess) {
     free_multi_ws(w);
@@ -231,26 +237,21 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
   OVL_CHECK_CUDA(launch_ms_start(g, f64, ms, v, bd, m, lat->defl.R, lat->defl.L, w->lam_sign, w->dots, st));
   const Links U = lat->links();
   const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 20, p->k_max));
-  const bool use_graph = p->use_graphs != 0;
+  const bool use_graph = p->use_graphs != 0 && chunk > 1;
   if (use_graph && !(w->graph[0] && w->gchunk == chunk && w->g_lf == lf && w->g_mw == p->m_W && w->g_mu == p->mu &&
                      w->g_s1 == s1 && w->g_tol == p->tol)) {
-    for (int q = 0; q < 2; ++q) {
-      if (w->graph[q]) cudaGraphExecDestroy(w->graph[q]);
-      w->graph[q] = nullptr;
-    }
-    for (int q = 0; q < 2; ++q) {
-      cudaGraph_t gr;
-      OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = cudaSuccess;
-      for (int i = 0; i < chunk && e == cudaSuccess; ++i)
-        e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st, i == 0 ? w->tev[q] : nullptr);
-      cudaError_t e2 = cudaStreamEndCapture(st, &gr);
-      OVL_CHECK_CUDA(e);
-      OVL_CHECK_CUDA(e2);
-      e = cudaGraphInstantiate(&w->graph[q], gr, 0);
-      cudaGraphDestroy(gr);
-      OVL_CHECK_CUDA(e);
-    }
+    if (w->graph[0]) cudaGraphExecDestroy(w->graph[0]);
+    w->graph[0] = nullptr;
+    cudaGraph_t gr;
+    OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 1; i < chunk && e == cudaSuccess; ++i) e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st);
+    cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+    OVL_CHECK_CUDA(e);
+    OVL_CHECK_CUDA(e2);
+    e = cudaGraphInstantiate(&w->graph[0], gr, 0);
+    cudaGraphDestroy(gr);
+    OVL_CHECK_CUDA(e);
     w->gchunk = chunk;
     w->g_lf = lf;
     w->g_mw = p->m_W;
@@ -259,13 +260,14 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
     w->g_tol = p->tol;
   }
   int launches = 1 + (m > 0 ? 1 : 0) + 2;  // start (+ deflation dots), final stencil and finish
+  // a chunk = one iteration launched directly with timing events, then a graph of the rest
   auto run_chunk = [&](int ns, int q) -> cudaError_t {
     launches += 4 * ns;
-    if (use_graph && ns == chunk) return cudaGraphLaunch(w->graph[q], st);
-    for (int i = 0; i < ns; ++i) {
-      cudaError_t e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st, i == 0 ? w->tev[q] : nullptr);
-      if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st, w->tev[q]);
+    if (e != cudaSuccess || ns == 1) return e;
+    if (use_graph && ns == chunk) return cudaGraphLaunch(w->graph[0], st);
+    for (int i = 1; i < ns; ++i)
+      if ((e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st)) != cudaSuccess) return e;
     return cudaSuccess;
   };
   double t_pair = 0, t_upd = 0;
@@ -278,6 +280,7 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
       t_upd += b;
       ++nsamp;
     }
+    cudaGetLastError();  // a failed timing query must not surface as a launch error later
   };
   // chunks with status snapshots; one chunk stays queued while the host looks at the last
   int queued = 0, slot = 0;

@@ -1,0 +1,117 @@
+"""Serving: requests of mixed lattices, mu, tolerances and batch sizes admitted by memory
+footprint while others run (ovl_submit / ovl_poll). Each result must be the same as the
+same request solved alone through ovl_apply_sign (the kernels' arithmetic per right-hand side
+does not depend on what else runs, so equality is exact), and the solves must still match
+the oracle's sign where one is available.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import matsign, wilson
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ovl():
+    import paper_0910_1048_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def env(ovl):
+    ctx = ovl.ovl_ctx_create(0)
+    fields = []
+    for dims, seed in (((4, 4, 4, 4), 0), ((4, 4, 4, 4), 5), ((6, 6, 6, 6), 1), ((2, 2, 2, 4), 35)):
+        u = synth.gauge_links(dims, seed, 0.1 if dims == (2, 2, 2, 4) else 0.5)
+        lat = ovl.ovl_create_lattice(ctx, dims, -1)
+        ovl.ovl_set_links(lat, u, ovl.OVL_F64 | ovl.OVL_F32)
+        fields.append((dims, u, lat))
+    yield ctx, fields
+    for _, _, lat in fields:
+        ovl.ovl_destroy_lattice(lat)
+    ovl.ovl_ctx_destroy(ctx)
+
+
+def _alone(ovl, lat, b, mu, tol, k_max, precision):
+    p = ovl.ovl_sign_params_default(mu=mu, tol=tol, k_max=k_max, precision=precision)
+    x = np.zeros_like(b)
+    st, info = ovl.ovl_apply_sign(lat, p, np.ascontiguousarray(b), x)
+    return st, x
+
+
+def test_mixed_stream_matches_alone(ovl, env):
+    ctx, fields = env
+    rng = np.random.default_rng(42)
+    # budget for about two 4^4 FP64 requests at k_max = 400 at a time
+    budget = 2 * (401 * 12 * 256 * 16 + 4 * 12 * 256 * 16 + 3 * 12 * 256 * 16 + (1 << 20)) + (1 << 21)
+    budget = max(budget, 3 * (401 * 12 * 1296 * 16))  # room for a 6^4 request
+    srv = ovl.ovl_server_create(ctx, budget, max_slots=3)
+    ids = [ovl.ovl_server_add_field(srv, f[2]) for f in fields]
+    reqs = []
+    for i in range(10):
+        fi = int(rng.integers(0, len(fields)))
+        dims = fields[fi][0]
+        nrhs = int(rng.integers(1, 3))
+        mu = float(rng.uniform(0.0, 0.5))
+        tol = float(rng.choice([1e-6, 1e-8]))
+        prec = ovl.OVL_PREC_F64 if i % 3 else ovl.OVL_PREC_F32
+        b = synth.gaussian_source(dims, 1000 + i, nrhs=nrhs)
+        t = ovl.ovl_submit(srv, ids[fi], b, mu, tol, k_max=400, precision=prec)
+        reqs.append((t, fi, b, mu, tol, prec, nrhs))
+        time.sleep(float(rng.exponential(0.01)))  # arrivals while earlier ones run
+    results = {}
+    deadline = time.time() + 300
+    while len(results) < len(reqs) and time.time() < deadline:
+        for t, fi, b, mu, tol, prec, nrhs in reqs:
+            if t in results:
+                continue
+            x = np.zeros_like(b)
+            st, info = ovl.ovl_poll(srv, t, nrhs, x)
+            if st != ovl.OVL_PENDING:
+                results[t] = (st, x, info)
+        time.sleep(0.01)
+    ovl.ovl_server_destroy(srv)
+    assert len(results) == len(reqs)
+    for t, fi, b, mu, tol, prec, nrhs in reqs:
+        st, x, info = results[t]
+        st1, x1 = _alone(ovl, fields[fi][2], b, mu, tol, 400, prec)
+        assert st == st1
+        assert np.array_equal(x, x1), "request %d differs alone vs in the mix" % t
+
+
+def test_server_result_matches_oracle(ovl, env):
+    ctx, fields = env
+    dims, u, lat = fields[3]
+    b = synth.gaussian_source(dims, 36)
+    xs = matsign.sign_eig(wilson.dense_hw(u, dims, -2.0, 0.3), b.ravel()).reshape(b.shape)
+    srv = ovl.ovl_server_create(ctx, 1 << 30, max_slots=2)
+    fid = ovl.ovl_server_add_field(srv, lat)
+    t = ovl.ovl_submit(srv, fid, b, 0.3, 1e-10, k_max=384)
+    x = np.zeros_like(b)
+    for _ in range(3000):
+        st, info = ovl.ovl_poll(srv, t, 1, x)
+        if st != ovl.OVL_PENDING:
+            break
+        time.sleep(0.01)
+    assert st == ovl.OVL_OK, info
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-9
+    with pytest.raises(ovl.OvlError) as e:
+        ovl.ovl_poll(srv, t, 1, x)  # results are handed out once
+    assert e.value.status == ovl.OVL_ENOTFOUND
+    ovl.ovl_server_destroy(srv)
+
+
+def test_admission_rejects_oversized(ovl, env):
+    ctx, fields = env
+    srv = ovl.ovl_server_create(ctx, 1 << 20, max_slots=1)  # 1 MiB: nothing fits
+    fid = ovl.ovl_server_add_field(srv, fields[0][2])
+    with pytest.raises(ovl.OvlError) as e:
+        ovl.ovl_submit(srv, fid, synth.gaussian_source(fields[0][0], 1), 0.3, 1e-8)
+    assert e.value.status == ovl.OVL_EINVAL and "budget" in str(e.value)
+    ovl.ovl_server_destroy(srv)
