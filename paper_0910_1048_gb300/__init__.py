@@ -316,17 +316,35 @@ def ovl_server_add_field(srv, lat) -> int:
     return fid.value
 
 
+def _nrhs_of(b: np.ndarray, nrhs):
+    """Right-hand sides in a canonical spinor array: [Lt][Lz][Ly][Lx][4][3] is one,
+    [nrhs][Lt][Lz][Ly][Lx][4][3] is a batch; a flat array needs nrhs given."""
+    if nrhs is not None:
+        return int(nrhs)
+    if b.ndim == 7:
+        return int(b.shape[0])
+    if b.ndim == 6:
+        return 1
+    raise ValueError("pass nrhs for a spinor array of shape %r" % (b.shape,))
+
+
 def ovl_submit(srv, field_id, b: np.ndarray, mu, tol, m_W=-2.0, k_max=600, precision=OVL_PREC_F64, nrhs=None):
+    """Queue x = sign(H_W(mu)) b on a registered field; b is copied before the call returns."""
     b = np.ascontiguousarray(b, dtype=np.complex128)
-    req = ovl_request(field_id, int(nrhs if nrhs is not None else (b.shape[0] if b.ndim > 1 else 1)),
-                      mu, m_W, tol, k_max, precision, b.ctypes.data)
+    nr = _nrhs_of(b, nrhs)
+    if b.size % (12 * nr) != 0:
+        raise ValueError("b does not hold nrhs whole spinors")
+    req = ovl_request(field_id, nr, mu, m_W, tol, k_max, precision, b.ctypes.data)
     t = ctypes.c_uint64()
     _check(lib.ovl_submit(srv, ctypes.byref(req), ctypes.byref(t)))
     return t.value
 
 
 def ovl_poll(srv, ticket, nrhs, x_out: np.ndarray | None = None):
-    """Returns (status, infos); status OVL_PENDING while running."""
+    """Returns (status, infos); status OVL_PENDING while running. x_out (complex128) must hold
+    the request's nrhs spinors; it is written once, when the request is done."""
+    if x_out is not None and (x_out.dtype != np.complex128 or not x_out.flags["C_CONTIGUOUS"]):
+        raise TypeError("x_out must be a C-contiguous complex128 array")
     infos = (ovl_sign_info * max(nrhs, 1))()
     st = lib.ovl_poll(srv, ticket, infos, _ptr(x_out) if x_out is not None else None)
     if st in (OVL_EINVAL, OVL_ENOTFOUND, OVL_ECUDA, OVL_ENOMEM):

@@ -102,3 +102,14 @@ def test_rational_rejects_bad_interval(ovl):
         ovl.ovl_rational_coeffs(ovl.OVL_RAT_NEUBERGER, 0, 1.0, 0.5, 1e-8)
     assert e.value.status == ovl.OVL_EINVAL
     assert "lo" in str(e.value)
+
+
+def test_submit_nrhs_inference(ovl):
+    """A single canonical spinor is one right-hand side; a 7-D array is a batch."""
+    one = np.zeros((4, 2, 2, 2, 4, 3), np.complex128)
+    many = np.zeros((3, 4, 2, 2, 2, 4, 3), np.complex128)
+    assert ovl._nrhs_of(one, None) == 1
+    assert ovl._nrhs_of(many, None) == 3
+    assert ovl._nrhs_of(one.ravel(), 1) == 1
+    with pytest.raises(ValueError):
+        ovl._nrhs_of(one.ravel(), None)
