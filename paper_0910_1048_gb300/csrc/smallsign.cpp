@@ -27,6 +27,7 @@
 // and the result is accepted when the involution residual |g(cH) y - e_1| is small.
 #include <algorithm>
 #include <complex>
+#include <thread>
 #include <vector>
 
 #include "common.h"
@@ -377,11 +378,17 @@ void rational_apply(int k, const cz* al, const cz* be, const cz* de, double c, i
     }
   }
   const double c2 = c * c;
-  std::vector<cz> acc(k, 0.0);
+  // the s shifted solves are independent: split them over host threads, each summing its
+  // own shifts in order, then add the per-thread sums in thread order (deterministic)
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nth = std::max(1, std::min({hw, 16, s, (int)((size_t)s * k / 20000 + 1)}));
+  std::vector<std::vector<cz>> part(nth, std::vector<cz>(k, 0.0));
+  auto work = [&](int tid) {
+  std::vector<cz>& acc = part[tid];
   // band storage for LU with partial pivoting: row i holds columns i-2..i+4 (7 entries)
   const int W = 7, OFF = 2;
   std::vector<cz> a((size_t)k * W), rhs(k);
-  for (int sh = 1; sh <= s; ++sh) {
+  for (int sh = 1 + tid; sh <= s; sh += nth) {
     const double th = 3.14159265358979323846 / (2.0 * s) * (sh - 0.5);
     const double om = 1.0 / (s * std::cos(th) * std::cos(th));
     const double sg = -std::tan(th) * std::tan(th);
@@ -423,6 +430,18 @@ void rational_apply(int k, const cz* al, const cz* be, const cz* de, double c, i
     }
     for (int i = 0; i < k; ++i) acc[i] += om * rhs[i];
   }
+  };
+  if (nth == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> th;
+    for (int t = 1; t < nth; ++t) th.emplace_back(work, t);
+    work(0);
+    for (auto& t : th) t.join();
+  }
+  std::vector<cz> acc(k, 0.0);
+  for (int t = 0; t < nth; ++t)
+    for (int i = 0; i < k; ++i) acc[i] += part[t][i];
   for (int i = 0; i < k; ++i) {
     cz t = al[i] * acc[i];
     if (i > 0) t += de[i - 1] * acc[i - 1];

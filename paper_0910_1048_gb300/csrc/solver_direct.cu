@@ -399,6 +399,7 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   cudaError_t ce = cudaSuccess;
   int qlast = 0;
   bool any_running = true;  // a chunk launched while some rhs ran did real work
+  int next_eval = 0;        // next step count at which sign(H_j) e_1 is evaluated
   if (fixed) {
     while (queued < kmax && ce == cudaSuccess) {
       int ns = std::min(chunk, kmax - queued);
@@ -430,6 +431,20 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
       if (any_running) sample(q);
       qlast = q;
       const bool final_snapshot = evq[q] >= kmax;
+      // geometric schedule: evaluate sign(H_j) e_1 when j passed the last evaluation by 10%
+      // (the host cost grows with j while the estimate changes slowly)
+      if (!final_snapshot && evq[q] < next_eval) {
+        any_running = false;
+        for (int r = 0; r < nrhs; ++r) any_running = any_running || w->h[q].status[r] == 0;
+        if (!any_running) {
+          bool all = true;  // every rhs retired or broke down on the device: evaluate now
+          for (int r = 0; r < nrhs; ++r) all = all && (rs[r].done || w->h[q].status[r] != 0);
+          if (!all) continue;
+        } else {
+          continue;
+        }
+      }
+      next_eval = std::max(evq[q] + chunk, (int)(1.1 * evq[q]));
       bool all_done = true;
       for (int r = 0; r < nrhs; ++r) {
         RhsState& s = rs[r];
