@@ -105,4 +105,59 @@ __device__ __forceinline__ void store_spin(typename V2<R>::T* p, int vol, int s,
 }
 
 
+// ------------------------------------------------------------------ split-site pair stencil
+// For small lattices (too few sites to fill 152 SMs with one thread per site) every site is
+// shared by 8 threads: threadIdx.y = which * 4 + dir, `which` selecting input 0 (coefficients
+// c0) or input 1 (c1), `dir` one direction's forward and backward hops. Directions 1..3 leave
+// their partial spinors in shared memory; the dir-0 thread of each (site, which) adds them to
+// its own hops and the diagonal term and hands the full D_W(+-mu) psi to `emit`.
+constexpr int kSplitSites = 32;
+
+template <class R>
+struct SplitSmem {
+  cplx<R> part[2][3][12][kSplitSites];
+};
+
+template <class R, int LF, class Emit>
+__device__ __forceinline__ void pair_split(const Geom& g, const Links& U, const HopCoef<R>& c0, const HopCoef<R>& c1,
+                                           const typename V2<R>::T* in0, const typename V2<R>::T* in1,
+                                           SplitSmem<R>& sm, Emit emit) {
+  const int tx = threadIdx.x, which = threadIdx.y >> 2, dir = threadIdx.y & 3;
+  const int s = blockIdx.x * kSplitSites + tx;
+  const typename V2<R>::T* in = which ? in1 : in0;
+  const HopCoef<R>& c = which ? c1 : c0;
+  Loader<R, true> ld{in, g.vol, false};
+  Spin<R> acc;
+  if (s < g.vol) {
+    Nbr n;
+    neighbours(g, s, n);
+    if (dir == 0) {
+      ld(s, acc);  // diagonal term
+      hop_dir<0, LF>(g, U, s, n, c.ks, c.ks, ld, acc);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 12; ++q) acc.c[q / 3][q % 3] = mk<R>(0, 0);
+      if (dir == 1) {
+        hop_dir<1, LF>(g, U, s, n, c.ks, c.ks, ld, acc);
+      } else if (dir == 2) {
+        hop_dir<2, LF>(g, U, s, n, c.ks, c.ks, ld, acc);
+      } else {
+        R ktf = (n.t == g.lt - 1) ? (R)g.t_bc * c.ktf : c.ktf;
+        R ktb = (n.t == 0) ? (R)g.t_bc * c.ktb : c.ktb;
+        hop_dir<3, LF>(g, U, s, n, ktf, ktb, ld, acc);
+      }
+#pragma unroll
+      for (int q = 0; q < 12; ++q) sm.part[which][dir - 1][q][tx] = acc.c[q / 3][q % 3];
+    }
+  }
+  __syncthreads();
+  if (dir == 0 && s < g.vol) {
+#pragma unroll
+    for (int q = 0; q < 12; ++q)
+      acc.c[q / 3][q % 3] = acc.c[q / 3][q % 3] + sm.part[which][0][q][tx] + sm.part[which][1][q][tx] +
+                            sm.part[which][2][q][tx];
+    emit(which, s, acc);
+  }
+}
+
 }  // namespace ovl

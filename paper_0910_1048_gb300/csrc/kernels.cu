@@ -320,12 +320,66 @@ __global__ void __launch_bounds__(2 * kPairSites) k_lz_pair(Geom g, Links U, Hop
   }
 }
 
+// The same step with 8 threads per site (small lattices): see pair_split.
+template <class R, int LF>
+__global__ void __launch_bounds__(8 * kSplitSites) k_lz_pair_split(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm,
+                                                                   LzDev lz, const typename V2<R>::T* vh,
+                                                                   const typename V2<R>::T* wh,
+                                                                   typename V2<R>::T* av, typename V2<R>::T* aw) {
+  using T = typename V2<R>::T;
+  __shared__ SplitSmem<R> sm;
+  const int rhs = blockIdx.y;
+  if (lz.status[rhs]) return;
+  const int j = lz.j[rhs];
+  const size_t n = (size_t)12 * g.vol;
+  const size_t o = (size_t)rhs * (lz.kmax + 2);
+  const double2 swd = lz.sw[o + j];
+  const T* vj = vh + ((size_t)rhs * (lz.kmax + 1) + (j - 1)) * n;
+  const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
+  const R sv = (R)lz.sv[o + j];
+  const cplx<R> sw = mk<R>((R)swd.x, (R)swd.y);
+  double acc[2] = {0, 0};
+  pair_split<R, LF>(g, U, cp, cm, vj, wj, sm, [&](int which, int s, Spin<R>& out) {
+    if (which == 0) {
+      cplx<R> a = mk<R>(0, 0);
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        cplx<R> x = sv * out.c[c / 3][c % 3];
+        if (c >= 6) x = -x;  // gamma5
+        stc<R>(av + (size_t)rhs * n, (size_t)c * g.vol + s, x);
+        a = a + cdot(ldc<R>(wj, (size_t)c * g.vol + s), x);
+      }
+      acc[0] = (double)a.re;
+      acc[1] = (double)a.im;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        cplx<R> y = sw * out.c[c / 3][c % 3];
+        if (c >= 6) y = -y;
+        stc<R>(aw + (size_t)rhs * n, (size_t)c * g.vol + s, y);
+      }
+    }
+  });
+  block_sum<2>(acc);
+  double* part = lz.part + (size_t)rhs * lz.nblk * 4;
+  double pv[4] = {acc[0], acc[1], 0, 0};
+  if (publish_partials<4>(pv, part, lz.count + rhs)) {
+    reduce_partials<4>(part, gridDim.x, pv);
+    if (lin_tid() == 0) {
+      zd alpha = conj(mk(swd.x, swd.y)) * mk(pv[0], pv[1]);
+      lz.alpha[o + j] = make_double2(alpha.re, alpha.im);
+    }
+  }
+}
+
 // vhat_{j+1} = Av_j - alpha_j v_j - beta_{j-1} v_{j-1}
 // what_{j+1} = Aw_j - conj(alpha_j) w_j - conj(delta_{j-1}) w_{j-1}    (Eqs. 2sided1/2)
 // then delta_j = sqrt|what^H vhat|, beta_j = what^H vhat / delta_j (scaling reading).
+// One thread per vector element (component, site): 12 V threads per rhs.
 template <class R>
-__global__ void __launch_bounds__(kBlock) k_lz_update(Geom g, LzDev lz, typename V2<R>::T* vh, typename V2<R>::T* wh,
-                                                      const typename V2<R>::T* av, const typename V2<R>::T* aw) {
+__global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typename V2<R>::T* vh,
+                                                         typename V2<R>::T* wh, const typename V2<R>::T* av,
+                                                         const typename V2<R>::T* aw) {
   using T = typename V2<R>::T;
   const int rhs = blockIdx.y;
   if (lz.status[rhs]) return;
@@ -347,31 +401,22 @@ __global__ void __launch_bounds__(kBlock) k_lz_update(Geom g, LzDev lz, typename
   T* vnew = vh + ((size_t)rhs * (lz.kmax + 1) + j) * n;
   const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
   T* wnew = wh + ((size_t)((j + 1) & 1) * lz.nrhs + rhs) * n;  // holds what_{j-1} until overwritten
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   double acc[4] = {0, 0, 0, 0};
-  if (s < g.vol) {
-    R ipr = 0, ipi = 0, nv = 0, nw = 0;
-#pragma unroll
-    for (int c = 0; c < 12; ++c) {
-      size_t e = (size_t)c * g.vol + s;
-      cplx<R> x = ldc<R>(av + (size_t)rhs * n, e) - a1 * ldc<R>(vj, e);
-      cplx<R> y = ldc<R>(aw + (size_t)rhs * n, e) - b1 * ldc<R>(wj, e);
-      if (j > 1) {
-        x = x - a2 * ldc<R>(vjm, e);
-        y = y - b2 * ldc<R>(wnew, e);
-      }
-      stc<R>(vnew, e, x);
-      stc<R>(wnew, e, y);
-      cplx<R> ip = cdot(y, x);
-      ipr += ip.re;
-      ipi += ip.im;
-      nv += norm2(x);
-      nw += norm2(y);
+  if (e < n) {
+    cplx<R> x = ldc<R>(av + (size_t)rhs * n, e) - a1 * ldc<R>(vj, e);
+    cplx<R> y = ldc<R>(aw + (size_t)rhs * n, e) - b1 * ldc<R>(wj, e);
+    if (j > 1) {
+      x = x - a2 * ldc<R>(vjm, e);
+      y = y - b2 * ldc<R>(wnew, e);
     }
-    acc[0] = ipr;
-    acc[1] = ipi;
-    acc[2] = nv;
-    acc[3] = nw;
+    stc<R>(vnew, e, x);
+    stc<R>(wnew, e, y);
+    cplx<R> ip = cdot(y, x);
+    acc[0] = ip.re;
+    acc[1] = ip.im;
+    acc[2] = norm2(x);
+    acc[3] = norm2(y);
   }
   block_sum<4>(acc);
   double* part = lz.part + (size_t)rhs * lz.nblk * 4;
@@ -399,6 +444,22 @@ __global__ void __launch_bounds__(kBlock) k_lz_update(Geom g, LzDev lz, typename
 
 cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
                                 const LzDev& lz, const LzVecs& vec, cudaStream_t st) {
+  if (use_split(g)) {
+    dim3 sgrid((g.vol + kSplitSites - 1) / kSplitSites, lz.nrhs), sblock(kSplitSites, 8);
+    if (f64)
+      k_lz_pair_split<double, LINK_F64><<<sgrid, sblock, 0, st>>>(
+          g, U, hop_coef<double>(m_w, mu), hop_coef<double>(m_w, -mu), lz, (const double2*)vec.vh,
+          (const double2*)vec.wh, (double2*)vec.av, (double2*)vec.aw);
+    else if (lf == LINK_F16R12)
+      k_lz_pair_split<float, LINK_F16R12><<<sgrid, sblock, 0, st>>>(
+          g, U, hop_coef<float>(m_w, mu), hop_coef<float>(m_w, -mu), lz, (const float2*)vec.vh,
+          (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
+    else
+      k_lz_pair_split<float, LINK_F32><<<sgrid, sblock, 0, st>>>(
+          g, U, hop_coef<float>(m_w, mu), hop_coef<float>(m_w, -mu), lz, (const float2*)vec.vh,
+          (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
+    return cudaGetLastError();
+  }
   dim3 pgrid((g.vol + kPairSites - 1) / kPairSites, lz.nrhs), pblock(kPairSites, 2);
   if (f64)
     k_lz_pair<double, LINK_F64><<<pgrid, pblock, 0, st>>>(g, U, hop_coef<double>(m_w, mu), hop_coef<double>(m_w, -mu),
@@ -416,13 +477,13 @@ cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64,
 }
 
 cudaError_t launch_lanczos_update(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, cudaStream_t st) {
-  dim3 grid((g.vol + kBlock - 1) / kBlock, lz.nrhs);
+  dim3 grid(vec_blocks(g), lz.nrhs);
   if (f64)
-    k_lz_update<double><<<grid, kBlock, 0, st>>>(g, lz, (double2*)vec.vh, (double2*)vec.wh, (const double2*)vec.av,
-                                                  (const double2*)vec.aw);
+    k_lz_update<double><<<grid, kVecBlock, 0, st>>>(g, lz, (double2*)vec.vh, (double2*)vec.wh,
+                                                     (const double2*)vec.av, (const double2*)vec.aw);
   else
-    k_lz_update<float><<<grid, kBlock, 0, st>>>(g, lz, (float2*)vec.vh, (float2*)vec.wh, (const float2*)vec.av,
-                                                 (const float2*)vec.aw);
+    k_lz_update<float><<<grid, kVecBlock, 0, st>>>(g, lz, (float2*)vec.vh, (float2*)vec.wh, (const float2*)vec.av,
+                                                    (const float2*)vec.aw);
   return cudaGetLastError();
 }
 
@@ -464,6 +525,62 @@ __global__ void __launch_bounds__(256) k_lz_combine(int vol, int kmax, const int
   if (xp) acc = acc + ldc<double>(xp, (size_t)rhs * n + e);
   int c = (int)(e / vol), s = (int)(e % vol);
   x[(size_t)rhs * n + (size_t)s * 12 + c] = make_double2(acc.re, acc.im);
+}
+
+// ||sum_j d1_j vhat_j||^2 and ||sum_j d2_j vhat_j||^2 per rhs (the change of x between two
+// checks and the Krylov part of x), each rhs up to its own kr; result out[rhs][2].
+template <class R>
+__global__ void __launch_bounds__(256) k_lz_vnorms(int vol, int kmax, const int* kr, const typename V2<R>::T* vh,
+                                                   const double2* d1, const double2* d2, int kcoef, double* part,
+                                                   unsigned* count, double* out) {
+  __shared__ double2 c1[256], c2[256];
+  const int rhs = blockIdx.y;
+  const int k = kr[rhs];
+  const size_t n = (size_t)12 * vol;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const typename V2<R>::T* base = vh + (size_t)rhs * (kmax + 1) * n;
+  zd a1 = mk(0.0, 0.0), a2 = mk(0.0, 0.0);
+  for (int j0 = 0; j0 < k; j0 += 256) {
+    __syncthreads();
+    if (j0 + (int)threadIdx.x < k) {
+      c1[threadIdx.x] = d1[(size_t)rhs * kcoef + j0 + threadIdx.x];
+      c2[threadIdx.x] = d2[(size_t)rhs * kcoef + j0 + threadIdx.x];
+    }
+    __syncthreads();
+    if (e < n) {
+      int jn = min(256, k - j0);
+      for (int jj = 0; jj < jn; ++jj) {
+        cplx<R> v = ldc<R>(base, (size_t)(j0 + jj) * n + e);
+        zd vd = mk((double)v.re, (double)v.im);
+        a1 = a1 + mk(c1[jj].x, c1[jj].y) * vd;
+        a2 = a2 + mk(c2[jj].x, c2[jj].y) * vd;
+      }
+    }
+  }
+  double acc[2] = {norm2(a1), norm2(a2)};
+  block_sum<2>(acc);
+  double* pr = part + (size_t)rhs * gridDim.x * 2;
+  if (publish_partials<2>(acc, pr, count + rhs)) {
+    reduce_partials<2>(pr, gridDim.x, acc);
+    if (threadIdx.x == 0) {
+      out[rhs * 2] = acc[0];
+      out[rhs * 2 + 1] = acc[1];
+    }
+  }
+}
+
+cudaError_t launch_lanczos_vnorms(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, const int* kr,
+                                  const double2* d1, const double2* d2, int kcoef, double* part, unsigned* count,
+                                  double* out, cudaStream_t st) {
+  size_t n = (size_t)12 * g.vol;
+  dim3 grid((unsigned)((n + 255) / 256), lz.nrhs);
+  if (f64)
+    k_lz_vnorms<double><<<grid, 256, 0, st>>>(g.vol, lz.kmax, kr, (const double2*)vec.vh, d1, d2, kcoef, part, count,
+                                               out);
+  else
+    k_lz_vnorms<float><<<grid, 256, 0, st>>>(g.vol, lz.kmax, kr, (const float2*)vec.vh, d1, d2, kcoef, part, count,
+                                              out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_lanczos_combine(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, const int* kr,

@@ -7,6 +7,12 @@ namespace ovl {
 
 constexpr int kBlock = 128;     // threads per block of the site-parallel kernels
 constexpr int kPairSites = 64;  // sites per block of the pair stencil (x2 threads)
+constexpr int kSplitVolume = 32768;  // below this many sites the pair stencils split each site over 8 threads
+inline bool use_split(const Geom& g) { return g.vol < kSplitVolume; }
+constexpr int kVecBlock = 256;  // threads per block of the element-parallel vector kernels
+inline unsigned vec_blocks(const Geom& g) { return (unsigned)((12 * (size_t)g.vol + kVecBlock - 1) / kVecBlock); }
+// partial-sum slots per rhs: the most blocks any reduction kernel launches (the element-parallel ones)
+inline int partial_slots(const Geom& g) { return (int)vec_blocks(g); }
 
 // Device state of the two-sided Lanczos recurrences for nrhs right-hand sides.
 // Index conventions: column j = 1..kmax+1 of the basis; scalars indexed by j.
@@ -66,6 +72,11 @@ cudaError_t launch_lanczos_update(const Geom& g, bool f64, const LzDev& lz, cons
 // One step j (read from lz.j): pair stencil + alpha, then the biorthogonal update.
 cudaError_t launch_lanczos_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
                                 const LzDev& lz, const LzVecs& vec, cudaStream_t st);
+// out[rhs][0..1] = ||sum_{j<k_r} d1_j vhat_j||^2, ||sum_{j<k_r} d2_j vhat_j||^2 (own scratch part,
+// count: part >= nrhs * 2 * ceil(12V/256) doubles, count >= nrhs zeros).
+cudaError_t launch_lanczos_vnorms(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, const int* kr,
+                                  const double2* d1, const double2* d2, int kcoef, double* part, unsigned* count,
+                                  double* out, cudaStream_t st);
 // x = x_P + sum_{j<=k_r} coef_j vhat_j, written canonical complex128; coef [nrhs][kcoef],
 // kr [nrhs] (device) the Krylov dimension of each rhs.
 cudaError_t launch_lanczos_combine(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, const int* kr,

@@ -87,6 +87,45 @@ __global__ void __launch_bounds__(kBlock) k_ms_start(Geom g, MsDev ms, MsVecs v,
   }
 }
 
+// last block of pair2: alpha_k, then zeta^i_{k+1} and alpha^i_k of the live shifts
+__device__ __forceinline__ void ms_alpha_and_shifts(MsDev& ms, int rhs, const double (&pv)[4]) {
+  __shared__ zd alpha_sh;
+  __shared__ int bad;
+  const int t = lin_tid();
+  double2* sd = ms.seed + (size_t)rhs * 8;
+  if (t == 0) {
+    zd den = mk(pv[0], pv[1]);
+    zd rho = ldc<double>(sd, 0);
+    double dd = norm2(den);
+    bad = !(dd > 0.0) || !(dd < 1e300);
+    zd alpha = bad ? mk(0.0, 0.0) : (1.0 / dd) * (rho * conj(den));
+    alpha_sh = alpha;
+    if (bad) ms.status[rhs] = 1;
+    sd[1] = make_double2(alpha.re, alpha.im);
+  }
+  __syncthreads();
+  if (bad) return;
+  const zd ak = alpha_sh, akm = ldc<double>(sd, 2), bkm = ldc<double>(sd, 3);
+  for (int i = t; i < ms.s; i += lin_nthreads()) {
+    const size_t si = (size_t)rhs * ms.s + i;
+    int act = ms.active[si];
+    if (act == 2) ms.active[si] = act = 0;
+    if (!act) continue;
+    double2* z = ms.zeta + si * 3;
+    zd zm = ldc<double>(z, 0), z0 = ldc<double>(z, 1);
+    zd d1 = mk(1.0 - ak.re * ms.dsig[i], -ak.im * ms.dsig[i]);
+    zd den = akm * zm * d1 + ak * bkm * (zm - z0);
+    zd num = z0 * zm * akm;
+    double dn = norm2(den);
+    zd zp = dn > 0 ? (1.0 / dn) * (num * conj(den)) : mk(0.0, 0.0);
+    z[2] = make_double2(zp.re, zp.im);
+    double z0n = norm2(z0);
+    zd ratio = z0n > 0 ? (1.0 / z0n) * (zp * conj(z0)) : mk(0.0, 0.0);
+    zd ai = ak * ratio;
+    ms.ash[si] = make_double2(ai.re, ai.im);
+  }
+}
+
 // pair1 (MODE 0): t = A p, t~ = A^H p~.  pair2 (MODE 1): q = A t - s1 p, q~ = A^H t~ - s1 p~, p~^H q.
 template <class R, int LF, int MODE>
 __global__ void __launch_bounds__(2 * kPairSites) k_ms_pair(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm, MsDev ms,
@@ -127,78 +166,77 @@ __global__ void __launch_bounds__(2 * kPairSites) k_ms_pair(Geom g, Links U, Hop
   double pv[4] = {acc[0], acc[1], 0, 0};
   if (publish_partials<4>(pv, part, ms.count + rhs)) {
     reduce_partials<4>(part, gridDim.x, pv);
-    __shared__ zd alpha_sh;
-    __shared__ int bad;
-    const int t = lin_tid();
-    double2* sd = ms.seed + (size_t)rhs * 8;
-    if (t == 0) {
-      zd den = mk(pv[0], pv[1]);
-      zd rho = ldc<double>(sd, 0);
-      double dd = norm2(den);
-      bad = !(dd > 0.0) || !(dd < 1e300);
-      zd alpha = bad ? mk(0.0, 0.0) : (1.0 / dd) * (rho * conj(den));
-      alpha_sh = alpha;
-      if (bad) ms.status[rhs] = 1;
-      sd[1] = make_double2(alpha.re, alpha.im);
+    ms_alpha_and_shifts(ms, rhs, pv);
+  }
+}
+
+// pair1 / pair2 with 8 threads per site (small lattices): see pair_split.
+template <class R, int LF, int MODE>
+__global__ void __launch_bounds__(8 * kSplitSites) k_ms_pair_split(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm,
+                                                                   MsDev ms, MsVecs v) {
+  using T = typename V2<R>::T;
+  __shared__ SplitSmem<R> sm;
+  const int rhs = blockIdx.y;
+  if (MODE == 0 && blockIdx.x == 0 && lin_tid() == 0 && ms.status[rhs] == 4) ms.status[rhs] = 2;
+  if (ms.status[rhs] != 0) return;
+  const size_t n = (size_t)12 * g.vol;
+  const T* in0 = (const T*)(MODE == 0 ? v.p : v.t) + voff<R>(rhs, n);
+  const T* in1 = (const T*)(MODE == 0 ? v.pt : v.tt) + voff<R>(rhs, n);
+  const R s1 = (R)ms.sigma1;
+  double acc[2] = {0, 0};
+  pair_split<R, LF>(g, U, cp, cm, in0, in1, sm, [&](int which, int s, Spin<R>& o) {
+    T* out = (T*)(MODE == 0 ? (which ? v.tt : v.t) : (which ? v.qt : v.q)) + voff<R>(rhs, n);
+    const T* pp = (const T*)(which ? v.pt : v.p) + voff<R>(rhs, n);
+    const T* ptl = (const T*)v.pt + voff<R>(rhs, n);
+    cplx<R> a = mk<R>(0, 0);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      cplx<R> x = o.c[c / 3][c % 3];
+      if (c >= 6) x = -x;  // gamma5
+      if (MODE == 1) {
+        x = x - s1 * ldc<R>(pp, (size_t)c * g.vol + s);
+        if (!which) a = a + cdot(ldc<R>(ptl, (size_t)c * g.vol + s), x);
+      }
+      stc<R>(out, (size_t)c * g.vol + s, x);
     }
-    __syncthreads();
-    if (bad) return;
-    const zd ak = alpha_sh, akm = ldc<double>(sd, 2), bkm = ldc<double>(sd, 3);
-    for (int i = t; i < ms.s; i += lin_nthreads()) {
-      const size_t si = (size_t)rhs * ms.s + i;
-      int act = ms.active[si];
-      if (act == 2) ms.active[si] = act = 0;  // its final update happened last step
-      if (!act) continue;
-      double2* z = ms.zeta + si * 3;
-      zd zm = ldc<double>(z, 0), z0 = ldc<double>(z, 1);
-      // zeta_{k+1} = z0 zm a_{k-1} / (a_{k-1} zm (1 - a_k d) + a_k b_{k-1} (zm - z0))
-      zd d1 = mk(1.0 - ak.re * ms.dsig[i], -ak.im * ms.dsig[i]);
-      zd den = akm * zm * d1 + ak * bkm * (zm - z0);
-      zd num = z0 * zm * akm;
-      double dn = norm2(den);
-      zd zp = dn > 0 ? (1.0 / dn) * (num * conj(den)) : mk(0.0, 0.0);
-      z[2] = make_double2(zp.re, zp.im);
-      double z0n = norm2(z0);
-      zd ratio = z0n > 0 ? (1.0 / z0n) * (zp * conj(z0)) : mk(0.0, 0.0);
-      zd ai = ak * ratio;
-      ms.ash[si] = make_double2(ai.re, ai.im);
-    }
+    acc[0] = (double)a.re;
+    acc[1] = (double)a.im;
+  });
+  if (MODE == 0) return;
+  block_sum<2>(acc);
+  double* part = ms.part + (size_t)rhs * ms.nblk * 4;
+  double pv[4] = {acc[0], acc[1], 0, 0};
+  if (publish_partials<4>(pv, part, ms.count + rhs)) {
+    reduce_partials<4>(part, gridDim.x, pv);
+    ms_alpha_and_shifts(ms, rhs, pv);
   }
 }
 
 // update: r -= alpha q, r~ -= conj(alpha) q~; rho' = r~^H r, |r|^2
 template <class R>
-__global__ void __launch_bounds__(kBlock) k_ms_update(Geom g, MsDev ms, MsVecs v) {
+__global__ void __launch_bounds__(kVecBlock) k_ms_update(Geom g, MsDev ms, MsVecs v) {
   using T = typename V2<R>::T;
   const int rhs = blockIdx.y;
   if (ms.status[rhs] != 0) return;
   const size_t n = (size_t)12 * g.vol;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // one vector element per thread
   double2* sd = ms.seed + (size_t)rhs * 8;
   const zd ak = ldc<double>(sd, 1);
   const cplx<R> a = mk<R>((R)ak.re, (R)ak.im), ac = mk<R>((R)ak.re, (R)-ak.im);
   double acc[4] = {0, 0, 0, 0};
-  if (s < g.vol) {
+  if (e < n) {
     T* r = (T*)v.r + voff<R>(rhs, n);
     T* rt = (T*)v.rt + voff<R>(rhs, n);
     const T* q = (const T*)v.q + voff<R>(rhs, n);
     const T* qt = (const T*)v.qt + voff<R>(rhs, n);
-    R ipr = 0, ipi = 0, nr = 0;
-#pragma unroll
-    for (int c = 0; c < 12; ++c) {
-      size_t e = (size_t)c * g.vol + s;
-      cplx<R> x = ldc<R>(r, e) - a * ldc<R>(q, e);
-      cplx<R> y = ldc<R>(rt, e) - ac * ldc<R>(qt, e);
-      stc<R>(r, e, x);
-      stc<R>(rt, e, y);
-      cplx<R> ip = cdot(y, x);
-      ipr += ip.re;
-      ipi += ip.im;
-      nr += norm2(x);
-    }
-    acc[0] = ipr;
-    acc[1] = ipi;
-    acc[2] = nr;
+    cplx<R> x = ldc<R>(r, e) - a * ldc<R>(q, e);
+    cplx<R> y = ldc<R>(rt, e) - ac * ldc<R>(qt, e);
+    stc<R>(r, e, x);
+    stc<R>(rt, e, y);
+    cplx<R> ip = cdot(y, x);
+    acc[0] = ip.re;
+    acc[1] = ip.im;
+    acc[2] = norm2(x);
   }
   block_sum<4>(acc);
   double* part = ms.part + (size_t)rhs * ms.nblk * 4;
@@ -254,13 +292,13 @@ __global__ void __launch_bounds__(kBlock) k_ms_update(Geom g, MsDev ms, MsVecs v
 
 // dirs: X += sum_i omega_i alpha^i p^i (FP64); p^i = zeta^i r + beta^i p^i; p, p~ updates
 template <class R>
-__global__ void __launch_bounds__(kBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs v) {
+__global__ void __launch_bounds__(kVecBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs v) {
   using T = typename V2<R>::T;
   const int rhs = blockIdx.y;
   const int st = ms.status[rhs];
   if (st != 0 && st != 4) return;
   const size_t n = (size_t)12 * g.vol;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // one vector element per thread
   __shared__ double2 coefx[kMaxShifts], coefz[kMaxShifts], coefb[kMaxShifts];
   __shared__ int act[kMaxShifts];
   for (int i = threadIdx.x; i < ms.s; i += blockDim.x) {
@@ -272,7 +310,7 @@ __global__ void __launch_bounds__(kBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs v) 
     coefb[i] = ms.bsh[si];
   }
   __syncthreads();
-  if (s >= g.vol) return;
+  if (e >= n) return;
   const zd bk = ldc<double>(ms.seed + (size_t)rhs * 8, 5);
   const cplx<R> b = mk<R>((R)bk.re, (R)bk.im), bc = mk<R>((R)bk.re, (R)-bk.im);
   const T* r = (const T*)v.r + voff<R>(rhs, n);
@@ -281,8 +319,7 @@ __global__ void __launch_bounds__(kBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs v) 
   T* pt = (T*)v.pt + voff<R>(rhs, n);
   T* ps = (T*)v.ps + (size_t)rhs * ms.s * n;
   double2* X = v.X + voff<R>(rhs, n);
-  for (int c = 0; c < 12; ++c) {
-    const size_t e = (size_t)c * g.vol + s;
+  {
     const cplx<R> rv = ldc<R>(r, e);
     zd xa = ldc<double>(X, e);
     for (int i = 0; i < ms.s; ++i) {
@@ -322,16 +359,24 @@ cudaError_t launch_ms_start(const Geom& g, bool f64, const MsDev& ms, const MsVe
 template <class R, int LF>
 static cudaError_t ms_step_t(const Geom& g, const Links& U, double m_w, double mu, const MsDev& ms, const MsVecs& v,
                              cudaStream_t st, cudaEvent_t* ev) {
-  dim3 grid((g.vol + kBlock - 1) / kBlock, ms.nrhs);
+  dim3 grid(vec_blocks(g), ms.nrhs);
   dim3 pgrid((g.vol + kPairSites - 1) / kPairSites, ms.nrhs), pblock(kPairSites, 2);
   HopCoef<R> cp = hop_coef<R>(m_w, mu), cm = hop_coef<R>(m_w, -mu);
+  dim3 sgrid((g.vol + kSplitSites - 1) / kSplitSites, ms.nrhs), sblock(kSplitSites, 8);
+  const bool split = use_split(g);
   if (ev) cudaEventRecord(ev[0], st);
-  k_ms_pair<R, LF, 0><<<pgrid, pblock, 0, st>>>(g, U, cp, cm, ms, v);
+  if (split)
+    k_ms_pair_split<R, LF, 0><<<sgrid, sblock, 0, st>>>(g, U, cp, cm, ms, v);
+  else
+    k_ms_pair<R, LF, 0><<<pgrid, pblock, 0, st>>>(g, U, cp, cm, ms, v);
   if (ev) cudaEventRecord(ev[1], st);
-  k_ms_pair<R, LF, 1><<<pgrid, pblock, 0, st>>>(g, U, cp, cm, ms, v);
-  k_ms_update<R><<<grid, kBlock, 0, st>>>(g, ms, v);
+  if (split)
+    k_ms_pair_split<R, LF, 1><<<sgrid, sblock, 0, st>>>(g, U, cp, cm, ms, v);
+  else
+    k_ms_pair<R, LF, 1><<<pgrid, pblock, 0, st>>>(g, U, cp, cm, ms, v);
+  k_ms_update<R><<<grid, kVecBlock, 0, st>>>(g, ms, v);
   if (ev) cudaEventRecord(ev[2], st);
-  k_ms_dirs<R><<<grid, kBlock, 0, st>>>(g, ms, v);
+  k_ms_dirs<R><<<grid, kVecBlock, 0, st>>>(g, ms, v);
   if (ev) cudaEventRecord(ev[3], st);
   return cudaGetLastError();
 }

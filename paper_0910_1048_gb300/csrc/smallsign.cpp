@@ -458,8 +458,12 @@ ovl_status small_sign_rational(int k, const cz* al, const cz* be, const cz* de, 
                                double* inv_res) {
   const double eps = 1e-15, tol_inv = 1e-11;
   const int s_max = 4000;
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    if (*hint_s <= 0 || attempt == 1) {
+  // attempts: the cached (c, s); the same c with 50% more poles (new Ritz values closer to
+  // the imaginary axis usually need only a few more); (c, s) from freshly computed Ritz values
+  const bool had_hint = *hint_s > 0;
+  for (int attempt = had_hint ? 0 : 2; attempt < 3; ++attempt) {
+    if (attempt == 1) *hint_s = std::min(s_max, (*hint_s * 3 + 1) / 2);
+    if (attempt == 2) {
       std::vector<cz> lam;
       if (!ritz_values(k, al, be, de, lam)) return OVL_ENOCONV;
       double lmax = 0;

@@ -1,9 +1,11 @@
 // Host driver of direct two-sided Lanczos-LR(m, k), Algorithm 4:
 //   x_P = R f(Lambda) L^H b;  r = b - R L^H b;  r~ = b - L R^H b;  v_1 = r/beta, w_1 ~ r~;
 //   k steps of two-sided Lanczos (Eqs. 2sided1/2);  x = x_P + beta V_k f(H_k) e_1.
-// The paper fixes k a priori; this driver also stops early: every `check_every` steps it
-// copies H_j to the host, evaluates y_j = sign(H_j) e_1 and stops when
-//   sum_i |y_j(i) - y_j'(i)| ||v_i|| <= tol ||y_j||   (j' = previous check).
+// The paper fixes k a priori; this driver also stops early: the scalars of every chunk of
+// `check_every` steps are copied to the host, and (once j has grown 10% past the previous
+// evaluation j') y_j = sign(H_j) e_1 is evaluated; it stops when
+//   ||V_j (y_j - [y_j'; 0])|| <= tol ||V_j y_j||,
+// both norms computed on the GPU on a side stream.
 // All per-step scalars stay on the device (no host round trip inside a chunk), so a chunk
 // of steps is one CUDA graph, replayed; the next chunk is queued before the host checks
 // the previous one, overlapping sign(H_j) e_1 with device work.
@@ -54,6 +56,15 @@ struct DirectWS {
   int g_lf = -1;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
+  // stopping estimate ||V (y_j - y_j')|| / ||V y_j||, computed on a side stream with its own
+  // scratch so that it overlaps the chunk in flight on `stream`
+  cudaStream_t nstream = nullptr;
+  double2* nd1 = nullptr;     // [nrhs][kmax] coefficients of the change
+  double2* nd2 = nullptr;     // [nrhs][kmax] coefficients of the Krylov part
+  int* nkr = nullptr;         // [nrhs]
+  double* npart = nullptr;    // [nrhs][2][vec blocks]
+  unsigned* ncount = nullptr; // [nrhs]
+  double* nout = nullptr;     // [nrhs][2]
 };
 
 void free_direct_ws(DirectWS* w) {
@@ -71,6 +82,7 @@ void free_direct_ws(DirectWS* w) {
       cudaFreeHost(w->h_block);
   }
   if (w->stream) cudaStreamDestroy(w->stream);
+  if (w->nstream) cudaStreamDestroy(w->nstream);
   if (w->ev) cudaEventDestroy(w->ev);
   delete w;
 }
@@ -91,7 +103,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   w->vol = vol;
   const size_t n = (size_t)12 * vol;
   const size_t elt = f64 ? 16 : 8;
-  const int nblk = (vol + kPairSites - 1) / kPairSites;  // the most blocks of any reduction kernel
+  const int nblk = partial_slots(lat->g);  // the most blocks of any reduction kernel
   const int ks = kmax + 2;
   // carve one device block
   size_t off = 0;
@@ -122,7 +134,11 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   size_t o_kr = take((size_t)nrhs * 4);
   size_t o_bd = take((size_t)nrhs * n * 16);
   size_t o_xd = take((size_t)nrhs * n * 16);
-  if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  size_t o_n1 = take((size_t)nrhs * kmax * 16), o_n2 = take((size_t)nrhs * kmax * 16);
+  size_t o_nk = take((size_t)nrhs * 4), o_np = take((size_t)nrhs * 2 * vec_blocks(lat->g) * 8);
+  size_t o_nc = take((size_t)nrhs * 4), o_no = take((size_t)nrhs * 2 * 8);
+  if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&w->nstream, cudaStreamNonBlocking) != cudaSuccess) {
     delete w;
     set_error("apply_sign: cannot create a stream");
     return OVL_ECUDA;
@@ -132,6 +148,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
   if (e != cudaSuccess) {
     cudaStreamDestroy(w->stream);
+    cudaStreamDestroy(w->nstream);
     delete w;
     set_error("apply_sign: cannot allocate %zu bytes of device workspace: %s", off, cudaGetErrorString(e));
     return OVL_ENOMEM;
@@ -164,7 +181,14 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   w->kr = (int*)(base + o_kr);
   w->bdev = (double2*)(base + o_bd);
   w->xdev = (double2*)(base + o_xd);
-  if (cudaMemsetAsync(lz.count, 0, (size_t)nrhs * 4, w->stream) != cudaSuccess) {
+  w->nd1 = (double2*)(base + o_n1);
+  w->nd2 = (double2*)(base + o_n2);
+  w->nkr = (int*)(base + o_nk);
+  w->npart = (double*)(base + o_np);
+  w->ncount = (unsigned*)(base + o_nc);
+  w->nout = (double*)(base + o_no);
+  if (cudaMemsetAsync(lz.count, 0, (size_t)nrhs * 4, w->stream) != cudaSuccess ||
+      cudaMemsetAsync(w->ncount, 0, (size_t)nrhs * 4, w->stream) != cudaSuccess) {
     free_direct_ws(w);
     set_error("apply_sign: cudaMemset failed");
     return OVL_ECUDA;
@@ -261,16 +285,47 @@ static ovl_status evaluate_rhs(DirectWS* w, int q, int r, RhsState& rs, double* 
   ovl_status s = small_sign(k, al.data(), be.data(), de.data(), y.data(), 0, &rs.hint_c, &rs.hint_s);
   *t_small += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (s != OVL_OK) return s;
-  double ny = 0, dif = 0;
-  for (int i = 0; i < k; ++i) {
-    ny += std::norm(y[i]);
-    std::complex<double> p = (i < (int)rs.y.size()) ? rs.y[i] : 0.0;
-    dif += std::abs(y[i] - p) * h.vnorm[r * ks + i + 1];
-  }
-  rs.est = rs.y.empty() ? 1e300 : dif / std::sqrt(ny);
+  rs.est = 1e300;  // set by estimate_changes()
   rs.yprev.swap(rs.y);
   rs.y.swap(y);
   rs.k = k;
+  return OVL_OK;
+}
+
+// est_r = ||V_k (y_k - [y_k'; 0])|| / ||V_k y_k|| for the rhs in `which` (the relative change of
+// the Krylov part of x since the previous evaluation), computed on the side stream.
+static ovl_status estimate_changes(DirectWS* w, const Geom& g, bool f64, const LzVecs& vec, int q,
+                                   std::vector<RhsState>& rs, const std::vector<int>& which) {
+  const int nrhs = w->nrhs, kmax = w->kmax;
+  const size_t ks = (size_t)kmax + 2;
+  const DirectWS::Mirror& h = w->h[q];
+  std::vector<double2> d1((size_t)nrhs * kmax, make_double2(0, 0)), d2 = d1;
+  std::vector<int> kr(nrhs, 0);
+  bool any = false;
+  for (int r : which) {
+    RhsState& s = rs[r];
+    if (s.k < 1 || s.yprev.empty()) continue;
+    kr[r] = s.k;
+    any = true;
+    for (int i = 0; i < s.k; ++i) {
+      std::complex<double> p = i < (int)s.yprev.size() ? s.yprev[i] : 0.0;
+      std::complex<double> a = (s.y[i] - p) * h.sv[r * ks + i + 1], b = s.y[i] * h.sv[r * ks + i + 1];
+      d1[(size_t)r * kmax + i] = make_double2(a.real(), a.imag());
+      d2[(size_t)r * kmax + i] = make_double2(b.real(), b.imag());
+    }
+  }
+  if (!any) return OVL_OK;
+  cudaStream_t ns = w->nstream;
+  OVL_CHECK_CUDA(cudaMemcpyAsync(w->nd1, d1.data(), d1.size() * 16, cudaMemcpyHostToDevice, ns));
+  OVL_CHECK_CUDA(cudaMemcpyAsync(w->nd2, d2.data(), d2.size() * 16, cudaMemcpyHostToDevice, ns));
+  OVL_CHECK_CUDA(cudaMemcpyAsync(w->nkr, kr.data(), nrhs * 4, cudaMemcpyHostToDevice, ns));
+  OVL_CHECK_CUDA(launch_lanczos_vnorms(g, f64, w->lz, vec, w->nkr, w->nd1, w->nd2, kmax, w->npart, w->ncount, w->nout,
+                                       ns));
+  std::vector<double> out((size_t)nrhs * 2);
+  OVL_CHECK_CUDA(cudaMemcpyAsync(out.data(), w->nout, out.size() * 8, cudaMemcpyDeviceToHost, ns));
+  OVL_CHECK_CUDA(cudaStreamSynchronize(ns));
+  for (int r : which)
+    if (kr[r] > 0) rs[r].est = out[2 * r + 1] > 0 ? std::sqrt(out[2 * r] / out[2 * r + 1]) : 1e300;
   return OVL_OK;
 }
 
@@ -446,10 +501,21 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
       }
       next_eval = std::max(evq[q] + chunk, (int)(1.1 * evq[q]));
       bool all_done = true;
+      std::vector<ovl_status> es_r(nrhs, OVL_OK);
+      std::vector<int> evaluated;
+      for (int r = 0; r < nrhs; ++r) {
+        if (rs[r].done) continue;
+        es_r[r] = evaluate_rhs(w, q, r, rs[r], &t_small);
+        if (es_r[r] == OVL_OK) evaluated.push_back(r);
+      }
+      {
+        ovl_status est_st = estimate_changes(w, g, f64, vec, q, rs, evaluated);
+        if (est_st != OVL_OK) return est_st;
+      }
       for (int r = 0; r < nrhs; ++r) {
         RhsState& s = rs[r];
         if (s.done) continue;
-        ovl_status es = evaluate_rhs(w, q, r, s, &t_small);
+        ovl_status es = es_r[r];
         if (es != OVL_OK) {
           s.status = es;
           s.done = true;

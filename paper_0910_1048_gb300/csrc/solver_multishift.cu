@@ -69,7 +69,7 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m)
   w->vol = vol;
   w->m = m;
   const size_t n = (size_t)12 * vol, elt = f64 ? 16 : 8;
-  const int nblk = (vol + kPairSites - 1) / kPairSites;
+  const int nblk = partial_slots(lat->g);
   size_t off = 0;
   auto take = [&](size_t b) {
     size_t o = off;

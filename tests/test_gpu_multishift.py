@@ -146,3 +146,21 @@ def test_requires_spectrum_bounds(ovl, p4m):
     with pytest.raises(ovl.OvlError) as e:
         ovl.ovl_apply_sign(lat, p_, bt, torch.empty_like(bt))
     assert "spec" in str(e.value)
+
+
+def test_equal_k_parity_1616(ovl, ctx):
+    """16^4 runs the one-thread-per-site multishift pair kernels; equal-k parity at k = 3."""
+    dims = (16, 16, 16, 16)
+    u = synth.gauge_links(dims, 9)
+    b = synth.gaussian_source(dims, 10)
+    lat = ovl.ovl_create_lattice(ctx, dims, -1)
+    ovl.ovl_set_links(lat, u, ovl.OVL_F64)
+    k = 3
+    st, info, x = _solve(ovl, lat, b, mu=0.3, tol=0.0, k_max=k, spec_lo=0.05, spec_hi=2.7, s=6, check_every=1)
+    w, sg = rational.neuberger_scaled(6, rational.scale_and_d(*rational.circle_from_gap(0.05, 2.7))[0])
+    a = lambda v: wilson.apply_hw(u, v.reshape(b.shape), -2.0, 0.3).ravel()
+    ah = lambda v: wilson.apply_hw(u, v.reshape(b.shape), -2.0, -0.3).ravel()
+    xs, _ = lanczos.multishift_iterates(lambda v: a(a(v)), lambda v: ah(ah(v)), b.ravel(), b.ravel(), k, sg)
+    xo = a(np.tensordot(w, xs, axes=1))
+    assert _rel(x.ravel(), xo) < 1e-9
+    ovl.ovl_destroy_lattice(lat)
