@@ -179,6 +179,22 @@ void ovl_sign_params_default(ovl_sign_params* p);
 ovl_status ovl_apply_sign(ovl_lattice* lat, const ovl_sign_params* p, int32_t nrhs,
                           const void* b, void* x, ovl_sign_info* info, void* stream);
 
+/* Allocation-free variant of ovl_apply_sign's direct method, for callers that cannot
+ * allocate device memory: processes whose device memory belongs to another allocator (a
+ * framework's pool, a server that reserves its budget at start-up) and latency-critical
+ * loops that must not call cudaMalloc/cudaFree. The paper has no counterpart: this is a
+ * property of the library, not of the method. Same kernels and results as ovl_apply_sign
+ * (method OVL_DIRECT_2SL); b and x are device buffers; runs on `stream` and synchronizes it.
+ * All scratch lives in one static 64 MiB device array per GPU that loads the library, held
+ * until the process exits; its address is looked up on the first call for each device, so
+ * make that first call before any stream capture. Calls share the array: calls that overlap
+ * on the GPU race. No CUDA graphs, streams, events or pinned buffers are created.
+ * Errors: EINVAL (host_io set, method not direct, or scratch needed > 64 MiB, e.g. a basis of
+ * nrhs * (k_max+1) * 12 V complex values that does not fit), ECUDA; solve statuses as
+ * ovl_apply_sign. */
+ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_params* p, int32_t nrhs,
+                                  const void* b, void* x, ovl_sign_info* info, void* stream);
+
 /* Tridiagonal H_k of the last direct solve on this lattice, rhs index `rhs`:
  * alpha[k], beta[k-1] (super-diagonal), delta[k-1] (sub-diagonal), complex128 host
  * arrays; *k_out = k. Pass k_cap = capacity of alpha. Errors: EINVAL, ENOTFOUND. */

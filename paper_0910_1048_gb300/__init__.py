@@ -91,6 +91,8 @@ _PROTOS = {
     "ovl_apply_DW": (_I, [_P, _D, _D, ctypes.c_uint32, _I, _I, _P, _P, _P]),
     "ovl_sign_params_default": (None, [ctypes.POINTER(ovl_sign_params)]),
     "ovl_apply_sign": (_I, [_P, ctypes.POINTER(ovl_sign_params), _I, _P, _P, ctypes.POINTER(ovl_sign_info), _P]),
+    "ovl_apply_sign_noalloc": (_I, [_P, ctypes.POINTER(ovl_sign_params), _I, _P, _P,
+                                    ctypes.POINTER(ovl_sign_info), _P]),
     "ovl_get_tridiag": (_I, [_P, _I, _I, ctypes.POINTER(_I), _P, _P, _P]),
     "ovl_small_sign": (_I, [_I, _P, _P, _P, _P, _I]),
     "ovl_rational_coeffs": (_I, [_I, _I, _D, _D, _D, _I, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
@@ -260,6 +262,19 @@ def ovl_apply_sign(lat, params: ovl_sign_params, b, x, stream=None, raise_on_err
     infos = (ovl_sign_info * nrhs)()
     st = lib.ovl_apply_sign(lat, ctypes.byref(params), nrhs, _ptr(b), _ptr(x), infos, _stream(stream, b, x))
     if st in (OVL_EINVAL, OVL_ENOMEM, OVL_ECUDA) or (raise_on_error and st < 0):
+        raise _err(st)
+    return st, [i.as_dict() for i in infos]
+
+
+def ovl_apply_sign_noalloc(lat, params: ovl_sign_params, b, x, stream=None):
+    """ovl_apply_sign's direct method without any device allocation (scratch in a static
+    64 MiB device array): for callers that cannot allocate device memory. b, x are torch CUDA
+    tensors. Returns (status, [info dict per rhs]); raises OvlError for argument/CUDA errors."""
+    n = ovl_lattice_n(lat)
+    nrhs = b.numel() // n
+    infos = (ovl_sign_info * nrhs)()
+    st = lib.ovl_apply_sign_noalloc(lat, ctypes.byref(params), nrhs, _ptr(b), _ptr(x), infos, _stream(stream, b, x))
+    if st in (OVL_EINVAL, OVL_ENOMEM, OVL_ECUDA):
         raise _err(st)
     return st, [i.as_dict() for i in infos]
 
