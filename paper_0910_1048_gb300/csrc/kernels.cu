@@ -8,10 +8,31 @@
 // the last block to finish (atomic ticket) sums the partials in block order.
 #include <cuda_fp16.h>
 
+#include <map>
+#include <mutex>
+
 #include "devutil.cuh"
 #include "kernels.h"
 
 namespace ovl {
+
+// ------------------------------------------------------------------ autotuner table
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, int> g_tune;
+
+int tuned_pair_variant(int vol, int prec) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find({vol, prec});
+  return it == g_tune.end() ? -1 : it->second;
+}
+int tune_pair_variant(int vol, int prec, int (*measure)(void*), void* arg) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find({vol, prec});
+  if (it != g_tune.end()) return it->second;
+  int v = measure(arg);
+  if (v >= 0) g_tune[{vol, prec}] = v;
+  return v;
+}
 
 // ------------------------------------------------------------------ layout conversion
 template <class Tin, class Tout>
@@ -90,7 +111,7 @@ cudaError_t launch_ingest_links(const Geom& g, const double* ucan, double2* u64,
 
 // ------------------------------------------------------------------ apply D_W
 template <class R, int LF, bool NIN, bool NOUT>
-__global__ void __launch_bounds__(kBlock) k_dslash(Geom g, Links U, HopCoef<R> c, bool g5_in, bool g5_out,
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 7 : 1) k_dslash(Geom g, Links U, HopCoef<R> c, bool g5_in, bool g5_out,
                                                    const typename V2<R>::T* in, typename V2<R>::T* out) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.vol) return;
@@ -443,8 +464,10 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typen
 }
 
 cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
-                                const LzDev& lz, const LzVecs& vec, cudaStream_t st) {
-  if (use_split(g)) {
+                                const LzDev& lz, const LzVecs& vec, cudaStream_t st, int variant) {
+  if (variant < 0) variant = tuned_pair_variant(g.vol, f64 ? 0 : lf);
+  if (variant < 0) variant = use_split(g) ? 1 : 0;
+  if (variant == 1) {
     dim3 sgrid((g.vol + kSplitSites - 1) / kSplitSites, lz.nrhs), sblock(kSplitSites, 8);
     if (f64)
       k_lz_pair_split<double, LINK_F64><<<sgrid, sblock, 0, st>>>(
@@ -529,35 +552,38 @@ __global__ void __launch_bounds__(256) k_lz_combine(int vol, int kmax, const int
 
 // ||sum_j d1_j vhat_j||^2 and ||sum_j d2_j vhat_j||^2 per rhs (the change of x between two
 // checks and the Krylov part of x), each rhs up to its own kr; result out[rhs][2].
+// The sums run in FP32 arithmetic (FP64 only across elements): the result only feeds the
+// stopping estimate, whose terms are all of the size of the change itself.
 template <class R>
 __global__ void __launch_bounds__(256) k_lz_vnorms(int vol, int kmax, const int* kr, const typename V2<R>::T* vh,
                                                    const double2* d1, const double2* d2, int kcoef, double* part,
                                                    unsigned* count, double* out) {
-  __shared__ double2 c1[256], c2[256];
+  __shared__ float2 c1[256], c2[256];
   const int rhs = blockIdx.y;
   const int k = kr[rhs];
   const size_t n = (size_t)12 * vol;
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const typename V2<R>::T* base = vh + (size_t)rhs * (kmax + 1) * n;
-  zd a1 = mk(0.0, 0.0), a2 = mk(0.0, 0.0);
+  cplx<float> a1 = mk<float>(0, 0), a2 = mk<float>(0, 0);
   for (int j0 = 0; j0 < k; j0 += 256) {
     __syncthreads();
     if (j0 + (int)threadIdx.x < k) {
-      c1[threadIdx.x] = d1[(size_t)rhs * kcoef + j0 + threadIdx.x];
-      c2[threadIdx.x] = d2[(size_t)rhs * kcoef + j0 + threadIdx.x];
+      double2 x1 = d1[(size_t)rhs * kcoef + j0 + threadIdx.x], x2 = d2[(size_t)rhs * kcoef + j0 + threadIdx.x];
+      c1[threadIdx.x] = make_float2((float)x1.x, (float)x1.y);
+      c2[threadIdx.x] = make_float2((float)x2.x, (float)x2.y);
     }
     __syncthreads();
     if (e < n) {
       int jn = min(256, k - j0);
       for (int jj = 0; jj < jn; ++jj) {
         cplx<R> v = ldc<R>(base, (size_t)(j0 + jj) * n + e);
-        zd vd = mk((double)v.re, (double)v.im);
-        a1 = a1 + mk(c1[jj].x, c1[jj].y) * vd;
-        a2 = a2 + mk(c2[jj].x, c2[jj].y) * vd;
+        cplx<float> vf = mk<float>((float)v.re, (float)v.im);
+        a1 = a1 + mk<float>(c1[jj].x, c1[jj].y) * vf;
+        a2 = a2 + mk<float>(c2[jj].x, c2[jj].y) * vf;
       }
     }
   }
-  double acc[2] = {norm2(a1), norm2(a2)};
+  double acc[2] = {(double)norm2(a1), (double)norm2(a2)};
   block_sum<2>(acc);
   double* pr = part + (size_t)rhs * gridDim.x * 2;
   if (publish_partials<2>(acc, pr, count + rhs)) {

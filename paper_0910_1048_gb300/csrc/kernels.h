@@ -9,6 +9,12 @@ constexpr int kBlock = 128;     // threads per block of the site-parallel kernel
 constexpr int kPairSites = 64;  // sites per block of the pair stencil (x2 threads)
 constexpr int kSplitVolume = 32768;  // below this many sites the pair stencils split each site over 8 threads
 inline bool use_split(const Geom& g) { return g.vol < kSplitVolume; }
+// Pair-stencil variant chosen by the autotuner for (volume, precision): -1 none yet,
+// 0 one thread per site, 1 split over 8 threads. Thread-safe, process-wide.
+int tuned_pair_variant(int vol, int prec);
+// Returns the variant for the key, running `measure` (which returns 0 or 1) under the table's
+// lock the first time, so that every solve in the process uses one decision per key.
+int tune_pair_variant(int vol, int prec, int (*measure)(void*), void* arg);
 constexpr int kVecBlock = 256;  // threads per block of the element-parallel vector kernels
 inline unsigned vec_blocks(const Geom& g) { return (unsigned)((12 * (size_t)g.vol + kVecBlock - 1) / kVecBlock); }
 // partial-sum slots per rhs: the most blocks any reduction kernel launches (the element-parallel ones)
@@ -67,7 +73,7 @@ cudaError_t launch_lanczos_start(const Geom& g, bool f64, const LzDev& lz, const
                                  double2* dots, cudaStream_t st);
 // The two launches of step j (read from lz.j): pair stencil + alpha, biorthogonal update.
 cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
-                                const LzDev& lz, const LzVecs& vec, cudaStream_t st);
+                                const LzDev& lz, const LzVecs& vec, cudaStream_t st, int variant = -1);
 cudaError_t launch_lanczos_update(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, cudaStream_t st);
 // One step j (read from lz.j): pair stencil + alpha, then the biorthogonal update.
 cudaError_t launch_lanczos_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
@@ -91,6 +97,8 @@ namespace ovl {
 // (M - sigma_i) x = r share its Krylov space with residuals zeta^i_k r_k (collinear).
 // Status: 0 running, 1 breakdown, 2 converged, 3 empty (r = 0), 4 final update pending.
 constexpr int kMaxShifts = 128;
+constexpr double kFp32Floor = 2e-6;   // relative residual the FP32 iteration reaches by itself
+constexpr int kMaxRefineSweeps = 8;   // FP64 residual / FP32 correction rounds per shifted system
 struct MsDev {
   int nrhs = 0, s = 0, nblk = 0;
   int* k = nullptr;           // [nrhs] iterations done
@@ -113,6 +121,8 @@ struct MsVecs {
   void* ps = nullptr;          // [nrhs][s][12][V] shifted directions
   double2* X = nullptr;        // [nrhs][12][V] FP64 sum_i omega_i x^(i)
   double2* xp = nullptr;       // [nrhs][12][V] FP64 x_P (nullptr without deflation)
+  double2* xs = nullptr;       // [nrhs][s][12][V] FP64 per-shift solutions (refinement only; else X)
+  double2* r64 = nullptr;      // [nrhs][12][V] FP64 deflated residual r (refinement only)
 };
 
 cudaError_t launch_ms_start(const Geom& g, bool f64, const MsDev& ms, const MsVecs& v, const double2* b, int m,
@@ -121,6 +131,13 @@ cudaError_t launch_ms_start(const Geom& g, bool f64, const MsDev& ms, const MsVe
 // pair stencil, ev[1] after it, ev[2] before the direction update, ev[3] after it.
 cudaError_t launch_ms_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, const MsDev& ms,
                            const MsVecs& v, cudaStream_t st, cudaEvent_t* ev = nullptr);
+// Refinement helpers (one rhs `rhs`, one shift): res = r64 - (t2 - sigma x) with t2 = A^2 x
+// (native FP64), |res|^2 in out[0] (part/count scratch); x += e; X = sum_i omega_i xs_i.
+cudaError_t launch_ms_residual(const Geom& g, const double2* r64, const double2* t2, const double2* x, double sigma,
+                               double2* res, double* part, unsigned* count, double* out, cudaStream_t st);
+cudaError_t launch_axpy_f64(const Geom& g, int nrhs, const double2* e, double2* x, cudaStream_t st);
+cudaError_t launch_ms_combine_shifts(const Geom& g, int nrhs, int s, const double* omega, const double2* xs,
+                                     double2* X, cudaStream_t st);
 // x (canonical complex128) = x_P + AX (AX native FP64, = H_W(mu) X)
 cudaError_t launch_ms_finish(const Geom& g, int nrhs, const double2* ax, const double2* xp, double2* x, cudaStream_t st);
 

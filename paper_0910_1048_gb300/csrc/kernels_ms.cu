@@ -45,6 +45,9 @@ __global__ void __launch_bounds__(kBlock) k_ms_start(Geom g, MsDev ms, MsVecs v,
       }
       const size_t e = voff<R>(rhs, n) + (size_t)c * g.vol + s;
       if (v.xp) stc<double>(v.xp, e, x);
+      if (v.r64) stc<double>(v.r64, e, r);
+      if (v.xs)
+        for (int i = 0; i < ms.s; ++i) stc<double>(v.xs, ((size_t)rhs * ms.s + i) * n + (size_t)c * g.vol + s, mk(0.0, 0.0));
       stc<double>(v.X, e, mk(0.0, 0.0));
       cplx<R> rr = mk<R>((R)r.re, (R)r.im), rtt = mk<R>((R)rt.re, (R)rt.im);
       stc<R>((T*)v.r, e, rr);
@@ -327,7 +330,13 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs 
       T* pi = ps + (size_t)i * n;
       cplx<R> pv = ldc<R>(pi, e);
       double2 cx = coefx[i];
-      xa = xa + mk(cx.x, cx.y) * mk((double)pv.re, (double)pv.im);
+      if (v.xs) {  // keep x^(i) itself (FP64): x^(i) += alpha^i p^i
+        double2* xi = v.xs + ((size_t)rhs * ms.s + i) * n;
+        zd ai = ldc<double>(ms.ash, (size_t)rhs * ms.s + i);
+        stc<double>(xi, e, ldc<double>(xi, e) + ai * mk((double)pv.re, (double)pv.im));
+      } else {
+        xa = xa + mk(cx.x, cx.y) * mk((double)pv.re, (double)pv.im);
+      }
       if (act[i] == 1) {
         double2 cz = coefz[i], cb = coefb[i];
         cplx<R> nv = mk<R>((R)cz.x, (R)cz.y) * rv + mk<R>((R)cb.x, (R)cb.y) * pv;
@@ -363,7 +372,8 @@ static cudaError_t ms_step_t(const Geom& g, const Links& U, double m_w, double m
   dim3 pgrid((g.vol + kPairSites - 1) / kPairSites, ms.nrhs), pblock(kPairSites, 2);
   HopCoef<R> cp = hop_coef<R>(m_w, mu), cm = hop_coef<R>(m_w, -mu);
   dim3 sgrid((g.vol + kSplitSites - 1) / kSplitSites, ms.nrhs), sblock(kSplitSites, 8);
-  const bool split = use_split(g);
+  const int tv = tuned_pair_variant(g.vol, sizeof(R) == 8 ? 0 : LF);
+  const bool split = tv < 0 ? use_split(g) : tv == 1;
   if (ev) cudaEventRecord(ev[0], st);
   if (split)
     k_ms_pair_split<R, LF, 0><<<sgrid, sblock, 0, st>>>(g, U, cp, cm, ms, v);
@@ -386,6 +396,59 @@ cudaError_t launch_ms_step(const Geom& g, const Links& U, int lf, bool f64, doub
   if (f64) return ms_step_t<double, LINK_F64>(g, U, m_w, mu, ms, v, st, ev);
   if (lf == LINK_F16R12) return ms_step_t<float, LINK_F16R12>(g, U, m_w, mu, ms, v, st, ev);
   return ms_step_t<float, LINK_F32>(g, U, m_w, mu, ms, v, st, ev);
+}
+
+// res = r64 - (t2 - sigma x), |res|^2 -> out[0] (last block)
+__global__ void __launch_bounds__(kVecBlock) k_ms_residual(int vol, const double2* r64, const double2* t2,
+                                                           const double2* x, double sigma, double2* res,
+                                                           double* part, unsigned* count, double* out) {
+  const size_t n = (size_t)12 * vol;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0};
+  if (e < n) {
+    zd a = ldc<double>(r64, e) - (ldc<double>(t2, e) - sigma * ldc<double>(x, e));
+    stc<double>(res, e, a);
+    acc[0] = norm2(a);
+  }
+  block_sum<1>(acc);
+  if (publish_partials<1>(acc, part, count)) {
+    reduce_partials<1>(part, gridDim.x, acc);
+    if (lin_tid() == 0) out[0] = acc[0];
+  }
+}
+
+cudaError_t launch_ms_residual(const Geom& g, const double2* r64, const double2* t2, const double2* x, double sigma,
+                               double2* res, double* part, unsigned* count, double* out, cudaStream_t st) {
+  k_ms_residual<<<vec_blocks(g), kVecBlock, 0, st>>>(g.vol, r64, t2, x, sigma, res, part, count, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_axpy_f64(size_t n, const double2* e, double2* x) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) stc<double>(x, i, ldc<double>(x, i) + ldc<double>(e, i));
+}
+
+cudaError_t launch_axpy_f64(const Geom& g, int nrhs, const double2* e, double2* x, cudaStream_t st) {
+  size_t n = (size_t)12 * g.vol * nrhs;
+  k_axpy_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, e, x);
+  return cudaGetLastError();
+}
+
+__global__ void k_ms_combine_shifts(size_t n, int s, const double* omega, const double2* xs, double2* X) {
+  const int rhs = blockIdx.y;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  zd a = mk(0.0, 0.0);
+  for (int j = 0; j < s; ++j) a = a + omega[j] * ldc<double>(xs, ((size_t)rhs * s + j) * n + i);
+  stc<double>(X, (size_t)rhs * n + i, a);
+}
+
+cudaError_t launch_ms_combine_shifts(const Geom& g, int nrhs, int s, const double* omega, const double2* xs,
+                                     double2* X, cudaStream_t st) {
+  size_t n = (size_t)12 * g.vol;
+  dim3 grid((unsigned)((n + 255) / 256), nrhs);
+  k_ms_combine_shifts<<<grid, 256, 0, st>>>(n, s, omega, xs, X);
+  return cudaGetLastError();
 }
 
 __global__ void k_ms_finish(int vol, const double2* ax, const double2* xp, double2* x) {

@@ -254,6 +254,8 @@ struct RhsState {
   bool done = false;
   double hint_c = 0;               // (c, s) of the rational small sign, reused between checks
   int hint_s = 0;
+  double prev_est = 0;             // estimate and k of the previous evaluation (rate prediction)
+  int prev_eval_k = 0;
 };
 
 // Snapshot of rhs r from the pinned mirrors: H_k, y = sign(H_k) e_1, error estimate.
@@ -369,6 +371,43 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   if (m == 0) vec.xp = nullptr;
   OVL_CHECK_CUDA(launch_lanczos_start(g, f64, w->lz, vec, bd, m, lat->defl.R, lat->defl.L, w->lam_sign, w->dots, st));
   const Links U = lat->links();
+  // autotuner: on first use of (volume, precision) time both pair-stencil variants on this
+  // solve's step-1 data (the real step-1 launch below recomputes everything they write)
+  struct TuneArg {
+    const Geom* g;
+    const Links* U;
+    int lf;
+    bool f64;
+    const ovl_sign_params* p;
+    const LzDev* lz;
+    const LzVecs* vec;
+    cudaStream_t st;
+  } targ{&g, &U, lf, f64, p, &w->lz, &vec, st};
+  auto measure = [](void* v) -> int {
+    TuneArg& t = *(TuneArg*)v;
+    float best[2] = {1e30f, 1e30f};
+    cudaEvent_t a, b2;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1;
+    if (cudaEventCreate(&b2) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return -1;
+    }
+    bool ok = true;
+    for (int rep = 0; rep < 4 && ok; ++rep)
+      for (int var = 0; var < 2 && ok; ++var) {
+        ok = cudaEventRecord(a, t.st) == cudaSuccess &&
+             launch_lanczos_pair(*t.g, *t.U, t.lf, t.f64, t.p->m_W, t.p->mu, *t.lz, *t.vec, t.st, var) ==
+                 cudaSuccess &&
+             cudaEventRecord(b2, t.st) == cudaSuccess && cudaEventSynchronize(b2) == cudaSuccess;
+        float ms_ = 0;
+        if (ok && rep > 0 && cudaEventElapsedTime(&ms_, a, b2) == cudaSuccess) best[var] = std::min(best[var], ms_);
+      }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b2);
+    cudaGetLastError();
+    return ok ? (best[1] < best[0] ? 1 : 0) : -1;
+  };
+  tune_pair_variant(g.vol, f64 ? 0 : lf, measure, &targ);
   const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 20, kmax));
   // one step, with timing events around its two launches when `tev` is given
   auto step = [&](cudaEvent_t* tev) -> cudaError_t {
@@ -499,7 +538,7 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
           continue;
         }
       }
-      next_eval = std::max(evq[q] + chunk, (int)(1.1 * evq[q]));
+      const int jq = evq[q];
       bool all_done = true;
       std::vector<ovl_status> es_r(nrhs, OVL_OK);
       std::vector<int> evaluated;
@@ -538,6 +577,34 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
           if (ce) break;
         }
         all_done = all_done && s.done;
+      }
+      // next evaluation: where the slowest running rhs is predicted to reach tol if its estimate
+      // keeps falling geometrically (from its last two evaluations), clamped to [+chunk, x1.5];
+      // x1.25 while there is no rate yet
+      {
+        double jnext = 1.25 * jq;
+        bool have = false;
+        double jpred = jq;
+        for (int r = 0; r < nrhs; ++r) {
+          RhsState& s = rs[r];
+          if (s.done) continue;
+          if (s.prev_est > 0 && s.est < s.prev_est && s.prev_eval_k > 0 && s.k > s.prev_eval_k && s.est < 1e299) {
+            double rate = std::log(s.est / s.prev_est) / (s.k - s.prev_eval_k);  // < 0
+            double need = std::log(p->tol / s.est) / rate;                       // steps still needed
+            jpred = std::max(jpred, jq + std::max(0.0, need));
+            have = true;
+          } else {
+            have = false;
+            break;
+          }
+        }
+        if (have) jnext = std::min(1.5 * jq, std::max((double)jq + chunk, jpred));
+        next_eval = std::max(jq + chunk, (int)jnext);
+        for (int r = 0; r < nrhs; ++r)
+          if (!rs[r].done && rs[r].est < 1e299) {
+            rs[r].prev_est = rs[r].est;
+            rs[r].prev_eval_k = rs[r].k;
+          }
       }
       any_running = false;
       for (int r = 0; r < nrhs; ++r) any_running = any_running || w->h[q].status[r] == 0;

@@ -20,6 +20,12 @@ double zolotarev(int n, double lo, double hi, double* omega, double* sigma);
 
 struct MultiWS {
   int nrhs = 0, s = 0, f64 = -1, vol = 0, m = 0;
+  bool refine = false;
+  // refinement buffers (FP64, native layout): residual, two stencil temporaries, a canonical
+  // copy of the residual, reduction scratch, and the single-pole coefficients {1}, {0}
+  double2 *res = nullptr, *t1 = nullptr, *t2 = nullptr, *ecan = nullptr;
+  double *rpart = nullptr, *rout = nullptr, *one_zero = nullptr;
+  unsigned* rcount = nullptr;
   MsDev ms;
   MsVecs v;
   char* dev = nullptr;
@@ -56,10 +62,11 @@ void free_multi_ws(MultiWS* w) {
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m) {
+static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m, bool refine) {
   MultiWS* w = lat->mws;
   const int vol = lat->g.vol;
-  if (w && w->nrhs == nrhs && w->s == s && w->f64 == (int)f64 && w->vol == vol && w->m >= m) return OVL_OK;
+  if (w && w->nrhs == nrhs && w->s == s && w->f64 == (int)f64 && w->vol == vol && w->m >= m && w->refine == refine)
+    return OVL_OK;
   free_multi_ws(w);
   lat->mws = nullptr;
   w = new MultiWS();
@@ -68,6 +75,7 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m)
   w->f64 = f64;
   w->vol = vol;
   w->m = m;
+  w->refine = refine;
   const size_t n = (size_t)12 * vol, elt = f64 ? 16 : 8;
   const int nblk = partial_slots(lat->g);
   size_t off = 0;
@@ -97,6 +105,10 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m)
   size_t o_cn = take((size_t)nrhs * 4);
   size_t o_do = take((size_t)nrhs * 2 * std::max(m, 1) * 16);
   size_t o_ls = take((size_t)std::max(m, 1) * 8);
+  const size_t rn = refine ? n : 0;
+  size_t o_xs = take((size_t)nrhs * s * rn * 16), o_r64 = take((size_t)nrhs * rn * 16);
+  size_t o_res = take(rn * 16), o_t1 = take(rn * 16), o_t2 = take(rn * 16), o_ec = take(rn * 16);
+  size_t o_rp = take((size_t)vec_blocks(lat->g) * 8), o_ro = take(8), o_oz = take(16), o_rc = take(4);
   if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete w;
     set_error("apply_sign: cannot create a stream");
@@ -138,10 +150,25 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m)
   ms.count = (unsigned*)(b + o_cn);
   w->dots = (double2*)(b + o_do);
   w->lam_sign = (double*)(b + o_ls);
+  if (refine) {
+    w->v.xs = (double2*)(b + o_xs);
+    w->v.r64 = (double2*)(b + o_r64);
+    w->res = (double2*)(b + o_res);
+    w->t1 = (double2*)(b + o_t1);
+    w->t2 = (double2*)(b + o_t2);
+    w->ecan = (double2*)(b + o_ec);
+  }
+  w->rpart = (double*)(b + o_rp);
+  w->rout = (double*)(b + o_ro);
+  w->one_zero = (double*)(b + o_oz);
+  w->rcount = (unsigned*)(b + o_rc);
+  const double oz[2] = {1.0, 0.0};
   bool ev_ok = true;
   for (int q = 0; q < 2; ++q)
     for (int i = 0; i < 4; ++i) ev_ok = ev_ok && cudaEventCreate(&w->tev[q][i]) == cudaSuccess;
   if (!ev_ok || cudaMemsetAsync(ms.count, 0, (size_t)nrhs * 4, w->stream) != cudaSuccess ||
+      cudaMemsetAsync(w->rcount, 0, 4, w->stream) != cudaSuccess ||
+      cudaMemcpy(w->one_zero, oz, 16, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMallocHost(&w->h_status, (size_t)4 * nrhs * sizeof(int)) != cudaSuccess ||
       cudaEventCreateWithFlags(&w->ev[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&w->ev[1], cudaEventDisableTiming) != cudaSuccess) {
@@ -208,7 +235,11 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
                 "apply_sign: deflation set was computed for (m_W, mu) = (%g, %g)", lat->defl.m_w, lat->defl.mu);
     m = lat->defl.m;
   }
-  OVL_TRY(ensure_mws(lat, nrhs, s, f64, m));
+  // FP32 iterations reach about 1e-6; below that each shifted system is refined with FP64
+  // residuals (reliable updates): x^(i) kept in FP64, r^(i) = r - (A^2 - sigma_i) x^(i) from the
+  // FP64 stencil, corrections from FP32 single-shift BiCG solves on the same kernels
+  const bool refine = !f64 && p->tol < kFp32Floor;
+  OVL_TRY(ensure_mws(lat, nrhs, s, f64, m, refine));
   MultiWS* w = lat->mws;
   cudaStream_t st = w->stream;
   const Geom& g = lat->g;
@@ -219,7 +250,7 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
   for (int i = 0; i < s; ++i) ds[i] = sg[i] - s1;
   MsDev ms = w->ms;
   ms.sigma1 = s1;
-  ms.tol = p->tol;
+  ms.tol = refine ? kFp32Floor : p->tol;
   OVL_CHECK_CUDA(cudaEventRecord(w->ev[0], user_stream));
   OVL_CHECK_CUDA(cudaStreamWaitEvent(st, w->ev[0], 0));
   OVL_CHECK_CUDA(cudaMemcpyAsync(w->omega, om.data(), s * 8, cudaMemcpyHostToDevice, st));
@@ -234,12 +265,13 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
   if (m > 0) OVL_CHECK_CUDA(cudaMemcpyAsync(w->lam_sign, ls.data(), m * 8, cudaMemcpyHostToDevice, st));
   MsVecs v = w->v;
   if (m == 0) v.xp = nullptr;
+  if (!refine) v.xs = v.r64 = nullptr;
   OVL_CHECK_CUDA(launch_ms_start(g, f64, ms, v, bd, m, lat->defl.R, lat->defl.L, w->lam_sign, w->dots, st));
   const Links U = lat->links();
   const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 20, p->k_max));
   const bool use_graph = p->use_graphs != 0 && chunk > 1;
   if (use_graph && !(w->graph[0] && w->gchunk == chunk && w->g_lf == lf && w->g_mw == p->m_W && w->g_mu == p->mu &&
-                     w->g_s1 == s1 && w->g_tol == p->tol)) {
+                     w->g_s1 == s1 && w->g_tol == ms.tol)) {
     if (w->graph[0]) cudaGraphExecDestroy(w->graph[0]);
     w->graph[0] = nullptr;
     cudaGraph_t gr;
@@ -257,7 +289,7 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
     w->g_mw = p->m_W;
     w->g_mu = p->mu;
     w->g_s1 = s1;
-    w->g_tol = p->tol;
+    w->g_tol = ms.tol;
   }
   int launches = 1 + (m > 0 ? 1 : 0) + 2;  // start (+ deflation dots), final stencil and finish
   // a chunk = one iteration launched directly with timing events, then a graph of the rest
@@ -331,6 +363,61 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
   OVL_CHECK_CUDA(cudaMemcpy(act.data(), ms.active, act.size() * 4, cudaMemcpyDeviceToHost));
   OVL_CHECK_CUDA(cudaMemcpy(seed.data(), ms.seed, seed.size() * 16, cudaMemcpyDeviceToHost));
   OVL_CHECK_CUDA(cudaMemcpy(zeta.data(), ms.zeta, zeta.size() * 16, cudaMemcpyDeviceToHost));
+  // ---- reliable updates of every shifted system (reduced precision below kFp32Floor)
+  int ref_sweeps = 0, ref_iters = 0;
+  double ref_worst = 0;
+  if (refine) {
+    MsDev mi = ms;  // one-rhs, one-shift BiCG on the same buffers (the multishift pass is over)
+    mi.nrhs = 1;
+    mi.s = 1;
+    mi.omega = w->one_zero;
+    mi.dsig = w->one_zero + 1;
+    MsVecs vi = v;
+    vi.xs = vi.r64 = vi.xp = nullptr;
+    for (int r = 0; r < nrhs && ref_worst >= 0; ++r) {
+      const double r0 = seed[(size_t)r * 8 + 4].x;
+      for (int i = 0; i < s; ++i) {
+        double2* xi = v.xs + ((size_t)r * s + i) * n;
+        double resn = 0;
+        for (int sweep = 0;; ++sweep) {
+          OVL_CHECK_CUDA(launch_dslash(g, U, LINK_F64, true, p->m_W, p->mu, false, true, true, true, 1, xi, w->t1, st));
+          OVL_CHECK_CUDA(launch_dslash(g, U, LINK_F64, true, p->m_W, p->mu, false, true, true, true, 1, w->t1, w->t2, st));
+          OVL_CHECK_CUDA(launch_ms_residual(g, v.r64 + (size_t)r * n, w->t2, xi, sg[i], w->res, w->rpart, w->rcount,
+                                            w->rout, st));
+          launches += 3;
+          double rr = 0;
+          OVL_CHECK_CUDA(cudaMemcpyAsync(&rr, w->rout, 8, cudaMemcpyDeviceToHost, st));
+          OVL_CHECK_CUDA(cudaStreamSynchronize(st));
+          resn = std::sqrt(rr);
+          if (!(resn > p->tol * r0) || sweep >= kMaxRefineSweeps) break;
+          ++ref_sweeps;
+          // FP32 correction: (A^2 - sigma_i) e = res to a relative accuracy the FP32 iteration reaches
+          mi.sigma1 = sg[i];
+          mi.tol = std::max(2.0 * kFp32Floor, std::min(0.5, 0.3 * p->tol * r0 / resn));
+          OVL_CHECK_CUDA(launch_from_native(g, 1, true, w->res, true, w->ecan, st));
+          OVL_CHECK_CUDA(launch_ms_start(g, false, mi, vi, w->ecan, 0, nullptr, nullptr, nullptr, nullptr, st));
+          launches += 2;
+          int it = 0, stat = 0;
+          while (it < p->k_max) {
+            int ns = std::min(chunk, p->k_max - it);
+            for (int q = 0; q < ns; ++q) OVL_CHECK_CUDA(launch_ms_step(g, U, lf, false, p->m_W, p->mu, mi, vi, st));
+            it += ns;
+            launches += 4 * ns;
+            OVL_CHECK_CUDA(cudaMemcpyAsync(&stat, mi.status, 4, cudaMemcpyDeviceToHost, st));
+            OVL_CHECK_CUDA(cudaStreamSynchronize(st));
+            if (stat != 0) break;
+          }
+          ref_iters += it;
+          if (stat == 1) break;  // breakdown of the correction solve: keep the best x^(i)
+          OVL_CHECK_CUDA(launch_axpy_f64(g, 1, vi.X, xi, st));
+          launches += 1;
+        }
+        ref_worst = std::max(ref_worst, r0 > 0 ? resn / r0 : 0.0);
+      }
+    }
+    OVL_CHECK_CUDA(launch_ms_combine_shifts(g, nrhs, s, w->omega, v.xs, v.X, st));
+    launches += 1;
+  }
   // x = x_P + A X (FP64 stencil, native layout)
   OVL_CHECK_CUDA(launch_dslash(g, U, LINK_F64, true, p->m_W, p->mu, false, true, true, true, nrhs, v.X, w->ax, st));
   double2* xd = p->host_io ? w->xdev : x;
@@ -353,11 +440,15 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
       for (int i = 0; i < s; ++i) all = all && act[(size_t)r * s + i] != 1;
       if (all) rs = OVL_OK;
     }
+    if (refine) {  // the refined true residuals decide
+      worst = ref_worst;
+      rs = ref_worst <= p->tol ? OVL_OK : OVL_ENOCONV;
+    }
     if (rs != OVL_OK && result == OVL_OK) result = rs;
     if (info) {
       info[r].status = rs;
-      info[r].iterations = hk[r];
-      info[r].matvecs = 4 * hk[r] + 1;
+      info[r].iterations = hk[r] + ref_iters;
+      info[r].matvecs = 4 * (hk[r] + ref_iters) + 1 + 2 * (ref_sweeps + s);
       info[r].poles = s;
       info[r].est_error = (stt == 3 ? 0.0 : worst) + bound;
       info[r].t_total_ms = t_total;

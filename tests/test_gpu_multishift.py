@@ -164,3 +164,21 @@ def test_equal_k_parity_1616(ovl, ctx):
     xo = a(np.tensordot(w, xs, axes=1))
     assert _rel(x.ravel(), xo) < 1e-9
     ovl.ovl_destroy_lattice(lat)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_reliable_updates_reach_fp64_accuracy(ovl, p4m, prec):
+    """FP32 vectors (and FP16 12-real links) with FP64 reliable updates: below the FP32 floor
+    every shifted system is refined with FP64 residuals, so the result matches the FP64
+    rational result (dense g(A) b) to the requested tolerance."""
+    p, lat, lo, hi = p4m
+    eps = 1e-10
+    pr = ovl.OVL_PREC_F32 if prec == "f32" else ovl.OVL_PREC_F32_F16LINKS
+    st, info, x = _solve(ovl, lat, p["b"], mu=0.3, tol=eps, k_max=5000, spec_lo=0.99 * lo, spec_hi=1.01 * hi,
+                         precision=pr)
+    assert st == ovl.OVL_OK, info
+    assert info[0]["residual"] <= eps
+    s, c, w, sg = rational.neuberger_for_spectrum(0.99 * lo, 1.01 * hi, eps)
+    xg = lanczos.rational_sign_dense(p["h"], p["b"].ravel(), w, sg)
+    assert _rel(x.ravel(), xg) < 2e-9
+    assert _rel(x.ravel(), p["xstar"].ravel()) < 1e-8
