@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "kernels.h"
+#include "stoprule.h"
 
 namespace ovl {
 
@@ -59,9 +60,10 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Rhs {
   int k = 0;
-  std::vector<std::complex<double>> y;
+  std::vector<std::complex<double>> y, yprev;
   double est = 1e300, hint_c = 0;
   int hint_s = 0;
+  StopTrack trk;
   ovl_status status = OVL_PENDING;
   bool done = false;
 };
@@ -117,6 +119,10 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   size_t o_pa = take((size_t)nrhs * std::max(m, 1) * nblk * 4 * 8), o_cn = take((size_t)nrhs * 4);
   size_t o_do = take((size_t)nrhs * 2 * std::max(m, 1) * 16), o_ls = take((size_t)std::max(m, 1) * 8);
   size_t o_co = take((size_t)nrhs * kmax * 16), o_kr = take((size_t)nrhs * 4);
+  // buffers of the stopping estimate (the same kernel and rule as ovl_apply_sign)
+  size_t o_n1 = take((size_t)nrhs * kmax * 16), o_n2 = take((size_t)nrhs * kmax * 16);
+  size_t o_nk = take((size_t)nrhs * 4), o_np = take((size_t)nrhs * 2 * vec_blocks(g) * 8);
+  size_t o_nc = take((size_t)nrhs * 4), o_no = take((size_t)nrhs * 2 * 8);
   if (off > kStaticScratchBytes) {
     set_error("apply_sign_noalloc: needs %zu bytes of scratch, the static array holds %zu (64 MiB); "
               "use ovl_apply_sign or a smaller k_max / lattice / nrhs", off, kStaticScratchBytes);
@@ -147,8 +153,14 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   double* lam_sign = (double*)(base + o_ls);
   double2* coef = (double2*)(base + o_co);
   int* kr = (int*)(base + o_kr);
+  double2 *nd1 = (double2*)(base + o_n1), *nd2 = (double2*)(base + o_n2);
+  int* nkr = (int*)(base + o_nk);
+  double* npart = (double*)(base + o_np);
+  unsigned* ncount = (unsigned*)(base + o_nc);
+  double* nout = (double*)(base + o_no);
   // the array keeps the previous call's contents: the block counters must start at zero
   OVL_CHECK_CUDA(cudaMemsetAsync(lz.count, 0, (size_t)nrhs * 4, st));
+  OVL_CHECK_CUDA(cudaMemsetAsync(ncount, 0, (size_t)nrhs * 4, st));
   std::vector<double> ls(std::max(m, 1));
   for (int i = 0; i < m; ++i) ls[i] = lat->defl.lam[2 * i] >= 0 ? 1.0 : -1.0;
   if (m > 0) OVL_CHECK_CUDA(cudaMemcpyAsync(lam_sign, ls.data(), m * 8, cudaMemcpyHostToDevice, st));
@@ -197,18 +209,42 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
     ovl_status e = small_sign(k, al.data(), be.data(), de.data(), y.data(), 0, &s.hint_c, &s.hint_s);
     t_small += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
     if (e != OVL_OK) return e;
-    double ny = 0, dif = 0;
-    for (int i = 0; i < k; ++i) {
-      ny += std::norm(y[i]);
-      std::complex<double> prev = i < (int)s.y.size() ? s.y[i] : 0.0;
-      dif += std::abs(y[i] - prev) * h_vn[r * ks + i + 1];
-    }
-    s.est = s.y.empty() ? 1e300 : dif / std::sqrt(ny);
+    s.est = 1e300;
+    s.yprev.swap(s.y);
     s.y.swap(y);
     s.k = k;
     return OVL_OK;
   };
-  int queued = 0, launches = 1 + (m > 0 ? 1 : 0) + 1;
+  // relative change ||V (y_k - [y_k'; 0])|| / ||V y_k|| of the evaluated rhs, on the GPU
+  auto changes = [&](const std::vector<int>& which) -> ovl_status {
+    std::vector<double2> d1((size_t)nrhs * kmax, make_double2(0, 0)), d2 = d1;
+    std::vector<int> kk(nrhs, 0);
+    bool any = false;
+    for (int r : which) {
+      Rhs& s = rs[r];
+      if (s.k < 1 || s.yprev.empty()) continue;
+      kk[r] = s.k;
+      any = true;
+      for (int i = 0; i < s.k; ++i) {
+        std::complex<double> pv = i < (int)s.yprev.size() ? s.yprev[i] : 0.0;
+        std::complex<double> a = (s.y[i] - pv) * h_sv[r * ks + i + 1], c = s.y[i] * h_sv[r * ks + i + 1];
+        d1[(size_t)r * kmax + i] = make_double2(a.real(), a.imag());
+        d2[(size_t)r * kmax + i] = make_double2(c.real(), c.imag());
+      }
+    }
+    if (!any) return OVL_OK;
+    OVL_CHECK_CUDA(cudaMemcpyAsync(nd1, d1.data(), d1.size() * 16, cudaMemcpyHostToDevice, st));
+    OVL_CHECK_CUDA(cudaMemcpyAsync(nd2, d2.data(), d2.size() * 16, cudaMemcpyHostToDevice, st));
+    OVL_CHECK_CUDA(cudaMemcpyAsync(nkr, kk.data(), nrhs * 4, cudaMemcpyHostToDevice, st));
+    OVL_CHECK_CUDA(launch_lanczos_vnorms(g, f64, lz, vec, nkr, nd1, nd2, kmax, npart, ncount, nout, st));
+    std::vector<double> out((size_t)nrhs * 2);
+    OVL_CHECK_CUDA(cudaMemcpyAsync(out.data(), nout, out.size() * 8, cudaMemcpyDeviceToHost, st));
+    OVL_CHECK_CUDA(cudaStreamSynchronize(st));
+    for (int r : which)
+      if (kk[r] > 0) rs[r].est = out[2 * r + 1] > 0 ? std::sqrt(out[2 * r] / out[2 * r + 1]) : 1e300;
+    return OVL_OK;
+  };
+  int queued = 0, launches = 1 + (m > 0 ? 1 : 0) + 1, next_eval = 0;
   while (queued < kmax) {
     int ns = std::min(chunk, kmax - queued);
     for (int i = 0; i < ns; ++i) OVL_CHECK_CUDA(launch_lanczos_step(g, U, lf, f64, p->m_W, p->mu, lz, vec, st));
@@ -216,26 +252,56 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
     launches += 2 * ns;
     if (fixed) continue;
     OVL_CHECK_CUDA(snapshot());
+    const bool final_snapshot = queued >= kmax;
+    if (!final_snapshot && queued < next_eval) {
+      bool all_stopped = true;  // evaluate early only if every running rhs stopped on the device
+      for (int r = 0; r < nrhs; ++r) all_stopped = all_stopped && (rs[r].done || h_st[r] != 0);
+      if (!all_stopped) continue;
+    }
+    std::vector<ovl_status> es(nrhs, OVL_OK);
+    std::vector<int> evaluated;
+    for (int r = 0; r < nrhs; ++r) {
+      if (rs[r].done) continue;
+      es[r] = evaluate(r);
+      if (es[r] == OVL_OK) evaluated.push_back(r);
+    }
+    OVL_TRY(changes(evaluated));
     bool all = true;
     for (int r = 0; r < nrhs; ++r) {
       Rhs& s = rs[r];
       if (s.done) continue;
-      ovl_status e = evaluate(r);
-      if (e != OVL_OK) {
-        s.status = e, s.done = true;
+      bool converged = false;
+      if (es[r] == OVL_OK && h_st[r] == 0) {
+        stop_record(s.trk, s.k, s.est < 1e299 ? s.est : -1.0);
+        s.est = s.trk.err;
+        converged = stop_converged(s.trk, p->tol);
+      }
+      if (es[r] != OVL_OK) {
+        s.status = es[r], s.done = true;
       } else if (h_st[r] == 3) {
         s.status = OVL_OK, s.done = true;
       } else if (h_st[r] == 1) {
         s.status = OVL_EBREAKDOWN, s.done = true;
-      } else if (s.est <= p->tol) {
+      } else if (converged) {
         s.status = OVL_OK, s.done = true;
-      } else if (queued >= kmax) {
+      } else if (final_snapshot) {
         s.status = OVL_ENOCONV, s.done = true;
       }
       if (s.done && h_st[r] == 0) OVL_CHECK_CUDA(cudaMemsetAsync(lz.status + r, 2, sizeof(int), st));
       all = all && s.done;
     }
     if (all) break;
+    double need = 0;
+    for (int r = 0; r < nrhs; ++r) {
+      if (rs[r].done) continue;
+      double n_r = stop_predict(rs[r].trk, p->tol);
+      if (n_r < 0) {
+        need = -1;
+        break;
+      }
+      need = std::max(need, n_r);
+    }
+    next_eval = stop_next_eval(queued, chunk, need);
   }
   if (fixed) {
     OVL_CHECK_CUDA(snapshot());

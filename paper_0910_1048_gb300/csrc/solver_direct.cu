@@ -14,6 +14,7 @@
 #include <cstdlib>
 
 #include "kernels.h"
+#include "stoprule.h"
 
 namespace ovl {
 
@@ -254,8 +255,7 @@ struct RhsState {
   bool done = false;
   double hint_c = 0;               // (c, s) of the rational small sign, reused between checks
   int hint_s = 0;
-  double prev_est = 0;             // estimate and k of the previous evaluation (rate prediction)
-  int prev_eval_k = 0;
+  StopTrack trk;                   // rate-corrected stopping estimate (stoprule.h)
 };
 
 // Snapshot of rhs r from the pinned mirrors: H_k, y = sign(H_k) e_1, error estimate.
@@ -555,6 +555,12 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
         RhsState& s = rs[r];
         if (s.done) continue;
         ovl_status es = es_r[r];
+        bool converged = false;
+        if (es == OVL_OK && w->h[q].status[r] == 0) {
+          stop_record(s.trk, s.k, s.est < 1e299 ? s.est : -1.0);
+          s.est = s.trk.err;
+          converged = stop_converged(s.trk, p->tol);
+        }
         if (es != OVL_OK) {
           s.status = es;
           s.done = true;
@@ -564,7 +570,7 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
         } else if (w->h[q].status[r] == 1) {
           s.status = OVL_EBREAKDOWN;
           s.done = true;
-        } else if (s.est <= p->tol) {
+        } else if (converged) {
           s.status = OVL_OK;
           s.done = true;
         } else if (final_snapshot) {
@@ -578,33 +584,19 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
         }
         all_done = all_done && s.done;
       }
-      // next evaluation: where the slowest running rhs is predicted to reach tol if its estimate
-      // keeps falling geometrically (from its last two evaluations), clamped to [+chunk, x1.5];
-      // x1.25 while there is no rate yet
+      // next evaluation: where the slowest running rhs is predicted to reach tol / 2
       {
-        double jnext = 1.25 * jq;
-        bool have = false;
-        double jpred = jq;
+        double need = 0;
         for (int r = 0; r < nrhs; ++r) {
-          RhsState& s = rs[r];
-          if (s.done) continue;
-          if (s.prev_est > 0 && s.est < s.prev_est && s.prev_eval_k > 0 && s.k > s.prev_eval_k && s.est < 1e299) {
-            double rate = std::log(s.est / s.prev_est) / (s.k - s.prev_eval_k);  // < 0
-            double need = std::log(p->tol / s.est) / rate;                       // steps still needed
-            jpred = std::max(jpred, jq + std::max(0.0, need));
-            have = true;
-          } else {
-            have = false;
+          if (rs[r].done) continue;
+          double n_r = stop_predict(rs[r].trk, p->tol);
+          if (n_r < 0) {
+            need = -1;
             break;
           }
+          need = std::max(need, n_r);
         }
-        if (have) jnext = std::min(1.5 * jq, std::max((double)jq + chunk, jpred));
-        next_eval = std::max(jq + chunk, (int)jnext);
-        for (int r = 0; r < nrhs; ++r)
-          if (!rs[r].done && rs[r].est < 1e299) {
-            rs[r].prev_est = rs[r].est;
-            rs[r].prev_eval_k = rs[r].k;
-          }
+        next_eval = stop_next_eval(jq, chunk, need);
       }
       any_running = false;
       for (int r = 0; r < nrhs; ++r) any_running = any_running || w->h[q].status[r] == 0;
