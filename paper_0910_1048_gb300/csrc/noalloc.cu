@@ -244,7 +244,7 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
       if (kk[r] > 0) rs[r].est = out[2 * r + 1] > 0 ? std::sqrt(out[2 * r] / out[2 * r + 1]) : 1e300;
     return OVL_OK;
   };
-  int queued = 0, launches = 1 + (m > 0 ? 1 : 0) + 1, next_eval = 0;
+  int queued = 0, launches = 1 + (m > 0 ? 1 : 0) + 1;
   while (queued < kmax) {
     int ns = std::min(chunk, kmax - queued);
     for (int i = 0; i < ns; ++i) OVL_CHECK_CUDA(launch_lanczos_step(g, U, lf, f64, p->m_W, p->mu, lz, vec, st));
@@ -253,28 +253,25 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
     if (fixed) continue;
     OVL_CHECK_CUDA(snapshot());
     const bool final_snapshot = queued >= kmax;
-    if (!final_snapshot && queued < next_eval) {
-      bool all_stopped = true;  // evaluate early only if every running rhs stopped on the device
-      for (int r = 0; r < nrhs; ++r) all_stopped = all_stopped && (rs[r].done || h_st[r] != 0);
-      if (!all_stopped) continue;
-    }
+    std::vector<int> todo;  // same per-rhs schedule as the allocating driver
+    for (int r = 0; r < nrhs; ++r)
+      if (!rs[r].done && stop_due(rs[r].trk, queued, final_snapshot, h_st[r] != 0)) todo.push_back(r);
+    if (todo.empty()) continue;
     std::vector<ovl_status> es(nrhs, OVL_OK);
     std::vector<int> evaluated;
-    for (int r = 0; r < nrhs; ++r) {
-      if (rs[r].done) continue;
+    for (int r : todo) {
       es[r] = evaluate(r);
       if (es[r] == OVL_OK) evaluated.push_back(r);
     }
     OVL_TRY(changes(evaluated));
-    bool all = true;
-    for (int r = 0; r < nrhs; ++r) {
+    for (int r : todo) {
       Rhs& s = rs[r];
-      if (s.done) continue;
       bool converged = false;
       if (es[r] == OVL_OK && h_st[r] == 0) {
         stop_record(s.trk, s.k, s.est < 1e299 ? s.est : -1.0);
         s.est = s.trk.err;
         converged = stop_converged(s.trk, p->tol);
+        stop_schedule(s.trk, queued, chunk, p->tol);
       }
       if (es[r] != OVL_OK) {
         s.status = es[r], s.done = true;
@@ -288,20 +285,10 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
         s.status = OVL_ENOCONV, s.done = true;
       }
       if (s.done && h_st[r] == 0) OVL_CHECK_CUDA(cudaMemsetAsync(lz.status + r, 2, sizeof(int), st));
-      all = all && s.done;
     }
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r) all = all && rs[r].done;
     if (all) break;
-    double need = 0;
-    for (int r = 0; r < nrhs; ++r) {
-      if (rs[r].done) continue;
-      double n_r = stop_predict(rs[r].trk, p->tol);
-      if (n_r < 0) {
-        need = -1;
-        break;
-      }
-      need = std::max(need, n_r);
-    }
-    next_eval = stop_next_eval(queued, chunk, need);
   }
   if (fixed) {
     OVL_CHECK_CUDA(snapshot());

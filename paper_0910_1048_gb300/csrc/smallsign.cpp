@@ -36,6 +36,11 @@ namespace ovl {
 
 using cz = std::complex<double>;
 
+// Number of small-sign evaluations the calling thread runs side by side (set by a driver that
+// evaluates several right-hand sides at once); each gets its share of the host threads.
+thread_local int g_sign_concurrency = 1;
+void set_sign_concurrency(int n) { g_sign_concurrency = std::max(1, n); }
+
 namespace {
 
 struct Rot {
@@ -380,7 +385,7 @@ void rational_apply(int k, const cz* al, const cz* be, const cz* de, double c, i
   const double c2 = c * c;
   // the s shifted solves are independent: split them over host threads, each summing its
   // own shifts in order, then add the per-thread sums in thread order (deterministic)
-  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int hw = std::max(1, (int)std::thread::hardware_concurrency() / std::max(1, g_sign_concurrency));
   const int nth = std::max(1, std::min({hw, 16, s, (int)((size_t)s * k / 20000 + 1)}));
   std::vector<std::vector<cz>> part(nth, std::vector<cz>(k, 0.0));
   auto work = [&](int tid) {

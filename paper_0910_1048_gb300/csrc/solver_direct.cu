@@ -12,6 +12,7 @@
 #include <chrono>
 #include <complex>
 #include <cstdlib>
+#include <thread>
 
 #include "kernels.h"
 #include "stoprule.h"
@@ -21,6 +22,7 @@ namespace ovl {
 ovl_status small_sign(int k, const std::complex<double>* al, const std::complex<double>* be,
                       const std::complex<double>* de, std::complex<double>* y, int method, double* hint_c,
                       int* hint_s);
+void set_sign_concurrency(int n);
 
 struct DirectWS {
   int nrhs = 0, kmax = 0, f64 = -1, m = 0, vol = 0;
@@ -493,7 +495,6 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   cudaError_t ce = cudaSuccess;
   int qlast = 0;
   bool any_running = true;  // a chunk launched while some rhs ran did real work
-  int next_eval = 0;        // next step count at which sign(H_j) e_1 is evaluated
   if (fixed) {
     while (queued < kmax && ce == cudaSuccess) {
       int ns = std::min(chunk, kmax - queued);
@@ -525,41 +526,49 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
       if (any_running) sample(q);
       qlast = q;
       const bool final_snapshot = evq[q] >= kmax;
-      // geometric schedule: evaluate sign(H_j) e_1 when j passed the last evaluation by 10%
-      // (the host cost grows with j while the estimate changes slowly)
-      if (!final_snapshot && evq[q] < next_eval) {
+      const int jq = evq[q];
+      std::vector<int> todo;  // rhs due for an evaluation of sign(H_j) e_1 at this snapshot
+      for (int r = 0; r < nrhs; ++r)
+        if (!rs[r].done && stop_due(rs[r].trk, jq, final_snapshot, w->h[q].status[r] != 0)) todo.push_back(r);
+      if (todo.empty()) {
         any_running = false;
         for (int r = 0; r < nrhs; ++r) any_running = any_running || w->h[q].status[r] == 0;
-        if (!any_running) {
-          bool all = true;  // every rhs retired or broke down on the device: evaluate now
-          for (int r = 0; r < nrhs; ++r) all = all && (rs[r].done || w->h[q].status[r] != 0);
-          if (!all) continue;
-        } else {
-          continue;
-        }
+        continue;
       }
-      const int jq = evq[q];
       bool all_done = true;
       std::vector<ovl_status> es_r(nrhs, OVL_OK);
       std::vector<int> evaluated;
-      for (int r = 0; r < nrhs; ++r) {
-        if (rs[r].done) continue;
-        es_r[r] = evaluate_rhs(w, q, r, rs[r], &t_small);
-        if (es_r[r] == OVL_OK) evaluated.push_back(r);
+      if (todo.size() <= 1) {
+        for (int r : todo) es_r[r] = evaluate_rhs(w, q, r, rs[r], &t_small);
+      } else {  // several right-hand sides: their sign(H_k) e_1 are independent, run them side by side
+        std::vector<double> ts(nrhs, 0.0);
+        std::vector<std::thread> th;
+        const int conc = (int)todo.size();
+        for (int r : todo)
+          th.emplace_back([&, r] {
+            set_sign_concurrency(conc);
+            es_r[r] = evaluate_rhs(w, q, r, rs[r], &ts[r]);
+          });
+        for (auto& t : th) t.join();
+        double tmax = 0;
+        for (double t : ts) tmax = std::max(tmax, t);
+        t_small += tmax;
       }
+      for (int r : todo)
+        if (es_r[r] == OVL_OK) evaluated.push_back(r);
       {
         ovl_status est_st = estimate_changes(w, g, f64, vec, q, rs, evaluated);
         if (est_st != OVL_OK) return est_st;
       }
-      for (int r = 0; r < nrhs; ++r) {
+      for (int r : todo) {
         RhsState& s = rs[r];
-        if (s.done) continue;
         ovl_status es = es_r[r];
         bool converged = false;
         if (es == OVL_OK && w->h[q].status[r] == 0) {
           stop_record(s.trk, s.k, s.est < 1e299 ? s.est : -1.0);
           s.est = s.trk.err;
           converged = stop_converged(s.trk, p->tol);
+          stop_schedule(s.trk, jq, chunk, p->tol);
         }
         if (es != OVL_OK) {
           s.status = es;
@@ -582,22 +591,8 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
           ce = cudaMemsetAsync(w->lz.status + r, 2, sizeof(int), st);
           if (ce) break;
         }
-        all_done = all_done && s.done;
       }
-      // next evaluation: where the slowest running rhs is predicted to reach tol / 2
-      {
-        double need = 0;
-        for (int r = 0; r < nrhs; ++r) {
-          if (rs[r].done) continue;
-          double n_r = stop_predict(rs[r].trk, p->tol);
-          if (n_r < 0) {
-            need = -1;
-            break;
-          }
-          need = std::max(need, n_r);
-        }
-        next_eval = stop_next_eval(jq, chunk, need);
-      }
+      for (int r = 0; r < nrhs; ++r) all_done = all_done && rs[r].done;
       any_running = false;
       for (int r = 0; r < nrhs; ++r) any_running = any_running || w->h[q].status[r] == 0;
       if (all_done || ce) break;

@@ -8,9 +8,10 @@
 // D_i = k_i - k_{i-1}, and the error at k_i is estimated as
 //     e_i = d_i rho^{D_i} / (1 - rho^{D_i}),
 // with log rho from the last two changes (log(d_i/d_{i-1}) over the mean spacing). A rhs stops
-// when d_i <= tol (the change itself is small) or, with a rate, when 2 e_i <= tol. The next
-// evaluation goes where the slowest rhs is predicted to reach tol/2, within [k+chunk, 1.5 k];
-// without a rate it is 1.25 k.
+// when d_i <= tol (the change itself is small) or, with a rate, when 2 e_i <= tol. Each rhs keeps
+// its own schedule: its next evaluation goes where it is predicted to reach tol/2, within
+// [k+chunk, 1.5 k]; without a rate it is 1.25 k. A rhs therefore stops at the same k whether it
+// is solved alone or in a batch.
 #pragma once
 
 #include <algorithm>
@@ -24,6 +25,7 @@ struct StopTrack {
   int dk_prev = 0;       // its spacing
   double log_rho = 0;    // per-step log rate (< 0 when known)
   double err = 1e300;    // current error estimate
+  int next = 0;          // step count at which this rhs is evaluated next
 };
 
 // Record evaluation at step k with relative change d (d < 0: first evaluation, no change yet).
@@ -61,6 +63,17 @@ inline double stop_predict(const StopTrack& t, double tol) {
 inline int stop_next_eval(int k, int chunk, double steps_needed) {
   double jn = steps_needed < 0 ? 1.25 * k : std::min(1.5 * k, std::max((double)k + chunk, k + steps_needed));
   return std::max(k + chunk, (int)jn);
+}
+
+// Schedule the next evaluation of a rhs evaluated at step k.
+inline void stop_schedule(StopTrack& t, int k, int chunk, double tol) {
+  t.next = stop_next_eval(k, chunk, stop_predict(t, tol));
+}
+
+// Is a rhs due for evaluation at a snapshot of k steps? (Always at the last snapshot, and at once
+// when it stopped on the device.)
+inline bool stop_due(const StopTrack& t, int k, bool final_snapshot, bool stopped_on_device) {
+  return final_snapshot || stopped_on_device || k >= t.next;
 }
 
 }  // namespace ovl
