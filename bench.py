@@ -39,11 +39,24 @@ WORKLOADS = {
     # k <= 600 does not reach 1e-8 at mu = 0.3 with 16 deflated vectors on this ensemble, so
     # k_max is 2000 and the k actually used is reported.
     "lattice8_mu0-0.1-0.3_defl16_direct_f64": dict(dims=(8, 8, 8, 8), mus=(0.0, 0.1, 0.3), m=16, method="direct",
-                                                     precision="f64", tol=1e-8, k_max=2000),
+                                                     precision="f64", tol=1e-8, k_max=2000,
+                                                     mixed="lattice8_mu0-0.1-0.3_defl16_multishift_f16links_f64rel"),
     # same lattice and deflation, rational variant (Algorithm 3 + Neuberger, Eq. no_of_poles)
     "lattice8_mu0-0.1-0.3_defl16_multishift_f64": dict(dims=(8, 8, 8, 8), mus=(0.0, 0.1, 0.3), m=16,
                                                          method="multishift", precision="f64", tol=1e-8,
                                                          k_max=5000),
+    # the same step in mixed precision: multishift BiCG with FP16 12-real links and FP32 vectors,
+    # FP64 reliable updates down to the metric's 1e-8 (SURVEY's precision item (1))
+    "lattice8_mu0-0.1-0.3_defl16_multishift_f16links_f64rel": dict(dims=(8, 8, 8, 8), mus=(0.0, 0.1, 0.3), m=16,
+                                                                     method="multishift", precision="f16",
+                                                                     tol=1e-8, k_max=5000),
+    "lattice8_mu0-0.1-0.3_defl16_multishift_f32_f64rel": dict(dims=(8, 8, 8, 8), mus=(0.0, 0.1, 0.3), m=16,
+                                                                method="multishift", precision="f32",
+                                                                tol=1e-8, k_max=5000),
+    # 16^4, mu = 0.2, 16 Gaussian sources in one batch sharing the links, FP32 vectors with FP64
+    # recurrence scalars and sign(H_k); FP32 vectors bound the attainable accuracy near 1e-5
+    "lattice16_mu0.2_nrhs16_direct_f32": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0, method="direct",
+                                              precision="f32", tol=1e-5, k_max=1500, nrhs=16),
     # 4^4 smoke-sized case (the oracle finishes it in seconds)
     "lattice4_mu0.3_direct_f64": dict(dims=(4, 4, 4, 4), mus=(0.3,), m=0, method="direct", precision="f64",
                                       tol=1e-8, k_max=1200),
@@ -56,8 +69,16 @@ DEFAULT_WORKLOAD = "lattice8_mu0-0.1-0.3_defl16_direct_f64"
 PAIR_BYTES_PER_SITE = {"f64": 2 * 192 + 576 + 2 * 192, "f32": 2 * 96 + 288 + 2 * 96, "f16": 2 * 96 + 96 + 2 * 96}
 PAIR_FLOPS_PER_SITE = 2 * 1368
 
-# FP64 FMA throughput of this machine's GB300 (measured with an FMA-chain probe) in TFLOP/s
+# FP64 FMA throughput of this machine's GB300 in TFLOP/s (the FMA-chain probe in csrc/probe/; the
+# bench runs the probe itself and uses this value only when the probe library is missing)
 FP64_PEAK_TFLOPS = 1.256
+
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture (cold L2, every
+# pass flushed), keyed (kernel, precision, lattice, nrhs); the captures and their commands are in
+# profiles/. An entry is removed when its kernel changes.
+TRAFFIC = {
+    ("k_lz_pair", "f64", (8, 8, 8, 8), 1): 4045184,  # k_lz_pair_split<double>, the autotuned variant at 8^4
+}
 
 
 def _peaks():
@@ -149,6 +170,9 @@ def throughput(steps: int, solves_per_step: int, world: int, max_ms: float) -> f
     return steps * solves_per_step * world / (max_ms / 1e3)
 
 
+_SETUP_MEMO: dict = {}  # spectral set-up already computed in this process
+
+
 def _setup(ovl, ctx, wl, rng_seed=0, cache=None):
     """Lattice, links, sources and per-mu deflation sets (untimed set-up). With `cache`, the
     spectral set-up is loaded from / saved to that .npz file (same workload inputs)."""
@@ -160,10 +184,10 @@ def _setup(ovl, ctx, wl, rng_seed=0, cache=None):
     lat = ovl.ovl_create_lattice(ctx, dims, -1)
     ovl.ovl_set_links(lat, u, ovl.OVL_F64 | ovl.OVL_F32 | ovl.OVL_F16R12)
     b = synth.gaussian_source(dims, 1000)
-    stored = {}
+    stored = _SETUP_MEMO
     if cache and os.path.exists(cache):
         with np.load(cache) as z:
-            stored = {k: z[k] for k in z.files}
+            stored.update({k: z[k] for k in z.files})
     per_mu = []
     changed = False
     for i, mu in enumerate(wl["mus"]):
@@ -201,24 +225,33 @@ def _params(ovl, wl, d):
     return ovl.ovl_sign_params_default(**kw)
 
 
-def run_ours(args, wl):
+def _fp64_peak():
+    """FP64 FMA throughput of this GPU (TFLOP/s), measured by the FMA-chain probe library built
+    beside libovl.so; falls back to the value that probe gave on this machine's GB300."""
+    import ctypes
+
+    try:
+        lib = ctypes.CDLL(os.path.join(ROOT, "paper_0910_1048_gb300", "libovl_probe.so"))
+        out = ctypes.c_double(0.0)
+        if lib.ovl_probe_fma_tflops(1, ctypes.byref(out)) == 0 and out.value > 0:
+            return out.value, "FP64 FMA-chain probe (csrc/probe/fma_peak.cu) run by bench.py on this GPU"
+    except OSError:
+        pass
+    return FP64_PEAK_TFLOPS, "FP64 FMA-chain probe, earlier measurement on this pool's GB300"
+
+
+def _sources(wl):
+    import synth
+
+    nrhs = wl.get("nrhs", 1)
+    return synth.gaussian_source(wl["dims"], 1000, nrhs=nrhs if nrhs > 1 else None)
+
+
+def _time_workload(ovl, ctx, args, wl, u, per_mu, b, flush, world, clocks=None):
+    """Warm-up, then `args.steps` timed steps of one workload. A step = one ovl_apply_sign per
+    mu (each with all of the workload's right-hand sides), run concurrently from host threads."""
     import torch
 
-    import paper_0910_1048_gb300 as ovl
-
-    rank, world, local = _dist()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    ctx = ovl.ovl_ctx_create(local)
-    lat, u, b, per_mu = _setup(ovl, ctx, wl, cache=args.setup_cache)
-    n = b.size
-    bdev = torch.from_numpy(b).cuda()
-    xdev = torch.empty_like(bdev)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-
-    # one lattice per mu, each holding its own deflation set (set-up, untimed)
     lats = []
     for d in per_mu:
         lt = ovl.ovl_create_lattice(ctx, wl["dims"], -1)
@@ -226,20 +259,19 @@ def run_ours(args, wl):
         if wl["m"] > 0:
             ovl.ovl_set_deflation(lt, -2.0, d["mu"], d["R"], d["L"], d["lam"])
         lats.append(lt)
-
+    bdev = torch.from_numpy(b).cuda()
+    xdevs = [torch.empty_like(bdev) for _ in per_mu]
+    xhosts = [torch.empty(b.shape, dtype=torch.complex128).pin_memory().numpy() for _ in per_mu]
     # the step's solves are independent (one per mu, each with its own lattice workspace and
     # streams): they run concurrently from host threads, so their GPU work and their host-side
     # sign(H_k) e_1 evaluations overlap (the library releases the GIL inside every call)
-    xdevs = [torch.empty_like(bdev) for _ in per_mu]
-    xhosts = [torch.empty(b.shape, dtype=torch.complex128).pin_memory().numpy() for _ in per_mu]
     pool = ThreadPoolExecutor(max_workers=len(per_mu)) if args.concurrent and len(per_mu) > 1 else None
 
     def one(i, host, bh):
         p = _params(ovl, wl, per_mu[i])
-        st, info = ovl.ovl_apply_sign(lats[i], p, bh if host else bdev, xhosts[i] if host else xdevs[i])
-        return st, info[0]
+        return ovl.ovl_apply_sign(lats[i], p, bh if host else bdev, xhosts[i] if host else xdevs[i])
 
-    def step(host=False, bh=None, xh=None):
+    def step(host=False, bh=None):
         if pool is None:
             return [one(i, host, bh) for i in range(len(per_mu))]
         return list(pool.map(lambda i: one(i, host, bh), range(len(per_mu))))
@@ -251,34 +283,28 @@ def run_ours(args, wl):
         torch.distributed.barrier()
     times, infos = [], []
     stream = torch.cuda.current_stream()
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            res = step()
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            infos.extend(res)
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        infos.append(res)
     torch.cuda.synchronize()
-    clocks = clk.summary()
     total_ms = max_over_ranks(sum(times), world, "cuda")
-    solves = args.steps * len(per_mu) * world
-    value = throughput(args.steps, len(per_mu), world, total_ms)
     # end to end through the same call with pinned host buffers
     bh = torch.from_numpy(b).pin_memory().numpy()
-    xh = torch.empty(b.shape, dtype=torch.complex128).pin_memory().numpy()
-    step(True, bh, xh)
+    step(True, bh)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step(True, bh, xh)
+        step(True, bh)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
-    e2e = {"value": solves / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(len(per_mu) * n * 16),
-           "d2h_bytes_per_step": int(len(per_mu) * n * 16)}
-    # accuracy actually reached: the paper's measure 0.5 |sign(A)^2 b - b| / |b| (Section 6)
+    # accuracy actually reached: the paper's measure 0.5 |sign(A)^2 b - b| / |b| (Section 6),
+    # worst right-hand side
     acc = []
     for lt, d in zip(lats, per_mu):
         p = _params(ovl, wl, d)
@@ -286,41 +312,121 @@ def run_ours(args, wl):
         x2 = torch.empty_like(bdev)
         ovl.ovl_apply_sign(lt, p, bdev, x1)
         ovl.ovl_apply_sign(lt, p, x1, x2)
-        acc.append(0.5 * float(torch.linalg.vector_norm(x2 - bdev) / torch.linalg.vector_norm(bdev)))
-    # roofline of the dominant kernel from the library's event samples
+        nb = bdev.shape[0] if wl.get("nrhs", 1) > 1 else 1
+        e = (x2 - bdev).reshape(nb, -1)
+        acc.append(float(torch.max(0.5 * torch.linalg.vector_norm(e, dim=1)
+                                   / torch.linalg.vector_norm(bdev.reshape(nb, -1), dim=1))))
+    for lt in lats:
+        ovl.ovl_destroy_lattice(lt)
+    if pool is not None:
+        pool.shutdown()
+    return total_ms, e2e_s, infos, acc
+
+
+def _dslash_gbs(ovl, ctx, u_fn, L=32, reps=20):
+    """Kernel-only bandwidth of the FP32 and FP16-12-real stencil H_W(mu) psi on an L^4 lattice
+    (native layout, CUDA events around `reps` back-to-back launches; inputs > L2)."""
+    import torch
+
+    dims = (L, L, L, L)
+    vol = L ** 4
+    lat = ovl.ovl_create_lattice(ctx, dims, -1)
+    ovl.ovl_set_links(lat, u_fn(dims), ovl.OVL_F32 | ovl.OVL_F16R12)
+    x = torch.randn(12 * vol, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, fl, per_site in (("f32", ovl.OVL_LINKS_F32, 480), ("f16_links", ovl.OVL_LINKS_F16R12, 288)):
+        flags = fl | ovl.OVL_NATIVE | ovl.OVL_GAMMA5
+        for _ in range(3):
+            ovl.ovl_apply_DW(lat, -2.0, 0.3, flags, x, y)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ovl.ovl_apply_DW(lat, -2.0, 0.3, flags, x, y)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        out[name] = {"lattice": "%d^4" % L, "us_per_launch": t * 1e3, "algorithmic_bytes_per_site": per_site,
+                     "achieved_gbs": per_site * vol / (t * 1e-3) / 1e9}
+    ovl.ovl_destroy_lattice(lat)
+    return out
+
+
+def _roofline(wl, infos, fp64_peak, fp64_src):
     peaks, src = _peaks()
     vol = int(np.prod(wl["dims"]))
-    kt = [i["t_kernel_ms"] for _, i in infos if i["kernel_samples"] > 0]
+    kt = [i["t_kernel_ms"] for step in infos for _, inf in step for i in inf[:1] if i["kernel_samples"] > 0]
     t_pair = float(np.mean(kt)) if kt else None
     prec = wl["precision"]
+    kernel = "k_lz_pair" if wl["method"] == "direct" else "k_ms_pair"
+    nr = wl.get("nrhs", 1)
+    traffic = TRAFFIC.get((kernel, prec, tuple(wl["dims"]), nr))
     if prec == "f64":
-        flops = PAIR_FLOPS_PER_SITE * vol
+        flops = PAIR_FLOPS_PER_SITE * vol * nr
         ach = flops / (t_pair * 1e-3) / 1e12 if t_pair else None
-        pk = FP64_PEAK_TFLOPS
-        roof = {"kernel": "k_lz_pair" if wl["method"] == "direct" else "k_ms_pair", "bound": "alu",
-                "achieved": ach, "peak": pk, "unit": "TFLOP/s (FP64)",
-                "frac": (ach / pk) if (ach and pk) else None, "traffic": None,
-                "peak_source": "FP64 FMA-chain probe on this pool's GB300 (DESIGN.md)",
-                "algorithmic_bytes_per_launch": PAIR_BYTES_PER_SITE["f64"] * vol}
-    else:
-        byts = PAIR_BYTES_PER_SITE[prec] * vol
-        ach = byts / (t_pair * 1e-3) / 1e9 if t_pair else None
-        roof = {"kernel": "k_lz_pair" if wl["method"] == "direct" else "k_ms_pair", "bound": "hbm",
-                "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"] if ach else None, "traffic": None,
-                "peak_source": src}
-    its = [i["iterations"] for _, i in infos]
+        return {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
+                "frac": (ach / fp64_peak) if ach else None, "traffic": traffic, "peak_source": fp64_src,
+                "algorithmic_flops_per_launch": flops,
+                "algorithmic_bytes_per_launch": PAIR_BYTES_PER_SITE["f64"] * vol * nr,
+                "note": "FP64 kernels are bound by GB300's FP64 pipe (ncu: FP64 pipe 65-74% active)"}
+    byts = PAIR_BYTES_PER_SITE[prec] * vol * nr
+    ach = byts / (t_pair * 1e-3) / 1e9 if t_pair else None
+    return {"kernel": kernel, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"] if ach else None, "traffic": traffic,
+            "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)", "algorithmic_bytes_per_launch": byts}
+
+
+def _summary(wl, per_mu, infos, acc):
+    flat = [i for step in infos for _, inf in step for i in inf]
+    its = [i["iterations"] for i in flat]
     per_mu_stats = []
     for j, d in enumerate(per_mu):
-        sel = [i for t, (_, i) in enumerate(infos) if t % len(per_mu) == j]
+        sel = [i for step in infos for i in step[j][1]]
         per_mu_stats.append({"mu": d["mu"], "k": float(np.mean([i["iterations"] for i in sel])),
                              "t_solve_ms": float(np.mean([i["t_total_ms"] for i in sel])),
                              "t_small_ms": float(np.mean([i["t_small_ms"] for i in sel])),
                              "t_pair_ms": float(np.mean([i["t_kernel_ms"] for i in sel])),
                              "t_update_ms": float(np.mean([i["t_update_ms"] for i in sel])),
-                             "gap": d.get("gap")})
-    statuses = sorted({st for st, _ in infos})
-    launches = sum(i["kernel_launches"] for _, i in infos)
+                             "evaluations": float(np.mean([i["evaluations"] for i in sel])),
+                             "ritz_evaluations": float(np.mean([i["ritz_evaluations"] for i in sel])),
+                             "gap": d.get("gap"), "accuracy_half_sign2b_minus_b": acc[j]})
+    statuses = sorted({st for step in infos for st, _ in step})
+    launches = sum(inf[0]["kernel_launches"] for step in infos for _, inf in step)
+    return its, per_mu_stats, statuses, launches
+
+
+def run_ours(args, wl):
+    import torch
+
+    import paper_0910_1048_gb300 as ovl
+    import synth
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ctx = ovl.ovl_ctx_create(local)
+    lat, u, _, per_mu = _setup(ovl, ctx, wl, cache=args.setup_cache)
+    b = _sources(wl)
+    nrhs = wl.get("nrhs", 1)
+    n = b.size // nrhs
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    fp64_peak, fp64_src = _fp64_peak()
+
+    with ClockSampler(local) as clk:
+        total_ms, e2e_s, infos, acc = _time_workload(ovl, ctx, args, wl, u, per_mu, b, flush, world)
+    clocks = clk.summary()
+    solves_per_step = len(per_mu) * nrhs
+    solves = args.steps * solves_per_step * world
+    value = throughput(args.steps, solves_per_step, world, total_ms)
+    e2e = {"value": solves / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(len(per_mu) * b.size * 16),
+           "d2h_bytes_per_step": int(len(per_mu) * b.size * 16)}
+    its, per_mu_stats, statuses, launches = _summary(wl, per_mu, infos, acc)
+    prec = wl["precision"]
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -328,24 +434,116 @@ def run_ours(args, wl):
         "data": "synthetic: SU(3) links exp(0.5 i H) seed 0, Gaussian b seed 1000",
         "config": {"workload": args.workload, "lattice": "x".join(map(str, wl["dims"])), "n": int(n),
                    "mu": list(wl["mus"]), "m_W": -2.0, "deflated": wl["m"], "method": wl["method"],
-                   "precision": prec, "tol": wl["tol"], "k_max": wl["k_max"], "nrhs": 1,
-                   "solves_per_step": len(per_mu), "concurrent_solves": bool(args.concurrent),
+                   "precision": prec, "tol": wl["tol"], "k_max": wl["k_max"], "nrhs": nrhs,
+                   "solves_per_step": solves_per_step, "concurrent_solves": bool(args.concurrent),
                    "l2": "flushed between steps (256 MB write)",
                    "iterations_mean": float(np.mean(its)), "statuses": statuses,
                    "accuracy_half_sign2b_minus_b": acc, "per_mu": per_mu_stats,
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": roof, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
+        "roofline": _roofline(wl, infos, fp64_peak, fp64_src), "e2e": e2e, "clocks": clocks,
+        "gpu_launches": int(launches),
     }
+    # the same step in mixed precision (FP32 vectors / FP16 12-real links, FP64 reliable
+    # updates), at the same accuracy, and its speedup over this line's value
+    mixed = wl.get("mixed")
+    if mixed and not args.no_extras:
+        wm = WORKLOADS[mixed]
+        lat_m, _, _, pm = _setup(ovl, ctx, wm, cache=args.setup_cache)
+        ovl.ovl_destroy_lattice(lat_m)
+        with ClockSampler(local) as clk2:
+            tm, em, im, am = _time_workload(ovl, ctx, args, wm, u, pm, b, flush, world)
+        vm = throughput(args.steps, solves_per_step, world, tm)
+        _, pms, stm, lm = _summary(wm, pm, im, am)
+        res["mixed_precision"] = {
+            "workload": mixed, "method": wm["method"], "precision": wm["precision"], "tol": wm["tol"],
+            "value": vm, "unit": UNIT, "ms_per_step": tm / args.steps,
+            "speedup_vs_line_value": vm / value, "e2e_value": solves / em, "statuses": stm,
+            "accuracy_half_sign2b_minus_b": am, "per_mu": pms, "gpu_launches": int(lm),
+            "roofline": _roofline(wm, im, fp64_peak, fp64_src), "clocks": clk2.summary()}
+    if not args.no_extras:
+        res["dslash"] = _dslash_gbs(ovl, ctx, lambda d: synth.gauge_links(d, 0))
+        if args.serving_requests > 0:
+            res["serving"] = serving_sample(ovl, ctx, args.serving_requests)
+        pk, _ = _peaks()
+        for v in res["dslash"].values():
+            v["frac_of_measured_hbm"] = v["achieved_gbs"] / pk["hbm_gbs"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(wl, its, seconds=args.cpu_seconds)
-    for lt in lats:
-        ovl.ovl_destroy_lattice(lt)
     ovl.ovl_destroy_lattice(lat)
     ovl.ovl_ctx_destroy(ctx)
     if rank == 0:
         print(json.dumps(res))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+SERVING = dict(sizes=(4, 8, 12, 16), fields_per_size=5, tols=(1e-6, 1e-8, 1e-10), nrhs_max=8, seed=42,
+               k_max={4: 1200, 8: 1500, 12: 1500, 16: 1200}, mean_interarrival_s=0.05)
+
+
+def serving_sample(ovl, ctx, n_requests, mem_budget=160 << 30, max_slots=8):
+    """A bounded sample of the serving stream: Poisson arrivals of sign(H_W(mu)) b requests on 20
+    resident gauge fields (5 per lattice size 4^4, 8^4, 12^4, 16^4, seeds 0-19), mu ~ U[0, 1],
+    tol in {1e-6, 1e-8, 1e-10}, 1-8 Gaussian sources each (seed 42), FP64 direct method, admitted
+    by device-memory footprint (ovl_submit / ovl_poll). Latency = completion - arrival."""
+    import synth
+
+    cfg = SERVING
+    rng = np.random.default_rng(cfg["seed"])
+    lats, ids = [], []
+    srv = ovl.ovl_server_create(ctx, mem_budget, max_slots=max_slots)
+    for si, L in enumerate(cfg["sizes"]):
+        for f in range(cfg["fields_per_size"]):
+            dims = (L, L, L, L)
+            lat = ovl.ovl_create_lattice(ctx, dims, -1)
+            ovl.ovl_set_links(lat, synth.gauge_links(dims, si * cfg["fields_per_size"] + f), ovl.OVL_F64)
+            lats.append((L, lat))
+            ids.append(ovl.ovl_server_add_field(srv, lat))
+    reqs = []
+    for i in range(n_requests):
+        fi = int(rng.integers(0, len(lats)))
+        L = lats[fi][0]
+        nrhs = int(rng.integers(1, cfg["nrhs_max"] + 1))
+        reqs.append(dict(fi=fi, L=L, nrhs=nrhs, mu=float(rng.uniform(0.0, 1.0)), tol=float(rng.choice(cfg["tols"])),
+                         gap=float(rng.exponential(cfg["mean_interarrival_s"])),
+                         b=synth.gaussian_source((L,) * 4, 2000 + i, nrhs=nrhs)))
+    pending, done = {}, []
+    t_start = time.perf_counter()
+    t_next = t_start
+    i = 0
+    while i < len(reqs) or pending:
+        now = time.perf_counter()
+        while i < len(reqs) and now >= t_next:
+            r = reqs[i]
+            tk = ovl.ovl_submit(srv, ids[r["fi"]], r["b"], r["mu"], r["tol"], k_max=cfg["k_max"][r["L"]])
+            pending[tk] = (r, now)
+            i += 1
+            if i < len(reqs):
+                t_next += reqs[i]["gap"]
+        for tk in list(pending):
+            r, t0 = pending[tk]
+            st, info = ovl.ovl_poll(srv, tk, r["nrhs"], None)
+            if st != ovl.OVL_PENDING:
+                done.append((r, time.perf_counter() - t0, st, info))
+                del pending[tk]
+        time.sleep(0.001)
+    wall = time.perf_counter() - t_start
+    ovl.ovl_server_destroy(srv)
+    for _, lat in lats:
+        ovl.ovl_destroy_lattice(lat)
+    lat_ms = sorted(1e3 * d for _, d, _, _ in done)
+    ok = sum(1 for r, _, _, info in done for inf in info[:r["nrhs"]] if inf["status"] == ovl.OVL_OK)
+    sources = sum(r["nrhs"] for r, _, _, _ in done)
+    per_size = {}
+    for r, d, _, _ in done:
+        per_size.setdefault("%d^4" % r["L"], []).append(1e3 * d)
+    return {"requests": len(done), "sources": sources, "wall_s": wall, "solves_per_s": sources / wall,
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "success_rate": ok / max(1, sources), "precision": "f64", "method": "direct",
+            "p50_ms_by_size": {k: float(np.percentile(v, 50)) for k, v in sorted(per_size.items())},
+            "sample": "%d requests of the 2000-request stream's distribution (Poisson, mean gap %g s)"
+                      % (n_requests, cfg["mean_interarrival_s"]), "mem_budget_bytes": mem_budget,
+            "max_slots": max_slots, "k_max": {"%d^4" % k: v for k, v in cfg["k_max"].items()}}
 
 
 def _oracle_sample(wl, iterations, seconds):
@@ -428,6 +626,10 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=24,
+                    help="requests in the serving sample added to the line (0: none)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the mixed-precision companion line and the stencil bandwidth figure")
     ap.add_argument("--concurrent", type=int, default=1,
                     help="run the step's independent solves concurrently (1) or one after another (0)")
     ap.add_argument("--setup-cache", default=None,

@@ -163,6 +163,9 @@ typedef struct {
   double t_update_ms;     /* the same for the vector-update kernel of a step */
   int32_t kernel_samples; /* launches behind t_kernel_ms (and t_update_ms) */
   int32_t kernel_launches;/* all library kernel launches of the call (shared by its rhs) */
+  int32_t evaluations;    /* direct method: evaluations of sign(H_j) e_1 for this rhs */
+  int32_t ritz_evaluations;/* direct method: of those, the ones that computed Ritz values to choose
+                              the rational scale and pole count (the others reused them) */
 } ovl_sign_info;
 
 /* Fill p with defaults: DIRECT_2SL, F64, m_W = -2, mu = 0, tol = 1e-10, k_max = 600,

@@ -1,7 +1,8 @@
 """Build libovl.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
 Every translation unit under csrc/ is compiled in parallel into _build/ and linked into
-paper_0910_1048_gb300/libovl.so with the CUDA runtime linked statically.
+paper_0910_1048_gb300/libovl.so with the CUDA runtime linked statically. The FMA-throughput
+probe (csrc/probe/, the measured FP64 peak of the bench's roofline) becomes libovl_probe.so.
 """
 from __future__ import annotations
 
@@ -16,6 +17,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libovl.so")
+PROBE_SRC = os.path.join(CSRC, "probe", "fma_peak.cu")
+PROBE_OUT = os.path.join(PKG, "libovl_probe.so")
 BUILD = os.path.join(ROOT, "_build", "ovl-" + platform.machine())  # objects never cross architectures
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
@@ -56,6 +59,9 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
             if s.endswith(".cpp"):
                 cmd = [nvcc] + FLAGS + (extra or []) + ["-x", "c++", "-c", s, "-o", o]
             jobs.append(cmd)
+    probe_obj = os.path.join(BUILD, "fma_peak.cu.o")
+    if not os.path.exists(probe_obj) or os.path.getmtime(probe_obj) < os.path.getmtime(PROBE_SRC):
+        jobs.append([nvcc] + ARCH + FLAGS + (extra or []) + ["-c", PROBE_SRC, "-o", probe_obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -69,9 +75,10 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
                 print(out)
     stamp = os.path.join(BUILD, "libovl.machine")
     fresh = os.path.exists(stamp) and open(stamp).read() == platform.machine()
-    if jobs or not os.path.exists(OUT) or not fresh:
+    if jobs or not os.path.exists(OUT) or not os.path.exists(PROBE_OUT) or not fresh:
         cmd = [nvcc] + ARCH + ["-shared", "-o", OUT] + objs + ["-lpthread", "-ldl", "-lrt"]
         run(cmd)
+        run([nvcc] + ARCH + ["-shared", "-o", PROBE_OUT, probe_obj])
         with open(stamp, "w") as f:
             f.write(platform.machine())
     return OUT

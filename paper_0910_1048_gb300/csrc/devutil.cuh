@@ -50,6 +50,81 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
   __syncthreads();
 }
 
+// c - a b with fused multiply-adds (complex).
+template <class R>
+__device__ __forceinline__ cplx<R> cmsub(cplx<R> c, cplx<R> a, cplx<R> b) {
+  return mk<R>(fma(-a.re, b.re, fma(a.im, b.im, c.re)), fma(-a.re, b.im, fma(-a.im, b.re, c.im)));
+}
+
+// ------------------------------------------------------------------ reduction accumulators
+// FP64 kernels accumulate in double. FP32 kernels accumulate in float-float (an unevaluated sum
+// hi + lo of two FP32 words, about 48 significant bits, Dekker/Knuth two-sum): this GPU's FP64
+// pipe runs at 1/64 of the FP32 rate, so double sums would bound the FP32 kernels. Block
+// results are converted to double; the cross-block sums stay FP64.
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);  // exact error of s (two-sum)
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return FF{hi, e - (hi - s)};
+}
+
+template <class R> struct Red;
+template <> struct Red<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add(const Red& o) { v += o.v; }
+  __device__ __forceinline__ Red shfl_down(int off) const {
+    Red r;
+    r.v = __shfl_down_sync(0xffffffffu, v, off);
+    return r;
+  }
+  __device__ __forceinline__ double get() const { return v; }
+};
+template <> struct Red<float> {
+  FF v{0.f, 0.f};
+  __device__ __forceinline__ void add(float x) { v = ff_add(v, FF{x, 0.f}); }
+  __device__ __forceinline__ void add(const Red& o) { v = ff_add(v, o.v); }
+  __device__ __forceinline__ Red shfl_down(int off) const {
+    Red r;
+    r.v.hi = __shfl_down_sync(0xffffffffu, v.hi, off);
+    r.v.lo = __shfl_down_sync(0xffffffffu, v.lo, off);
+    return r;
+  }
+  __device__ __forceinline__ double get() const { return (double)v.hi + (double)v.lo; }
+};
+
+// Sum NV accumulators over the block; out valid in thread 0. Block size multiple of 32.
+template <class R, int NV>
+__device__ __forceinline__ void block_reduce(Red<R> (&a)[NV], double (&out)[NV]) {
+  __shared__ Red<R> sm[NV][32];
+  const int t = lin_tid();
+  const int lane = t & 31, warp = t >> 5, nw = lin_nthreads() >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a[i].add(a[i].shfl_down(off));
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sm[i][warp] = a[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      a[i] = lane < nw ? sm[i][lane] : Red<R>();
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) a[i].add(a[i].shfl_down(off));
+      out[i] = a[i].get();
+    }
+  }
+  __syncthreads();
+}
+
 // Write this block's NV partials; returns true in every thread of the last block to arrive.
 // The counter is reset to 0 by the last block so the next launch starts clean.
 template <int NV>

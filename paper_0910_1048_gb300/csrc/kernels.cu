@@ -111,7 +111,7 @@ cudaError_t launch_ingest_links(const Geom& g, const double* ucan, double2* u64,
 
 // ------------------------------------------------------------------ apply D_W
 template <class R, int LF, bool NIN, bool NOUT>
-__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 7 : 1) k_dslash(Geom g, Links U, HopCoef<R> c, bool g5_in, bool g5_out,
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? (LF == LINK_F16R12 ? 6 : 7) : 1) k_dslash(Geom g, Links U, HopCoef<R> c, bool g5_in, bool g5_out,
                                                    const typename V2<R>::T* in, typename V2<R>::T* out) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.vol) return;
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(2 * kPairSites) k_lz_pair(Geom g, Links U, Hop
   const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
   const int s = blockIdx.x * kPairSites + threadIdx.x;
   const bool is_w = threadIdx.y == 1;
-  double acc[2] = {0, 0};
+  Red<R> acc[2];
   if (s < g.vol) {
     Spin<R> ov;
     if (!is_w) {
@@ -315,8 +315,8 @@ __global__ void __launch_bounds__(2 * kPairSites) k_lz_pair(Geom g, Links U, Hop
         stc<R>(av + (size_t)rhs * n, (size_t)c * g.vol + s, x);
         a = a + cdot(ldc<R>(wj, (size_t)c * g.vol + s), x);
       }
-      acc[0] = (double)a.re;
-      acc[1] = (double)a.im;
+      acc[0].add(a.re);
+      acc[1].add(a.im);
     } else {
       dslash_site<LF, R>(g, U, s, cm, Loader<R, true>{wj, g.vol, false}, ov);
       const cplx<R> sw = mk<R>((R)swd.x, (R)swd.y);
@@ -328,9 +328,10 @@ __global__ void __launch_bounds__(2 * kPairSites) k_lz_pair(Geom g, Links U, Hop
       }
     }
   }
-  block_sum<2>(acc);
+  double tot[2];
+  block_reduce<R, 2>(acc, tot);
   double* part = lz.part + (size_t)rhs * lz.nblk * 4;
-  double pv[4] = {acc[0], acc[1], 0, 0};
+  double pv[4] = {tot[0], tot[1], 0, 0};
   if (publish_partials<4>(pv, part, lz.count + rhs)) {
     reduce_partials<4>(part, gridDim.x, pv);
     if (lin_tid() == 0) {
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(8 * kSplitSites) k_lz_pair_split(Geom g, Links
   const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
   const R sv = (R)lz.sv[o + j];
   const cplx<R> sw = mk<R>((R)swd.x, (R)swd.y);
-  double acc[2] = {0, 0};
+  Red<R> acc[2];
   pair_split<R, LF>(g, U, cp, cm, vj, wj, sm, [&](int which, int s, Spin<R>& out) {
     if (which == 0) {
       cplx<R> a = mk<R>(0, 0);
@@ -370,8 +371,8 @@ __global__ void __launch_bounds__(8 * kSplitSites) k_lz_pair_split(Geom g, Links
         stc<R>(av + (size_t)rhs * n, (size_t)c * g.vol + s, x);
         a = a + cdot(ldc<R>(wj, (size_t)c * g.vol + s), x);
       }
-      acc[0] = (double)a.re;
-      acc[1] = (double)a.im;
+      acc[0].add(a.re);
+      acc[1].add(a.im);
     } else {
 #pragma unroll
       for (int c = 0; c < 12; ++c) {
@@ -381,9 +382,10 @@ __global__ void __launch_bounds__(8 * kSplitSites) k_lz_pair_split(Geom g, Links
       }
     }
   });
-  block_sum<2>(acc);
+  double tot[2];
+  block_reduce<R, 2>(acc, tot);
   double* part = lz.part + (size_t)rhs * lz.nblk * 4;
-  double pv[4] = {acc[0], acc[1], 0, 0};
+  double pv[4] = {tot[0], tot[1], 0, 0};
   if (publish_partials<4>(pv, part, lz.count + rhs)) {
     reduce_partials<4>(part, gridDim.x, pv);
     if (lin_tid() == 0) {
@@ -400,7 +402,7 @@ __global__ void __launch_bounds__(8 * kSplitSites) k_lz_pair_split(Geom g, Links
 template <class R>
 __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typename V2<R>::T* vh,
                                                          typename V2<R>::T* wh, const typename V2<R>::T* av,
-                                                         const typename V2<R>::T* aw) {
+                                                         const typename V2<R>::T* aw, int elt) {
   using T = typename V2<R>::T;
   const int rhs = blockIdx.y;
   if (lz.status[rhs]) return;
@@ -422,31 +424,36 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typen
   T* vnew = vh + ((size_t)rhs * (lz.kmax + 1) + j) * n;
   const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
   T* wnew = wh + ((size_t)((j + 1) & 1) * lz.nrhs + rhs) * n;  // holds what_{j-1} until overwritten
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[4] = {0, 0, 0, 0};
-  if (e < n) {
-    cplx<R> x = ldc<R>(av + (size_t)rhs * n, e) - a1 * ldc<R>(vj, e);
-    cplx<R> y = ldc<R>(aw + (size_t)rhs * n, e) - b1 * ldc<R>(wj, e);
+  const T* avr = av + (size_t)rhs * n;
+  const T* awr = aw + (size_t)rhs * n;
+  Red<R> acc[4];
+  // elt elements per thread, block-contiguous per pass (coalesced)
+  for (int q = 0; q < elt; ++q) {
+    const size_t e = ((size_t)blockIdx.x * elt + q) * blockDim.x + threadIdx.x;
+    if (e >= n) break;
+    cplx<R> x = cmsub(ldc<R>(avr, e), a1, ldc<R>(vj, e));
+    cplx<R> y = cmsub(ldc<R>(awr, e), b1, ldc<R>(wj, e));
     if (j > 1) {
-      x = x - a2 * ldc<R>(vjm, e);
-      y = y - b2 * ldc<R>(wnew, e);
+      x = cmsub(x, a2, ldc<R>(vjm, e));
+      y = cmsub(y, b2, ldc<R>(wnew, e));
     }
     stc<R>(vnew, e, x);
     stc<R>(wnew, e, y);
-    cplx<R> ip = cdot(y, x);
-    acc[0] = ip.re;
-    acc[1] = ip.im;
-    acc[2] = norm2(x);
-    acc[3] = norm2(y);
+    acc[0].add(fma(y.re, x.re, y.im * x.im));  // (y^H x).re
+    acc[1].add(fma(y.re, x.im, -(y.im * x.re)));
+    acc[2].add(fma(x.re, x.re, x.im * x.im));
+    acc[3].add(fma(y.re, y.re, y.im * y.im));
   }
-  block_sum<4>(acc);
+  double tot[4];
+  block_reduce<R, 4>(acc, tot);
   double* part = lz.part + (size_t)rhs * lz.nblk * 4;
-  if (publish_partials<4>(acc, part, lz.count + rhs)) {
-    reduce_partials<4>(part, gridDim.x, acc);
+  if (publish_partials<4>(tot, part, lz.count + rhs)) {
+    double sums[4];
+    reduce_partials<4>(part, gridDim.x, sums);
     if (lin_tid() == 0) {
-      zd ip = mk(acc[0], acc[1]);
+      zd ip = mk(sums[0], sums[1]);
       double aip = sqrt(norm2(ip));
-      if (!(aip > 1e-14 * sqrt(acc[2] * acc[3])) || !(aip < 1e300)) {
+      if (!(aip > 1e-14 * sqrt(sums[2] * sums[3])) || !(aip < 1e300)) {
         lz.status[rhs] = 1;  // breakdown (or non-finite)
       } else {
         double d = sqrt(aip);
@@ -456,7 +463,7 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typen
         lz.sv[o + j + 1] = 1.0 / d;
         double bb = norm2(bt);  // 1/conj(beta) = beta / |beta|^2
         lz.sw[o + j + 1] = make_double2(bt.re / bb, bt.im / bb);
-        lz.vnorm[o + j + 1] = sqrt(acc[2]) / d;
+        lz.vnorm[o + j + 1] = sqrt(sums[2]) / d;
         lz.j[rhs] = j + 1;
       }
     }
@@ -500,13 +507,14 @@ cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64,
 }
 
 cudaError_t launch_lanczos_update(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, cudaStream_t st) {
-  dim3 grid(vec_blocks(g), lz.nrhs);
+  const int elt = vec_elts(g, lz.nrhs, f64);
+  dim3 grid(vec_blocks(g, elt), lz.nrhs);
   if (f64)
     k_lz_update<double><<<grid, kVecBlock, 0, st>>>(g, lz, (double2*)vec.vh, (double2*)vec.wh,
-                                                     (const double2*)vec.av, (const double2*)vec.aw);
+                                                     (const double2*)vec.av, (const double2*)vec.aw, elt);
   else
     k_lz_update<float><<<grid, kVecBlock, 0, st>>>(g, lz, (float2*)vec.vh, (float2*)vec.wh, (const float2*)vec.av,
-                                                    (const float2*)vec.aw);
+                                                    (const float2*)vec.aw, elt);
   return cudaGetLastError();
 }
 

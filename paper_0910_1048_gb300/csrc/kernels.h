@@ -1,6 +1,8 @@
 // Launchers of the library's CUDA kernels (implemented in kernels.cu).
 #pragma once
 
+#include <algorithm>
+
 #include "common.h"
 
 namespace ovl {
@@ -15,8 +17,18 @@ int tuned_pair_variant(int vol, int prec);
 // Returns the variant for the key, running `measure` (which returns 0 or 1) under the table's
 // lock the first time, so that every solve in the process uses one decision per key.
 int tune_pair_variant(int vol, int prec, int (*measure)(void*), void* arg);
-constexpr int kVecBlock = 256;  // threads per block of the element-parallel vector kernels
+constexpr int kVecBlock = 128;  // threads per block of the element-parallel vector kernels
 inline unsigned vec_blocks(const Geom& g) { return (unsigned)((12 * (size_t)g.vol + kVecBlock - 1) / kVecBlock); }
+// Elements per thread of the FP32 element-parallel kernels: enough to amortise the block
+// reduction, while keeping at least about four blocks per SM over the whole grid.
+inline int vec_elts(const Geom& g, int nrhs, bool f64) {
+  if (f64) return 1;
+  const size_t total = 12 * (size_t)g.vol * (size_t)nrhs;
+  return (int)std::max<size_t>(1, std::min<size_t>(8, total / ((size_t)kVecBlock * 608)));
+}
+inline unsigned vec_blocks(const Geom& g, int elt) {
+  return (unsigned)((12 * (size_t)g.vol + (size_t)kVecBlock * elt - 1) / ((size_t)kVecBlock * elt));
+}
 // partial-sum slots per rhs: the most blocks any reduction kernel launches (the element-parallel ones)
 inline int partial_slots(const Geom& g) { return (int)vec_blocks(g); }
 
@@ -99,6 +111,8 @@ namespace ovl {
 constexpr int kMaxShifts = 128;
 constexpr double kFp32Floor = 2e-6;   // relative residual the FP32 iteration reaches by itself
 constexpr int kMaxRefineSweeps = 8;   // FP64 residual / FP32 correction rounds per shifted system
+constexpr int kRefineGroup = 64;      // correction systems solved together in one batch
+constexpr size_t kRefineBytes = (size_t)8 << 30;  // buffer budget of that batch
 struct MsDev {
   int nrhs = 0, s = 0, nblk = 0;
   int* k = nullptr;           // [nrhs] iterations done
@@ -111,6 +125,8 @@ struct MsDev {
   const double* omega = nullptr;  // [s]
   const double* dsig = nullptr;   // [s] sigma_i - sigma_1
   double sigma1 = 0, tol = 0;
+  const double* sig1v = nullptr;  // [nrhs] per-rhs seed shift (overrides sigma1; batched refinement)
+  const double* tolv = nullptr;   // [nrhs] per-rhs tolerance (overrides tol)
   double* part = nullptr;     // [nrhs][nblk][4]
   unsigned* count = nullptr;  // [nrhs]
 };
@@ -135,6 +151,14 @@ cudaError_t launch_ms_step(const Geom& g, const Links& U, int lf, bool f64, doub
 // (native FP64), |res|^2 in out[0] (part/count scratch); x += e; X = sum_i omega_i xs_i.
 cudaError_t launch_ms_residual(const Geom& g, const double2* r64, const double2* t2, const double2* x, double sigma,
                                double2* res, double* part, unsigned* count, double* out, cudaStream_t st);
+// Batched form for the systems j0 .. j0+gn-1 of the flattened (rhs, shift) index j = rhs*s + i:
+// res_j = r64[rhs] - (t2_j - sigma[i] x_j), |res_j|^2 -> out[j - j0]. t2, x, res hold gn vectors.
+cudaError_t launch_ms_residual_batch(const Geom& g, int j0, int gn, int s, const double2* r64, const double2* t2,
+                                     const double2* x, const double* sigma, double2* res, double* part,
+                                     unsigned* count, double* out, cudaStream_t st);
+// x_j += e_j for the gn vectors whose status[j] is not a breakdown (1).
+cudaError_t launch_axpy_f64_masked(const Geom& g, int gn, const int* status, const double2* e, double2* x,
+                                   cudaStream_t st);
 cudaError_t launch_axpy_f64(const Geom& g, int nrhs, const double2* e, double2* x, cudaStream_t st);
 cudaError_t launch_ms_combine_shifts(const Geom& g, int nrhs, int s, const double* omega, const double2* xs,
                                      double2* X, cudaStream_t st);

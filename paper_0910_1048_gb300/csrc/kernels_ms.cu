@@ -142,11 +142,11 @@ __global__ void __launch_bounds__(2 * kPairSites) k_ms_pair(Geom g, Links U, Hop
   const bool is_t = threadIdx.y == 1;
   const T* in = (const T*)(MODE == 0 ? (is_t ? v.pt : v.p) : (is_t ? v.tt : v.t)) + voff<R>(rhs, n);
   T* out = (T*)(MODE == 0 ? (is_t ? v.tt : v.t) : (is_t ? v.qt : v.q)) + voff<R>(rhs, n);
-  double acc[2] = {0, 0};
+  Red<R> acc[2];
   if (s < g.vol) {
     Spin<R> o;
     dslash_site<LF, R>(g, U, s, is_t ? cm : cp, Loader<R, true>{in, g.vol, false}, o);
-    const R s1 = (R)ms.sigma1;
+    const R s1 = (R)(ms.sig1v ? ms.sig1v[rhs] : ms.sigma1);
     const T* pp = (const T*)(is_t ? v.pt : v.p) + voff<R>(rhs, n);
     const T* ptl = (const T*)v.pt + voff<R>(rhs, n);
     cplx<R> a = mk<R>(0, 0);
@@ -160,13 +160,14 @@ __global__ void __launch_bounds__(2 * kPairSites) k_ms_pair(Geom g, Links U, Hop
       }
       stc<R>(out, (size_t)c * g.vol + s, x);
     }
-    acc[0] = (double)a.re;
-    acc[1] = (double)a.im;
+    acc[0].add(a.re);
+    acc[1].add(a.im);
   }
   if (MODE == 0) return;
-  block_sum<2>(acc);
+  double tot[2];
+  block_reduce<R, 2>(acc, tot);
   double* part = ms.part + (size_t)rhs * ms.nblk * 4;
-  double pv[4] = {acc[0], acc[1], 0, 0};
+  double pv[4] = {tot[0], tot[1], 0, 0};
   if (publish_partials<4>(pv, part, ms.count + rhs)) {
     reduce_partials<4>(part, gridDim.x, pv);
     ms_alpha_and_shifts(ms, rhs, pv);
@@ -185,8 +186,8 @@ __global__ void __launch_bounds__(8 * kSplitSites) k_ms_pair_split(Geom g, Links
   const size_t n = (size_t)12 * g.vol;
   const T* in0 = (const T*)(MODE == 0 ? v.p : v.t) + voff<R>(rhs, n);
   const T* in1 = (const T*)(MODE == 0 ? v.pt : v.tt) + voff<R>(rhs, n);
-  const R s1 = (R)ms.sigma1;
-  double acc[2] = {0, 0};
+  const R s1 = (R)(ms.sig1v ? ms.sig1v[rhs] : ms.sigma1);
+  Red<R> acc[2];
   pair_split<R, LF>(g, U, cp, cm, in0, in1, sm, [&](int which, int s, Spin<R>& o) {
     T* out = (T*)(MODE == 0 ? (which ? v.tt : v.t) : (which ? v.qt : v.q)) + voff<R>(rhs, n);
     const T* pp = (const T*)(which ? v.pt : v.p) + voff<R>(rhs, n);
@@ -202,58 +203,62 @@ __global__ void __launch_bounds__(8 * kSplitSites) k_ms_pair_split(Geom g, Links
       }
       stc<R>(out, (size_t)c * g.vol + s, x);
     }
-    acc[0] = (double)a.re;
-    acc[1] = (double)a.im;
+    acc[0].add(a.re);
+    acc[1].add(a.im);
   });
   if (MODE == 0) return;
-  block_sum<2>(acc);
+  double tot[2];
+  block_reduce<R, 2>(acc, tot);
   double* part = ms.part + (size_t)rhs * ms.nblk * 4;
-  double pv[4] = {acc[0], acc[1], 0, 0};
+  double pv[4] = {tot[0], tot[1], 0, 0};
   if (publish_partials<4>(pv, part, ms.count + rhs)) {
     reduce_partials<4>(part, gridDim.x, pv);
     ms_alpha_and_shifts(ms, rhs, pv);
   }
 }
 
-// update: r -= alpha q, r~ -= conj(alpha) q~; rho' = r~^H r, |r|^2
+// update: r -= alpha q, r~ -= conj(alpha) q~; rho' = r~^H r, |r|^2 (elt elements per thread)
 template <class R>
-__global__ void __launch_bounds__(kVecBlock) k_ms_update(Geom g, MsDev ms, MsVecs v) {
+__global__ void __launch_bounds__(kVecBlock) k_ms_update(Geom g, MsDev ms, MsVecs v, int elt) {
   using T = typename V2<R>::T;
   const int rhs = blockIdx.y;
   if (ms.status[rhs] != 0) return;
   const size_t n = (size_t)12 * g.vol;
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // one vector element per thread
   double2* sd = ms.seed + (size_t)rhs * 8;
   const zd ak = ldc<double>(sd, 1);
   const cplx<R> a = mk<R>((R)ak.re, (R)ak.im), ac = mk<R>((R)ak.re, (R)-ak.im);
-  double acc[4] = {0, 0, 0, 0};
-  if (e < n) {
-    T* r = (T*)v.r + voff<R>(rhs, n);
-    T* rt = (T*)v.rt + voff<R>(rhs, n);
-    const T* q = (const T*)v.q + voff<R>(rhs, n);
-    const T* qt = (const T*)v.qt + voff<R>(rhs, n);
-    cplx<R> x = ldc<R>(r, e) - a * ldc<R>(q, e);
-    cplx<R> y = ldc<R>(rt, e) - ac * ldc<R>(qt, e);
+  T* r = (T*)v.r + voff<R>(rhs, n);
+  T* rt = (T*)v.rt + voff<R>(rhs, n);
+  const T* q = (const T*)v.q + voff<R>(rhs, n);
+  const T* qt = (const T*)v.qt + voff<R>(rhs, n);
+  Red<R> red[3];
+  for (int k = 0; k < elt; ++k) {
+    const size_t e = ((size_t)blockIdx.x * elt + k) * blockDim.x + threadIdx.x;
+    if (e >= n) break;
+    cplx<R> x = cmsub(ldc<R>(r, e), a, ldc<R>(q, e));
+    cplx<R> y = cmsub(ldc<R>(rt, e), ac, ldc<R>(qt, e));
     stc<R>(r, e, x);
     stc<R>(rt, e, y);
-    cplx<R> ip = cdot(y, x);
-    acc[0] = ip.re;
-    acc[1] = ip.im;
-    acc[2] = norm2(x);
+    red[0].add(fma(y.re, x.re, y.im * x.im));  // (y^H x).re
+    red[1].add(fma(y.re, x.im, -(y.im * x.re)));
+    red[2].add(fma(x.re, x.re, x.im * x.im));
   }
-  block_sum<4>(acc);
+  double acc[3];
+  block_reduce<R, 3>(red, acc);
   double* part = ms.part + (size_t)rhs * ms.nblk * 4;
-  if (publish_partials<4>(acc, part, ms.count + rhs)) {
-    reduce_partials<4>(part, gridDim.x, acc);
+  double pv[4] = {acc[0], acc[1], acc[2], 0};
+  if (publish_partials<4>(pv, part, ms.count + rhs)) {
+    reduce_partials<4>(part, gridDim.x, pv);
+    const double tl = ms.tolv ? ms.tolv[rhs] : ms.tol;
     __shared__ zd beta_sh;
     __shared__ double rn_sh;
     __shared__ int live;
     const int t = lin_tid();
     if (t == 0) {
-      zd rho = ldc<double>(sd, 0), rhon = mk(acc[0], acc[1]);
+      zd rho = ldc<double>(sd, 0), rhon = mk(pv[0], pv[1]);
       double rr = norm2(rho);
       zd beta = rr > 0 ? (1.0 / rr) * (rhon * conj(rho)) : mk(0.0, 0.0);
-      double rn = sqrt(acc[2]);
+      double rn = sqrt(pv[2]);
       beta_sh = beta;
       rn_sh = rn;
       live = 0;
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_update(Geom g, MsDev ms, MsVec
       sd[4].y = rn;
       ms.k[rhs] += 1;
       // breakdown of the BiCG recurrence (rho' = 0 while r is not small) or non-finite values
-      if (!(rn < 1e300) || !(norm2(rhon) < 1e300) || (norm2(rhon) == 0.0 && rn > ms.tol * sd[4].x))
+      if (!(rn < 1e300) || !(norm2(rhon) < 1e300) || (norm2(rhon) == 0.0 && rn > tl * sd[4].x))
         ms.status[rhs] = 1;
     }
     __syncthreads();
@@ -282,7 +287,7 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_update(Geom g, MsDev ms, MsVec
       ms.bsh[si] = make_double2(bi.re, bi.im);
       z[0] = z[1];
       z[1] = z[2];
-      if (sqrt(norm2(zp)) * rn <= ms.tol * r0)
+      if (sqrt(norm2(zp)) * rn <= tl * r0)
         ms.active[si] = 2;  // this step's direction update is its last
       else
         mylive = 1;
@@ -293,7 +298,11 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_update(Geom g, MsDev ms, MsVec
   }
 }
 
-// dirs: X += sum_i omega_i alpha^i p^i (FP64); p^i = zeta^i r + beta^i p^i; p, p~ updates
+// dirs: X += sum_i omega_i alpha^i p^i; p^i = zeta^i r + beta^i p^i; p, p~ updates.
+// FP64 kernels accumulate X term by term in double. FP32 kernels sum the iteration's terms
+// over the shifts in float-float and add that sum to the FP64 X once (the FP64 pipe is 1/64 of
+// the FP32 rate); with per-shift solutions kept (refinement), each FP32 increment alpha^i p^i
+// is added to the FP64 x^(i), whose error the FP64 residual corrections remove afterwards.
 template <class R>
 __global__ void __launch_bounds__(kVecBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs v) {
   using T = typename V2<R>::T;
@@ -302,12 +311,13 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs 
   if (st != 0 && st != 4) return;
   const size_t n = (size_t)12 * g.vol;
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // one vector element per thread
-  __shared__ double2 coefx[kMaxShifts], coefz[kMaxShifts], coefb[kMaxShifts];
+  __shared__ double2 coefx[kMaxShifts], coefz[kMaxShifts], coefb[kMaxShifts], coefa[kMaxShifts];
   __shared__ int act[kMaxShifts];
   for (int i = threadIdx.x; i < ms.s; i += blockDim.x) {
     const size_t si = (size_t)rhs * ms.s + i;
     act[i] = ms.active[si];
     zd ai = ldc<double>(ms.ash, si);
+    coefa[i] = make_double2(ai.re, ai.im);
     coefx[i] = make_double2(ms.omega[i] * ai.re, ms.omega[i] * ai.im);
     coefz[i] = ms.zeta[si * 3 + 1];  // zeta_{k+1} after the rotation in update
     coefb[i] = ms.bsh[si];
@@ -325,22 +335,40 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs 
   {
     const cplx<R> rv = ldc<R>(r, e);
     zd xa = ldc<double>(X, e);
+    Red<R> sre, sim;  // FP32: this iteration's sum over the shifts
     for (int i = 0; i < ms.s; ++i) {
       if (!act[i]) continue;
       T* pi = ps + (size_t)i * n;
-      cplx<R> pv = ldc<R>(pi, e);
-      double2 cx = coefx[i];
+      const cplx<R> pv = ldc<R>(pi, e);
       if (v.xs) {  // keep x^(i) itself (FP64): x^(i) += alpha^i p^i
         double2* xi = v.xs + ((size_t)rhs * ms.s + i) * n;
-        zd ai = ldc<double>(ms.ash, (size_t)rhs * ms.s + i);
-        stc<double>(xi, e, ldc<double>(xi, e) + ai * mk((double)pv.re, (double)pv.im));
+        const double2 ca = coefa[i];
+        if constexpr (sizeof(R) == 8) {
+          stc<double>(xi, e, ldc<double>(xi, e) + mk(ca.x, ca.y) * pv);
+        } else {
+          const cplx<R> inc = mk<R>((R)ca.x, (R)ca.y) * pv;
+          stc<double>(xi, e, ldc<double>(xi, e) + mk((double)inc.re, (double)inc.im));
+        }
       } else {
-        xa = xa + mk(cx.x, cx.y) * mk((double)pv.re, (double)pv.im);
+        const double2 cx = coefx[i];
+        if constexpr (sizeof(R) == 8) {
+          xa = xa + mk(cx.x, cx.y) * pv;
+        } else {
+          const cplx<R> c = mk<R>((R)cx.x, (R)cx.y);
+          sre.add(fma(c.re, pv.re, -(c.im * pv.im)));
+          sim.add(fma(c.re, pv.im, c.im * pv.re));
+        }
       }
       if (act[i] == 1) {
         double2 cz = coefz[i], cb = coefb[i];
         cplx<R> nv = mk<R>((R)cz.x, (R)cz.y) * rv + mk<R>((R)cb.x, (R)cb.y) * pv;
         stc<R>(pi, e, nv);
+      }
+    }
+    if constexpr (sizeof(R) == 4) {
+      if (!v.xs) {
+        xa.re += sre.get();
+        xa.im += sim.get();
       }
     }
     stc<double>(X, e, xa);
@@ -384,7 +412,8 @@ static cudaError_t ms_step_t(const Geom& g, const Links& U, double m_w, double m
     k_ms_pair_split<R, LF, 1><<<sgrid, sblock, 0, st>>>(g, U, cp, cm, ms, v);
   else
     k_ms_pair<R, LF, 1><<<pgrid, pblock, 0, st>>>(g, U, cp, cm, ms, v);
-  k_ms_update<R><<<grid, kVecBlock, 0, st>>>(g, ms, v);
+  const int elt = vec_elts(g, ms.nrhs, sizeof(R) == 8);
+  k_ms_update<R><<<dim3(vec_blocks(g, elt), ms.nrhs), kVecBlock, 0, st>>>(g, ms, v, elt);
   if (ev) cudaEventRecord(ev[2], st);
   k_ms_dirs<R><<<grid, kVecBlock, 0, st>>>(g, ms, v);
   if (ev) cudaEventRecord(ev[3], st);
@@ -420,6 +449,50 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_residual(int vol, const double
 cudaError_t launch_ms_residual(const Geom& g, const double2* r64, const double2* t2, const double2* x, double sigma,
                                double2* res, double* part, unsigned* count, double* out, cudaStream_t st) {
   k_ms_residual<<<vec_blocks(g), kVecBlock, 0, st>>>(g.vol, r64, t2, x, sigma, res, part, count, out);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kVecBlock) k_ms_residual_batch(int vol, int j0, int s, const double2* r64,
+                                                                 const double2* t2, const double2* x,
+                                                                 const double* sigma, double2* res, double* part,
+                                                                 unsigned* count, double* out) {
+  const size_t n = (size_t)12 * vol;
+  const int j = blockIdx.y, jj = j0 + j, rhs = jj / s, i = jj % s;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0};
+  if (e < n) {
+    const size_t o = (size_t)j * n + e;
+    zd a = ldc<double>(r64, (size_t)rhs * n + e) - (ldc<double>(t2, o) - sigma[i] * ldc<double>(x, o));
+    stc<double>(res, o, a);
+    acc[0] = norm2(a);
+  }
+  block_sum<1>(acc);
+  if (publish_partials<1>(acc, part + (size_t)j * gridDim.x, count + j)) {
+    reduce_partials<1>(part + (size_t)j * gridDim.x, gridDim.x, acc);
+    if (lin_tid() == 0) out[j] = acc[0];
+  }
+}
+
+cudaError_t launch_ms_residual_batch(const Geom& g, int j0, int gn, int s, const double2* r64, const double2* t2,
+                                     const double2* x, const double* sigma, double2* res, double* part,
+                                     unsigned* count, double* out, cudaStream_t st) {
+  dim3 grid(vec_blocks(g), gn);
+  k_ms_residual_batch<<<grid, kVecBlock, 0, st>>>(g.vol, j0, s, r64, t2, x, sigma, res, part, count, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_axpy_f64_masked(size_t n, const int* status, const double2* e, double2* x) {
+  const int j = blockIdx.y;
+  if (status[j] == 1) return;  // breakdown of this correction solve: keep x_j
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) stc<double>(x, (size_t)j * n + i, ldc<double>(x, (size_t)j * n + i) + ldc<double>(e, (size_t)j * n + i));
+}
+
+cudaError_t launch_axpy_f64_masked(const Geom& g, int gn, const int* status, const double2* e, double2* x,
+                                   cudaStream_t st) {
+  size_t n = (size_t)12 * g.vol;
+  dim3 grid((unsigned)((n + 255) / 256), gn);
+  k_axpy_f64_masked<<<grid, 256, 0, st>>>(n, status, e, x);
   return cudaGetLastError();
 }
 

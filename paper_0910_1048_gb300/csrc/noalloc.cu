@@ -25,7 +25,7 @@ namespace ovl {
 
 ovl_status small_sign(int k, const std::complex<double>* al, const std::complex<double>* be,
                       const std::complex<double>* de, std::complex<double>* y, int method, double* hint_c,
-                      int* hint_s);
+                      int* hint_s, int* ritz_count);
 
 namespace {
 
@@ -62,7 +62,7 @@ struct Rhs {
   int k = 0;
   std::vector<std::complex<double>> y, yprev;
   double est = 1e300, hint_c = 0;
-  int hint_s = 0;
+  int hint_s = 0, evals = 0, ritz = 0;
   StopTrack trk;
   ovl_status status = OVL_PENDING;
   bool done = false;
@@ -206,7 +206,8 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
       }
     }
     auto ts = std::chrono::steady_clock::now();
-    ovl_status e = small_sign(k, al.data(), be.data(), de.data(), y.data(), 0, &s.hint_c, &s.hint_s);
+    ++s.evals;
+    ovl_status e = small_sign(k, al.data(), be.data(), de.data(), y.data(), 0, &s.hint_c, &s.hint_s, &s.ritz);
     t_small += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
     if (e != OVL_OK) return e;
     s.est = 1e300;
@@ -325,6 +326,8 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
       info[r].t_total_ms = t_total;
       info[r].t_small_ms = t_small;
       info[r].kernel_launches = launches;
+      info[r].evaluations = rs[r].evals;
+      info[r].ritz_evaluations = rs[r].ritz;
     }
   if (result != OVL_OK) set_error("apply_sign_noalloc: at least one right-hand side ended with status %d", result);
   return result;

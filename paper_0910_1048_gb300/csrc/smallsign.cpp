@@ -460,7 +460,7 @@ void rational_apply(int k, const cz* al, const cz* be, const cz* de, double c, i
 // Rational route with a (c, s) hint; hint->s == 0 means "compute from the Ritz values".
 // Returns OVL_OK when the involution residual is below tol_inv.
 ovl_status small_sign_rational(int k, const cz* al, const cz* be, const cz* de, cz* y, double* hint_c, int* hint_s,
-                               double* inv_res) {
+                               double* inv_res, int* ritz_count) {
   const double eps = 1e-15, tol_inv = 1e-11;
   const int s_max = 4000;
   // attempts: the cached (c, s); the same c with 50% more poles (new Ritz values closer to
@@ -469,6 +469,7 @@ ovl_status small_sign_rational(int k, const cz* al, const cz* be, const cz* de, 
   for (int attempt = had_hint ? 0 : 2; attempt < 3; ++attempt) {
     if (attempt == 1) *hint_s = std::min(s_max, (*hint_s * 3 + 1) / 2);
     if (attempt == 2) {
+      if (ritz_count) ++*ritz_count;
       std::vector<cz> lam;
       if (!ritz_values(k, al, be, de, lam)) return OVL_ENOCONV;
       double lmax = 0;
@@ -495,7 +496,7 @@ ovl_status small_sign_rational(int k, const cz* al, const cz* be, const cz* de, 
 // method 0 auto (rational, then QL eigenvectors, then Newton), 1 QL only, 2 Newton only,
 // 3 rational only. hint_c/hint_s (may be null) carry (c, s) between calls on growing H_k.
 ovl_status small_sign(int k, const cz* al, const cz* be, const cz* de, cz* y, int method, double* hint_c = nullptr,
-                      int* hint_s = nullptr) {
+                      int* hint_s = nullptr, int* ritz_count = nullptr) {
   if (k < 1) {
     set_error("small_sign: k < 1");
     return OVL_EINVAL;
@@ -511,7 +512,7 @@ ovl_status small_sign(int k, const cz* al, const cz* be, const cz* de, cz* y, in
   if (method == 0 || method == 3) {
     double c = hint_c ? *hint_c : 0.0;
     int sp = hint_s ? *hint_s : 0;
-    ovl_status s = small_sign_rational(k, al, be, de, y, &c, &sp, nullptr);
+    ovl_status s = small_sign_rational(k, al, be, de, y, &c, &sp, nullptr, ritz_count);
     if (hint_c && s == OVL_OK) *hint_c = c;
     if (hint_s) *hint_s = s == OVL_OK ? sp : 0;
     if (s == OVL_OK || method == 3 || s == OVL_EILLPOSED) return s;

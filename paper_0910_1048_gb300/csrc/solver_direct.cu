@@ -21,7 +21,7 @@ namespace ovl {
 
 ovl_status small_sign(int k, const std::complex<double>* al, const std::complex<double>* be,
                       const std::complex<double>* de, std::complex<double>* y, int method, double* hint_c,
-                      int* hint_s);
+                      int* hint_s, int* ritz_count);
 void set_sign_concurrency(int n);
 
 struct DirectWS {
@@ -258,6 +258,7 @@ struct RhsState {
   double hint_c = 0;               // (c, s) of the rational small sign, reused between checks
   int hint_s = 0;
   StopTrack trk;                   // rate-corrected stopping estimate (stoprule.h)
+  int evals = 0, ritz = 0;         // evaluations of sign(H_j) e_1, of which with new Ritz values
 };
 
 // Snapshot of rhs r from the pinned mirrors: H_k, y = sign(H_k) e_1, error estimate.
@@ -286,7 +287,8 @@ static ovl_status evaluate_rhs(DirectWS* w, int q, int r, RhsState& rs, double* 
   }
   std::vector<std::complex<double>> y(k);
   auto t0 = std::chrono::steady_clock::now();
-  ovl_status s = small_sign(k, al.data(), be.data(), de.data(), y.data(), 0, &rs.hint_c, &rs.hint_s);
+  ++rs.evals;
+  ovl_status s = small_sign(k, al.data(), be.data(), de.data(), y.data(), 0, &rs.hint_c, &rs.hint_s, &rs.ritz);
   *t_small += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (s != OVL_OK) return s;
   rs.est = 1e300;  // set by estimate_changes()
@@ -657,6 +659,8 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
       info[r].t_update_ms = nsamp ? t_upd / nsamp : 0;
       info[r].kernel_samples = nsamp;
       info[r].kernel_launches = launches;
+      info[r].evaluations = rs[r].evals;
+      info[r].ritz_evaluations = rs[r].ritz;
     }
   }
   if (lat->server_mode) {  // the server accounts device memory per request

@@ -21,11 +21,18 @@ double zolotarev(int n, double lo, double hi, double* omega, double* sigma);
 struct MultiWS {
   int nrhs = 0, s = 0, f64 = -1, vol = 0, m = 0;
   bool refine = false;
-  // refinement buffers (FP64, native layout): residual, two stencil temporaries, a canonical
-  // copy of the residual, reduction scratch, and the single-pole coefficients {1}, {0}
+  // refinement (reliable updates): the correction systems (A^2 - sigma_i) e = r^(i) of up to
+  // `grp` (rhs, shift) pairs are solved as one batch; per system: FP64 residual, two stencil
+  // temporaries and a canonical copy (native layout), its FP32 BiCG state (gms / gv), its seed
+  // shift and tolerance; plus the single-pole coefficients {1}, {0} and the shifts sigma_i
+  int grp = 0;
   double2 *res = nullptr, *t1 = nullptr, *t2 = nullptr, *ecan = nullptr;
-  double *rpart = nullptr, *rout = nullptr, *one_zero = nullptr;
+  double *rpart = nullptr, *rout = nullptr, *one_zero = nullptr, *sg_all = nullptr, *gsig = nullptr, *gtol = nullptr;
   unsigned* rcount = nullptr;
+  MsDev gms;
+  MsVecs gv;
+  double* h_gout = nullptr;  // pinned [grp] squared residual norms
+  int* h_gst = nullptr;      // pinned [grp] statuses of the correction solves
   MsDev ms;
   MsVecs v;
   char* dev = nullptr;
@@ -54,6 +61,8 @@ void free_multi_ws(MultiWS* w) {
   }
   if (w->dev) cudaFreeAsync(w->dev, w->stream);
   if (w->h_status) cudaFreeHost(w->h_status);
+  if (w->h_gout) cudaFreeHost(w->h_gout);
+  if (w->h_gst) cudaFreeHost(w->h_gst);
   if (w->stream) cudaStreamDestroy(w->stream);
   for (auto e : w->ev)
     if (e) cudaEventDestroy(e);
@@ -106,9 +115,23 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m,
   size_t o_do = take((size_t)nrhs * 2 * std::max(m, 1) * 16);
   size_t o_ls = take((size_t)std::max(m, 1) * 8);
   const size_t rn = refine ? n : 0;
+  // correction batch: at most kRefineGroup systems and about kRefineBytes of buffers
+  // (per system 9 FP32 vectors + 5 FP64 vectors)
+  const size_t per_sys = n * (9 * 8 + 5 * 16);
+  const int grp = refine ? (int)std::max<size_t>(1, std::min<size_t>({(size_t)nrhs * s, (size_t)kRefineGroup,
+                                                                       kRefineBytes / per_sys}))
+                         : 0;
+  const size_t gq = (size_t)grp;
   size_t o_xs = take((size_t)nrhs * s * rn * 16), o_r64 = take((size_t)nrhs * rn * 16);
-  size_t o_res = take(rn * 16), o_t1 = take(rn * 16), o_t2 = take(rn * 16), o_ec = take(rn * 16);
-  size_t o_rp = take((size_t)vec_blocks(lat->g) * 8), o_ro = take(8), o_oz = take(16), o_rc = take(4);
+  size_t o_res = take(gq * rn * 16), o_t1 = take(gq * rn * 16), o_t2 = take(gq * rn * 16), o_ec = take(gq * rn * 16);
+  size_t o_rp = take(std::max<size_t>(1, gq) * vec_blocks(lat->g) * 8), o_ro = take(std::max<size_t>(1, gq) * 8),
+         o_oz = take(16), o_rc = take(std::max<size_t>(1, gq) * 4);
+  size_t o_gvec[9];
+  for (int i = 0; i < 9; ++i) o_gvec[i] = take(gq * rn * 8);
+  size_t o_gX = take(gq * rn * 16), o_gk = take(gq * 4), o_gst = take(gq * 4), o_gseed = take(gq * 8 * 16),
+         o_gz = take(gq * 3 * 16), o_ga = take(gq * 16), o_gb = take(gq * 16), o_gact = take(gq * 4),
+         o_gpa = take(gq * nblk * 4 * 8), o_gcn = take(gq * 4), o_sga = take((size_t)s * 8), o_gsig = take(gq * 8),
+         o_gtol = take(gq * 8);
   if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete w;
     set_error("apply_sign: cannot create a stream");
@@ -150,6 +173,7 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m,
   ms.count = (unsigned*)(b + o_cn);
   w->dots = (double2*)(b + o_do);
   w->lam_sign = (double*)(b + o_ls);
+  w->grp = grp;
   if (refine) {
     w->v.xs = (double2*)(b + o_xs);
     w->v.r64 = (double2*)(b + o_r64);
@@ -157,6 +181,27 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m,
     w->t1 = (double2*)(b + o_t1);
     w->t2 = (double2*)(b + o_t2);
     w->ecan = (double2*)(b + o_ec);
+    void** gp[9] = {&w->gv.r, &w->gv.rt, &w->gv.p, &w->gv.pt, &w->gv.t, &w->gv.tt, &w->gv.q, &w->gv.qt, &w->gv.ps};
+    for (int i = 0; i < 9; ++i) *gp[i] = b + o_gvec[i];
+    w->gv.X = (double2*)(b + o_gX);
+    MsDev& gm = w->gms;
+    gm.nrhs = grp;
+    gm.s = 1;
+    gm.nblk = nblk;
+    gm.k = (int*)(b + o_gk);
+    gm.status = (int*)(b + o_gst);
+    gm.seed = (double2*)(b + o_gseed);
+    gm.zeta = (double2*)(b + o_gz);
+    gm.ash = (double2*)(b + o_ga);
+    gm.bsh = (double2*)(b + o_gb);
+    gm.active = (int*)(b + o_gact);
+    gm.part = (double*)(b + o_gpa);
+    gm.count = (unsigned*)(b + o_gcn);
+    w->sg_all = (double*)(b + o_sga);
+    w->gsig = (double*)(b + o_gsig);
+    w->gtol = (double*)(b + o_gtol);
+    gm.sig1v = w->gsig;
+    gm.tolv = w->gtol;
   }
   w->rpart = (double*)(b + o_rp);
   w->rout = (double*)(b + o_ro);
@@ -166,8 +211,13 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m,
   bool ev_ok = true;
   for (int q = 0; q < 2; ++q)
     for (int i = 0; i < 4; ++i) ev_ok = ev_ok && cudaEventCreate(&w->tev[q][i]) == cudaSuccess;
+  w->gms.omega = w->one_zero;
+  w->gms.dsig = w->one_zero + 1;
   if (!ev_ok || cudaMemsetAsync(ms.count, 0, (size_t)nrhs * 4, w->stream) != cudaSuccess ||
-      cudaMemsetAsync(w->rcount, 0, 4, w->stream) != cudaSuccess ||
+      cudaMemsetAsync(w->rcount, 0, std::max<size_t>(1, gq) * 4, w->stream) != cudaSuccess ||
+      (grp > 0 && cudaMemsetAsync(w->gms.count, 0, gq * 4, w->stream) != cudaSuccess) ||
+      (grp > 0 && cudaMallocHost(&w->h_gout, gq * 8) != cudaSuccess) ||
+      (grp > 0 && cudaMallocHost(&w->h_gst, gq * 4) != cudaSuccess) ||
       cudaMemcpy(w->one_zero, oz, 16, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMallocHost(&w->h_status, (size_t)4 * nrhs * sizeof(int)) != cudaSuccess ||
       cudaEventCreateWithFlags(&w->ev[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -367,53 +417,67 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
   int ref_sweeps = 0, ref_iters = 0;
   double ref_worst = 0;
   if (refine) {
-    MsDev mi = ms;  // one-rhs, one-shift BiCG on the same buffers (the multishift pass is over)
-    mi.nrhs = 1;
-    mi.s = 1;
-    mi.omega = w->one_zero;
-    mi.dsig = w->one_zero + 1;
-    MsVecs vi = v;
-    vi.xs = vi.r64 = vi.xp = nullptr;
-    for (int r = 0; r < nrhs && ref_worst >= 0; ++r) {
-      const double r0 = seed[(size_t)r * 8 + 4].x;
-      for (int i = 0; i < s; ++i) {
-        double2* xi = v.xs + ((size_t)r * s + i) * n;
-        double resn = 0;
-        for (int sweep = 0;; ++sweep) {
-          OVL_CHECK_CUDA(launch_dslash(g, U, LINK_F64, true, p->m_W, p->mu, false, true, true, true, 1, xi, w->t1, st));
-          OVL_CHECK_CUDA(launch_dslash(g, U, LINK_F64, true, p->m_W, p->mu, false, true, true, true, 1, w->t1, w->t2, st));
-          OVL_CHECK_CUDA(launch_ms_residual(g, v.r64 + (size_t)r * n, w->t2, xi, sg[i], w->res, w->rpart, w->rcount,
-                                            w->rout, st));
-          launches += 3;
-          double rr = 0;
-          OVL_CHECK_CUDA(cudaMemcpyAsync(&rr, w->rout, 8, cudaMemcpyDeviceToHost, st));
-          OVL_CHECK_CUDA(cudaStreamSynchronize(st));
-          resn = std::sqrt(rr);
-          if (!(resn > p->tol * r0) || sweep >= kMaxRefineSweeps) break;
-          ++ref_sweeps;
-          // FP32 correction: (A^2 - sigma_i) e = res to a relative accuracy the FP32 iteration reaches
-          mi.sigma1 = sg[i];
-          mi.tol = std::max(2.0 * kFp32Floor, std::min(0.5, 0.3 * p->tol * r0 / resn));
-          OVL_CHECK_CUDA(launch_from_native(g, 1, true, w->res, true, w->ecan, st));
-          OVL_CHECK_CUDA(launch_ms_start(g, false, mi, vi, w->ecan, 0, nullptr, nullptr, nullptr, nullptr, st));
-          launches += 2;
-          int it = 0, stat = 0;
-          while (it < p->k_max) {
-            int ns = std::min(chunk, p->k_max - it);
-            for (int q = 0; q < ns; ++q) OVL_CHECK_CUDA(launch_ms_step(g, U, lf, false, p->m_W, p->mu, mi, vi, st));
-            it += ns;
-            launches += 4 * ns;
-            OVL_CHECK_CUDA(cudaMemcpyAsync(&stat, mi.status, 4, cudaMemcpyDeviceToHost, st));
-            OVL_CHECK_CUDA(cudaStreamSynchronize(st));
-            if (stat != 0) break;
-          }
-          ref_iters += it;
-          if (stat == 1) break;  // breakdown of the correction solve: keep the best x^(i)
-          OVL_CHECK_CUDA(launch_axpy_f64(g, 1, vi.X, xi, st));
-          launches += 1;
+    // The (rhs, shift) systems j = rhs*s + i are refined in batches of up to grp: per sweep, the
+    // FP64 residuals r^(i) = r - (A^2 - sigma_i) x^(i) of the batch (two FP64 stencils over the
+    // batch), then for the systems above tol one batched FP32 BiCG solve of
+    // (A^2 - sigma_i) e = r^(i) (each system its own shift and relative target), x^(i) += e.
+    // Systems already converged get a zero right-hand side, which the solve skips.
+    const int total = nrhs * s, grp = w->grp;
+    MsDev gm = w->gms;
+    MsVecs gvv = w->gv;
+    gvv.xs = gvv.r64 = gvv.xp = nullptr;
+    OVL_CHECK_CUDA(cudaMemcpyAsync(w->sg_all, sg.data(), s * 8, cudaMemcpyHostToDevice, st));
+    std::vector<double> gsig(grp), gtol(grp);
+    for (int j0 = 0; j0 < total; j0 += grp) {
+      const int gn = std::min(grp, total - j0);
+      gm.nrhs = gn;
+      double2* xg = v.xs + (size_t)j0 * n;
+      std::vector<double> resn(gn, 0.0), r0(gn);
+      for (int j = 0; j < gn; ++j) r0[j] = seed[(size_t)((j0 + j) / s) * 8 + 4].x;
+      for (int sweep = 0;; ++sweep) {
+        OVL_CHECK_CUDA(launch_dslash(g, U, LINK_F64, true, p->m_W, p->mu, false, true, true, true, gn, xg, w->t1, st));
+        OVL_CHECK_CUDA(launch_dslash(g, U, LINK_F64, true, p->m_W, p->mu, false, true, true, true, gn, w->t1, w->t2, st));
+        OVL_CHECK_CUDA(launch_ms_residual_batch(g, j0, gn, s, v.r64, w->t2, xg, w->sg_all, w->res, w->rpart,
+                                                w->rcount, w->rout, st));
+        launches += 3;
+        OVL_CHECK_CUDA(cudaMemcpyAsync(w->h_gout, w->rout, gn * 8, cudaMemcpyDeviceToHost, st));
+        OVL_CHECK_CUDA(cudaStreamSynchronize(st));
+        int need = 0;
+        for (int j = 0; j < gn; ++j) {
+          resn[j] = std::sqrt(w->h_gout[j]);
+          if (resn[j] > p->tol * r0[j]) ++need;
         }
-        ref_worst = std::max(ref_worst, r0 > 0 ? resn / r0 : 0.0);
+        if (need == 0 || sweep >= kMaxRefineSweeps) break;
+        ++ref_sweeps;
+        for (int j = 0; j < gn; ++j) {
+          const bool above = resn[j] > p->tol * r0[j];
+          gsig[j] = sg[(j0 + j) % s];
+          // the FP32 iteration only needs to take this system's residual below tol
+          gtol[j] = above ? std::max(2.0 * kFp32Floor, std::min(0.5, 0.3 * p->tol * r0[j] / resn[j])) : 0.5;
+          if (!above) OVL_CHECK_CUDA(cudaMemsetAsync(w->res + (size_t)j * n, 0, n * 16, st));
+        }
+        OVL_CHECK_CUDA(cudaMemcpyAsync(w->gsig, gsig.data(), gn * 8, cudaMemcpyHostToDevice, st));
+        OVL_CHECK_CUDA(cudaMemcpyAsync(w->gtol, gtol.data(), gn * 8, cudaMemcpyHostToDevice, st));
+        OVL_CHECK_CUDA(launch_from_native(g, gn, true, w->res, true, w->ecan, st));
+        OVL_CHECK_CUDA(launch_ms_start(g, false, gm, gvv, w->ecan, 0, nullptr, nullptr, nullptr, nullptr, st));
+        launches += 2;
+        int it = 0;
+        while (it < p->k_max) {
+          int ns = std::min(chunk, p->k_max - it);
+          for (int q = 0; q < ns; ++q) OVL_CHECK_CUDA(launch_ms_step(g, U, lf, false, p->m_W, p->mu, gm, gvv, st));
+          it += ns;
+          launches += 4 * ns;
+          OVL_CHECK_CUDA(cudaMemcpyAsync(w->h_gst, gm.status, gn * 4, cudaMemcpyDeviceToHost, st));
+          OVL_CHECK_CUDA(cudaStreamSynchronize(st));
+          bool running = false;
+          for (int j = 0; j < gn; ++j) running = running || w->h_gst[j] == 0;
+          if (!running) break;
+        }
+        ref_iters += it;
+        OVL_CHECK_CUDA(launch_axpy_f64_masked(g, gn, gm.status, gvv.X, xg, st));
+        launches += 1;
       }
+      for (int j = 0; j < gn; ++j) ref_worst = std::max(ref_worst, r0[j] > 0 ? resn[j] / r0[j] : 0.0);
     }
     OVL_CHECK_CUDA(launch_ms_combine_shifts(g, nrhs, s, w->omega, v.xs, v.X, st));
     launches += 1;
@@ -458,6 +522,8 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
       info[r].t_update_ms = nsamp ? t_upd / nsamp : 0;
       info[r].kernel_samples = nsamp;
       info[r].kernel_launches = launches;
+      info[r].evaluations = 0;
+      info[r].ritz_evaluations = 0;
     }
   }
   if (result != OVL_OK) set_error("apply_sign: at least one right-hand side ended with status %d", result);

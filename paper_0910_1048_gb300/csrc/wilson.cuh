@@ -11,6 +11,8 @@
 // Only h (2 spins x 3 colours) is multiplied by the link.
 #pragma once
 
+#include <cmath>
+
 #include "common.h"
 
 #if defined(__CUDACC__)
@@ -44,50 +46,70 @@ OVL_HD void project(const Spin<R>& p, Half<R>& h) {
   }
 }
 
-// acc += (h, -/+ N h): the full spinor of the projected hop.
+// a*b + c, one fused operation on host and device.
+template <class R>
+OVL_HD R mad(R a, R b, R c) {
+#if defined(__CUDA_ARCH__)
+  return fma(a, b, c);
+#else
+  return std::fma(a, b, c);
+#endif
+}
+
+// a += f * rot(h) with rot = identity (ROT 0), i (1), -1 (2), -i (3): two fused operations.
+template <int ROT, class R>
+OVL_HD void acc_rot(cplx<R>& a, R f, const cplx<R>& h) {
+  const R vr = ROT == 0 ? h.re : ROT == 1 ? -h.im : ROT == 2 ? -h.re : h.im;
+  const R vi = ROT == 0 ? h.im : ROT == 1 ? h.re : ROT == 2 ? -h.im : -h.re;
+  a.re = mad(f, vr, a.re);
+  a.im = mad(f, vi, a.im);
+}
+
+// acc += f (h, -/+ N h): the full spinor of the projected hop, with the hop coefficient f
+// folded into the accumulation.
 template <int MU, bool FWD, class R>
-OVL_HD void reconstruct_add(Spin<R>& acc, const Half<R>& h) {
+OVL_HD void reconstruct_add(Spin<R>& acc, const Half<R>& h, R f) {
+  // lower rows: N h takes (h1, h0) for MU 0, 1 and (h0, h1) for MU 2, 3
+  constexpr int i2 = MU < 2 ? 1 : 0, i3 = MU < 2 ? 0 : 1;
+  // rotation applied to each: MU 0: FWD (-i, -i) / BWD (i, i); MU 1: (-1, 1) / (1, -1);
+  // MU 2: (-i, i) / (i, -i); MU 3: (-1, -1) / (1, 1)
+  constexpr int r2 = MU == 0 ? (FWD ? 3 : 1) : MU == 1 ? (FWD ? 2 : 0) : MU == 2 ? (FWD ? 3 : 1) : (FWD ? 2 : 0);
+  constexpr int r3 = MU == 0 ? (FWD ? 3 : 1) : MU == 1 ? (FWD ? 0 : 2) : MU == 2 ? (FWD ? 1 : 3) : (FWD ? 2 : 0);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    acc.c[0][a] = acc.c[0][a] + h.c[0][a];
-    acc.c[1][a] = acc.c[1][a] + h.c[1][a];
-    if (MU == 0) {  // N h = (i h1, i h0)
-      acc.c[2][a] = acc.c[2][a] + (FWD ? times_mi(h.c[1][a]) : times_i(h.c[1][a]));
-      acc.c[3][a] = acc.c[3][a] + (FWD ? times_mi(h.c[0][a]) : times_i(h.c[0][a]));
-    } else if (MU == 1) {  // N h = (h1, -h0)
-      acc.c[2][a] = FWD ? acc.c[2][a] - h.c[1][a] : acc.c[2][a] + h.c[1][a];
-      acc.c[3][a] = FWD ? acc.c[3][a] + h.c[0][a] : acc.c[3][a] - h.c[0][a];
-    } else if (MU == 2) {  // N h = (i h0, -i h1)
-      acc.c[2][a] = acc.c[2][a] + (FWD ? times_mi(h.c[0][a]) : times_i(h.c[0][a]));
-      acc.c[3][a] = acc.c[3][a] + (FWD ? times_i(h.c[1][a]) : times_mi(h.c[1][a]));
-    } else {  // N h = (h0, h1)
-      acc.c[2][a] = FWD ? acc.c[2][a] - h.c[0][a] : acc.c[2][a] + h.c[0][a];
-      acc.c[3][a] = FWD ? acc.c[3][a] - h.c[1][a] : acc.c[3][a] + h.c[1][a];
-    }
+    acc_rot<0>(acc.c[0][a], f, h.c[0][a]);
+    acc_rot<0>(acc.c[1][a], f, h.c[1][a]);
+    acc_rot<r2>(acc.c[2][a], f, h.c[i2][a]);
+    acc_rot<r3>(acc.c[3][a], f, h.c[i3][a]);
   }
 }
 
-// out = U h (DAG false) or U^H h (DAG true), colour multiply of both half-spinor rows.
+// out = U h (DAG false) or U^H h (DAG true), colour multiply of both half-spinor rows as
+// chains of fused multiply-adds (the first product seeds the chain).
 template <bool DAG, class R>
 OVL_HD void su3_mul(const Mat3<R>& u, const Half<R>& h, Half<R>& out) {
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      cplx<R> acc = mk<R>(0, 0);
+      // m_b = U[a][b] or conj(U[b][a]); out = sum_b m_b h_b
+      const R sg = DAG ? (R)-1 : (R)1;  // sign of Im m_b
+      cplx<R> m = DAG ? u.m[0][a] : u.m[a][0];
+      const cplx<R>& x = h.c[s][0];
+      R re = m.re * x.re;
+      R im = m.re * x.im;
+      re = mad(-sg * m.im, x.im, re);
+      im = mad(sg * m.im, x.re, im);
 #pragma unroll
-      for (int b = 0; b < 3; ++b) acc = acc + (DAG ? cdot(u.m[b][a], h.c[s][b]) : u.m[a][b] * h.c[s][b]);
-      out.c[s][a] = acc;
+      for (int b = 1; b < 3; ++b) {
+        m = DAG ? u.m[b][a] : u.m[a][b];
+        const cplx<R>& y = h.c[s][b];
+        re = mad(m.re, y.re, mad(-sg * m.im, y.im, re));
+        im = mad(m.re, y.im, mad(sg * m.im, y.re, im));
+      }
+      out.c[s][a] = mk<R>(re, im);
     }
   }
-}
-
-template <class R>
-OVL_HD void scale_half(Half<R>& h, R f) {
-#pragma unroll
-  for (int s = 0; s < 2; ++s)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) h.c[s][a] = f * h.c[s][a];
 }
 
 // ------------------------------------------------------------------ link loads
@@ -167,8 +189,7 @@ OVL_HD void hop_dir(const Geom& g, const Links& U, int s, const Nbr& n, R kf, R 
     project<MU, true>(p, h);
     load_link<LF>(U, MU, s, g.vol, u);
     su3_mul<false>(u, h, hu);
-    scale_half(hu, kf);
-    reconstruct_add<MU, true>(acc, hu);
+    reconstruct_add<MU, true>(acc, hu, kf);
   }
   {
     Spin<R> p;
@@ -176,8 +197,7 @@ OVL_HD void hop_dir(const Geom& g, const Links& U, int s, const Nbr& n, R kf, R 
     project<MU, false>(p, h);
     load_link<LF>(U, MU, n.b[MU], g.vol, u);
     su3_mul<true>(u, h, hu);
-    scale_half(hu, kb);
-    reconstruct_add<MU, false>(acc, hu);
+    reconstruct_add<MU, false>(acc, hu, kb);
   }
 }
 

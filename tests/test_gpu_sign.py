@@ -98,9 +98,12 @@ def p4(problem_4444):
 
 
 def test_c1_plain_lanczos_vs_dense(ovl, ctx, p4):
-    """4^4, mu = 0.3, FP64, no deflation: rel.err <= 1e-10 against the eigendecomposition."""
+    """4^4, mu = 0.3, FP64, no deflation: rel.err <= 1e-10 against the eigendecomposition.
+    The stopping tolerance sits a factor 3 below the bar: near 1e-11 the change between
+    evaluations reaches the rounding floor of FP64 two-sided Lanczos without reorthogonalisation
+    at this k, so a 1e-11 stopping tolerance is not always attainable."""
     lat = _lat(ovl, ctx, p4["dims"], p4["links"], ovl.OVL_F64)
-    st, info, x = _solve(ovl, lat, p4["b"], mu=0.3, tol=1e-11, k_max=1200, check_every=25)
+    st, info, x = _solve(ovl, lat, p4["b"], mu=0.3, tol=3e-11, k_max=1200, check_every=25)
     assert st == ovl.OVL_OK, info
     assert _rel(x, p4["xstar"]) < 1e-10
     ovl.ovl_destroy_lattice(lat)
