@@ -43,6 +43,19 @@ void set_sign_concurrency(int n) { g_sign_concurrency = std::max(1, n); }
 
 namespace {
 
+// Principal square root of a + ib (branch cut on the negative real axis, like std::sqrt) from
+// the half-angle identities: with r = |z|, t = sqrt((r + |a|) / 2), sqrt(z) = (t, b / 2t) for
+// a >= 0 and (|b| / 2t, sign(b) t) for a < 0.
+inline cz csqrt_fast(cz z) {
+  const double a = z.real(), b = z.imag();
+  if (a == 0.0 && b == 0.0) return cz(0.0, 0.0);
+  const double r = std::sqrt(a * a + b * b);
+  const double t = std::sqrt(0.5 * (r + std::fabs(a)));
+  if (a >= 0.0) return cz(t, b / (2.0 * t));
+  return cz(std::fabs(b) / (2.0 * t), std::copysign(t, b));
+}
+
+
 struct Rot {
   int p;
   cz c, s;
@@ -73,7 +86,8 @@ CsqlResult cs_qr(std::vector<cz> d, std::vector<cz> e) {
   const double eps = 1e-15;
   long long budget = 60LL * k + 100;
   res.rots.reserve((size_t)k * 8);
-  auto negligible = [&](int i) { return std::abs(e[i]) <= eps * (std::abs(d[i]) + std::abs(d[i + 1])); };
+  // |e_i| <= eps (|d_i| + |d_i+1|) in squared magnitudes (no square roots in the scan)
+  auto negligible = [&](int i) { return std::norm(e[i]) <= eps * eps * (std::norm(d[i]) + std::norm(d[i + 1])); };
   int hi = k - 1;
   while (hi > 0) {
     if (negligible(hi - 1)) {
@@ -88,7 +102,7 @@ CsqlResult cs_qr(std::vector<cz> d, std::vector<cz> e) {
     // Wilkinson shift: eigenvalue of the trailing 2x2 closer to d[hi]
     cz a = d[hi - 1], b = d[hi], ee = e[hi - 1];
     cz half = 0.5 * (a - b);
-    cz disc = std::sqrt(half * half + ee * ee);
+    cz disc = csqrt_fast(half * half + ee * ee);
     cz m1 = 0.5 * (a + b) + disc, m2 = 0.5 * (a + b) - disc;
     cz shift = std::abs(m1 - b) < std::abs(m2 - b) ? m1 : m2;
     cz x = d[lo] - shift, z = e[lo];
@@ -285,7 +299,8 @@ bool cs_eigs(std::vector<cz> d, std::vector<cz> e, std::vector<cz>& lam) {
   const int k = (int)d.size();
   const double eps = 1e-15;
   long long budget = 60LL * k + 100;
-  auto negligible = [&](int i) { return std::abs(e[i]) <= eps * (std::abs(d[i]) + std::abs(d[i + 1])); };
+  // |e_i| <= eps (|d_i| + |d_i+1|) in squared magnitudes (no square roots in the scan)
+  auto negligible = [&](int i) { return std::norm(e[i]) <= eps * eps * (std::norm(d[i]) + std::norm(d[i + 1])); };
   int hi = k - 1;
   while (hi > 0) {
     if (negligible(hi - 1)) {
@@ -299,16 +314,20 @@ bool cs_eigs(std::vector<cz> d, std::vector<cz> e, std::vector<cz>& lam) {
     if (--budget < 0) return false;
     cz a = d[hi - 1], b = d[hi], ee = e[hi - 1];
     cz half = 0.5 * (a - b);
-    cz disc = std::sqrt(half * half + ee * ee);
+    cz disc = csqrt_fast(half * half + ee * ee);
     cz m1 = 0.5 * (a + b) + disc, m2 = 0.5 * (a + b) - disc;
     cz shift = std::abs(m1 - b) < std::abs(m2 - b) ? m1 : m2;
     cz x = d[lo] - shift, z = e[lo];
     for (int p = lo; p < hi; ++p) {
       const int q = p + 1;
-      cz rho = std::sqrt(x * x + z * z);
-      double scale = std::sqrt(std::norm(x) + std::norm(z));
-      if (!(std::abs(rho) > 1e-8 * scale) || scale == 0.0) return false;
-      cz c = x / rho, s = -z / rho;
+      // complex orthogonal rotation: c = x / rho, s = -z / rho with rho^2 = x^2 + z^2; it fails
+      // (the complex symmetric QR breaks down) when |x^2 + z^2| << |x|^2 + |z|^2
+      const cz rho2 = x * x + z * z;
+      const double scale2 = std::norm(x) + std::norm(z);
+      if (!(std::norm(rho2) > 1e-32 * scale2 * scale2) || scale2 == 0.0) return false;
+      const cz rho = csqrt_fast(rho2);
+      const cz inv = std::conj(rho) * (1.0 / std::norm(rho));
+      cz c = x * inv, s = -z * inv;
       if (p > lo) e[p - 1] = rho;
       cz dp = d[p], dq = d[q], ep = e[p];
       cz c2 = c * c, s2 = s * s, cs = c * s;
@@ -364,77 +383,79 @@ bool choose_scale(const std::vector<cz>& lam, double eps, int s_max, double* c_o
   return true;
 }
 
-// out = g_s(c H) v = c H sum_i omega_i (c^2 H^2 - sigma_i)^-1 v (Eq. pfe_s), banded solves.
-void rational_apply(int k, const cz* al, const cz* be, const cz* de, double c, int s, const cz* v, cz* out) {
-  // H^2 bands: d0 main, u1/u2 upper, l1/l2 lower
-  std::vector<cz> d0(k), u1(k, 0.0), u2(k, 0.0), l1(k, 0.0), l2(k, 0.0);
+// |re| + |im|: the pivoting magnitude of the tridiagonal solves (no square root).
+inline double abs1(cz z) { return std::fabs(z.real()) + std::fabs(z.imag()); }
+inline cz cinv(cz z) { return std::conj(z) * (1.0 / std::norm(z)); }
+
+// Solve (c H + z) x = b in place (b -> x) for tridiagonal H (diag al, super be, sub de) by
+// Gaussian elimination with partial pivoting (one row interchange at most per step; the
+// interchange fills a second superdiagonal). d, du, dl, du2 are scratch of length k.
+// Returns false if a pivot is zero.
+inline bool tri_solve(int k, const cz* al, const cz* be, const cz* de, double c, cz z, cz* b, cz* d, cz* du, cz* dl,
+                      cz* du2) {
   for (int i = 0; i < k; ++i) {
-    cz t = al[i] * al[i];
-    if (i > 0) t += de[i - 1] * be[i - 1];
-    if (i + 1 < k) t += be[i] * de[i];
-    d0[i] = t;
+    d[i] = c * al[i] + z;
     if (i + 1 < k) {
-      u1[i] = al[i] * be[i] + be[i] * al[i + 1];
-      l1[i] = de[i] * al[i] + al[i + 1] * de[i];
+      du[i] = c * be[i];
+      dl[i] = c * de[i];
     }
-    if (i + 2 < k) {
-      u2[i] = be[i] * be[i + 1];
-      l2[i] = de[i + 1] * de[i];
+    du2[i] = 0.0;
+  }
+  for (int i = 0; i + 1 < k; ++i) {
+    if (abs1(d[i]) >= abs1(dl[i])) {
+      if (d[i] == cz(0.0)) return false;
+      const cz f = dl[i] * cinv(d[i]);
+      d[i + 1] -= f * du[i];
+      b[i + 1] -= f * b[i];
+    } else {  // interchange rows i and i+1
+      const cz f = d[i] * cinv(dl[i]);
+      d[i] = dl[i];
+      const cz t = d[i + 1];
+      d[i + 1] = du[i] - f * t;
+      if (i + 2 < k) {
+        du2[i] = du[i + 1];
+        du[i + 1] = -f * du2[i];
+      }
+      du[i] = t;
+      const cz bi = b[i];
+      b[i] = b[i + 1];
+      b[i + 1] = bi - f * b[i + 1];
     }
   }
-  const double c2 = c * c;
+  if (d[k - 1] == cz(0.0)) return false;
+  b[k - 1] *= cinv(d[k - 1]);
+  if (k > 1) b[k - 2] = (b[k - 2] - du[k - 2] * b[k - 1]) * cinv(d[k - 2]);
+  for (int i = k - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) * cinv(d[i]);
+  return true;
+}
+
+// out = g_s(c H) v = c H sum_i omega_i (c^2 H^2 - sigma_i)^-1 v (Eq. pfe_s). With sigma_i =
+// -t_i^2 (t_i = tan theta_i > 0) each shifted matrix factors into tridiagonal ones,
+// c^2 H^2 + t_i^2 = (c H - i t_i)(c H + i t_i), so each pole costs two tridiagonal solves
+// (no cancellation: the factors are applied one after the other). Returns false if a solve
+// meets a zero pivot.
+bool rational_apply(int k, const cz* al, const cz* be, const cz* de, double c, int s, const cz* v, cz* out) {
   // the s shifted solves are independent: split them over host threads, each summing its
   // own shifts in order, then add the per-thread sums in thread order (deterministic)
   const int hw = std::max(1, (int)std::thread::hardware_concurrency() / std::max(1, g_sign_concurrency));
-  const int nth = std::max(1, std::min({hw, 16, s, (int)((size_t)s * k / 20000 + 1)}));
+  const int nth = std::max(1, std::min({hw, 16, s, (int)((size_t)s * k / 40000 + 1)}));
   std::vector<std::vector<cz>> part(nth, std::vector<cz>(k, 0.0));
+  std::vector<char> ok(nth, 1);
   auto work = [&](int tid) {
-  std::vector<cz>& acc = part[tid];
-  // band storage for LU with partial pivoting: row i holds columns i-2..i+4 (7 entries)
-  const int W = 7, OFF = 2;
-  std::vector<cz> a((size_t)k * W), rhs(k);
-  for (int sh = 1 + tid; sh <= s; sh += nth) {
-    const double th = 3.14159265358979323846 / (2.0 * s) * (sh - 0.5);
-    const double om = 1.0 / (s * std::cos(th) * std::cos(th));
-    const double sg = -std::tan(th) * std::tan(th);
-    std::fill(a.begin(), a.end(), cz(0));
-    for (int i = 0; i < k; ++i) {
-      cz* r = &a[(size_t)i * W];
-      if (i >= 2) r[OFF - 2] = c2 * l2[i - 2];
-      if (i >= 1) r[OFF - 1] = c2 * l1[i - 1];
-      r[OFF] = c2 * d0[i] - sg;
-      if (i + 1 < k) r[OFF + 1] = c2 * u1[i];
-      if (i + 2 < k) r[OFF + 2] = c2 * u2[i];
-      rhs[i] = v[i];
-    }
-    auto at = [&](int i, int j) -> cz& { return a[(size_t)i * W + (j - i + OFF)]; };
-    for (int col = 0; col < k; ++col) {
-      int last = std::min(k - 1, col + 2);
-      int piv = col;
-      double best = std::abs(at(col, col));
-      for (int r = col + 1; r <= last; ++r)
-        if (std::abs(at(r, col)) > best) best = std::abs(at(r, col)), piv = r;
-      int cend = std::min(k - 1, col + 4);
-      if (piv != col) {
-        for (int j = col; j <= cend; ++j) std::swap(at(piv, j), at(col, j));
-        std::swap(rhs[piv], rhs[col]);
+    std::vector<cz>& acc = part[tid];
+    std::vector<cz> x(k), d(k), du(k), dl(k), du2(k);
+    for (int sh = 1 + tid; sh <= s; sh += nth) {
+      const double th = 3.14159265358979323846 / (2.0 * s) * (sh - 0.5);
+      const double om = 1.0 / (s * std::cos(th) * std::cos(th));
+      const double t = std::tan(th);  // sigma = -t^2
+      std::copy(v, v + k, x.begin());
+      if (!tri_solve(k, al, be, de, c, cz(0.0, -t), x.data(), d.data(), du.data(), dl.data(), du2.data()) ||
+          !tri_solve(k, al, be, de, c, cz(0.0, t), x.data(), d.data(), du.data(), dl.data(), du2.data())) {
+        ok[tid] = 0;
+        return;
       }
-      cz pinv = 1.0 / at(col, col);
-      for (int r = col + 1; r <= last; ++r) {
-        cz f = at(r, col) * pinv;
-        if (f == cz(0)) continue;
-        for (int j = col; j <= cend; ++j) at(r, j) -= f * at(col, j);
-        rhs[r] -= f * rhs[col];
-      }
+      for (int i = 0; i < k; ++i) acc[i] += om * x[i];
     }
-    for (int i = k - 1; i >= 0; --i) {
-      cz t = rhs[i];
-      int cend = std::min(k - 1, i + 4);
-      for (int j = i + 1; j <= cend; ++j) t -= at(i, j) * rhs[j];
-      rhs[i] = t / at(i, i);
-    }
-    for (int i = 0; i < k; ++i) acc[i] += om * rhs[i];
-  }
   };
   if (nth == 1) {
     work(0);
@@ -444,6 +465,8 @@ void rational_apply(int k, const cz* al, const cz* be, const cz* de, double c, i
     work(0);
     for (auto& t : th) t.join();
   }
+  for (int t = 0; t < nth; ++t)
+    if (!ok[t]) return false;
   std::vector<cz> acc(k, 0.0);
   for (int t = 0; t < nth; ++t)
     for (int i = 0; i < k; ++i) acc[i] += part[t][i];
@@ -453,6 +476,7 @@ void rational_apply(int k, const cz* al, const cz* be, const cz* de, double c, i
     if (i + 1 < k) t += be[i] * acc[i + 1];
     out[i] = c * t;
   }
+  return true;
 }
 
 }  // namespace
@@ -483,8 +507,9 @@ ovl_status small_sign_rational(int k, const cz* al, const cz* be, const cz* de, 
     }
     std::vector<cz> e1(k, 0.0), chk(k);
     e1[0] = 1.0;
-    rational_apply(k, al, be, de, *hint_c, *hint_s, e1.data(), y);
-    rational_apply(k, al, be, de, *hint_c, *hint_s, y, chk.data());
+    if (!rational_apply(k, al, be, de, *hint_c, *hint_s, e1.data(), y) ||
+        !rational_apply(k, al, be, de, *hint_c, *hint_s, y, chk.data()))
+      continue;  // a singular shifted factor: try the next (c, s)
     double r = std::abs(chk[0] - 1.0);
     for (int i = 1; i < k; ++i) r = std::max(r, std::abs(chk[i]));
     if (inv_res) *inv_res = r;
