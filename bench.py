@@ -53,6 +53,14 @@ WORKLOADS = {
     "lattice8_mu0-0.1-0.3_defl16_multishift_f32_f64rel": dict(dims=(8, 8, 8, 8), mus=(0.0, 0.1, 0.3), m=16,
                                                                 method="multishift", precision="f32",
                                                                 tol=1e-8, k_max=5000),
+    # 12^4, mu = 0.3: multishift BiCG with 20 Zolotarev poles on [|lambda|_min, |lambda|_max] from a
+    # spectrum estimate, FP16 12-real links and FP32 vectors under FP64 reliable updates, 1e-8;
+    # and the FP32 direct method (FP64 scalars and sign(H_k)), whose FP32 vectors bound it near 1e-5
+    "lattice12_mu0.3_multishift_zolo20_f16links_f64rel": dict(dims=(12, 12, 12, 12), mus=(0.3,), m=0,
+                                                               method="multishift", precision="f16", tol=1e-8,
+                                                               k_max=8000, rational="zolotarev", s=20),
+    "lattice12_mu0.3_direct_f32": dict(dims=(12, 12, 12, 12), mus=(0.3,), m=0, method="direct", precision="f32",
+                                       tol=1e-5, k_max=3000),
     # 16^4, mu = 0.2, 16 Gaussian sources in one batch sharing the links, FP32 vectors with FP64
     # recurrence scalars and sign(H_k); FP32 vectors bound the attainable accuracy near 1e-5
     "lattice16_mu0.2_nrhs16_direct_f32": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0, method="direct",
@@ -203,6 +211,13 @@ def _setup(ovl, ctx, wl, rng_seed=0, cache=None):
                 d.update(lam=lam, R=R, L=L, gap=gap, setup_s=time.time() - t0)
                 stored.update({key + "_lam": lam, key + "_R": R, key + "_L": L, key + "_gap": np.array(gap)})
                 changed = True
+        if wl["method"] == "multishift" and wl["m"] == 0:
+            if key + "_lo" in stored:
+                d["gap"] = float(stored[key + "_lo"])
+            else:
+                d["gap"] = spectrum.smallest_modulus(ovl, lat, -2.0, mu)
+                stored[key + "_lo"] = np.array(d["gap"])
+                changed = True
         if wl["method"] == "multishift":
             if key + "_hi" in stored:
                 d["spec_hi"] = float(stored[key + "_hi"])
@@ -222,6 +237,8 @@ def _params(ovl, wl, d):
               use_deflation=1 if wl["m"] > 0 else 0, check_every=25)
     if wl["method"] == "multishift":
         kw.update(method=ovl.OVL_MULTISHIFT_BICG, spec_lo=0.98 * d["gap"], spec_hi=d["spec_hi"], check_every=20)
+        if wl.get("rational") == "zolotarev":
+            kw.update(rational_kind=ovl.OVL_RAT_ZOLOTAREV, s=wl["s"])
     return ovl.ovl_sign_params_default(**kw)
 
 
@@ -478,10 +495,11 @@ def run_ours(args, wl):
 
 
 SERVING = dict(sizes=(4, 8, 12, 16), fields_per_size=5, tols=(1e-6, 1e-8, 1e-10), nrhs_max=8, seed=42,
-               k_max={4: 1200, 8: 1500, 12: 1500, 16: 1200}, mean_interarrival_s=0.05)
+               k_max_by_tol={1e-6: 600, 1e-8: 1200, 1e-10: 2000}, k_max_cap={4: 2000, 8: 2000, 12: 2000, 16: 1500},
+               mean_interarrival_s=0.25)
 
 
-def serving_sample(ovl, ctx, n_requests, mem_budget=160 << 30, max_slots=8):
+def serving_sample(ovl, ctx, n_requests, mem_budget=200 << 30, max_slots=8):
     """A bounded sample of the serving stream: Poisson arrivals of sign(H_W(mu)) b requests on 20
     resident gauge fields (5 per lattice size 4^4, 8^4, 12^4, 16^4, seeds 0-19), mu ~ U[0, 1],
     tol in {1e-6, 1e-8, 1e-10}, 1-8 Gaussian sources each (seed 42), FP64 direct method, admitted
@@ -515,7 +533,8 @@ def serving_sample(ovl, ctx, n_requests, mem_budget=160 << 30, max_slots=8):
         now = time.perf_counter()
         while i < len(reqs) and now >= t_next:
             r = reqs[i]
-            tk = ovl.ovl_submit(srv, ids[r["fi"]], r["b"], r["mu"], r["tol"], k_max=cfg["k_max"][r["L"]])
+            k_max = min(cfg["k_max_by_tol"][r["tol"]], cfg["k_max_cap"][r["L"]])
+            tk = ovl.ovl_submit(srv, ids[r["fi"]], r["b"], r["mu"], r["tol"], k_max=k_max)
             pending[tk] = (r, now)
             i += 1
             if i < len(reqs):
@@ -543,7 +562,8 @@ def serving_sample(ovl, ctx, n_requests, mem_budget=160 << 30, max_slots=8):
             "p50_ms_by_size": {k: float(np.percentile(v, 50)) for k, v in sorted(per_size.items())},
             "sample": "%d requests of the 2000-request stream's distribution (Poisson, mean gap %g s)"
                       % (n_requests, cfg["mean_interarrival_s"]), "mem_budget_bytes": mem_budget,
-            "max_slots": max_slots, "k_max": {"%d^4" % k: v for k, v in cfg["k_max"].items()}}
+            "max_slots": max_slots, "k_max_by_tol": {"%g" % k: v for k, v in cfg["k_max_by_tol"].items()},
+            "k_max_cap": {"%d^4" % k: v for k, v in cfg["k_max_cap"].items()}}
 
 
 def _oracle_sample(wl, iterations, seconds):
@@ -626,7 +646,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=24,
+    ap.add_argument("--serving-requests", type=int, default=16,
                     help="requests in the serving sample added to the line (0: none)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed-precision companion line and the stencil bandwidth figure")

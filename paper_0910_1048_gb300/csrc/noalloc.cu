@@ -267,6 +267,10 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
     OVL_TRY(changes(evaluated));
     for (int r : todo) {
       Rhs& s = rs[r];
+      if (es[r] != OVL_OK && !final_snapshot && h_st[r] == 0) {  // as in the allocating driver
+        s.trk.next = stop_next_eval(queued, chunk, -1.0);
+        continue;
+      }
       bool converged = false;
       if (es[r] == OVL_OK && h_st[r] == 0) {
         stop_record(s.trk, s.k, s.est < 1e299 ? s.est : -1.0);

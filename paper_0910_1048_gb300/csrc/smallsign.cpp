@@ -518,8 +518,10 @@ ovl_status small_sign_rational(int k, const cz* al, const cz* be, const cz* de, 
   return OVL_ENOCONV;
 }
 
-// method 0 auto (rational, then QL eigenvectors, then Newton), 1 QL only, 2 Newton only,
-// 3 rational only. hint_c/hint_s (may be null) carry (c, s) between calls on growing H_k.
+// method 0 auto (rational, then QL eigenvectors, then Newton up to k = kNewtonMaxK: its O(k^3)
+// steps would dominate a solve beyond), 1 QL only, 2 Newton only, 3 rational only.
+// hint_c/hint_s (may be null) carry (c, s) between calls on growing H_k.
+constexpr int kNewtonMaxK = 200;
 ovl_status small_sign(int k, const cz* al, const cz* be, const cz* de, cz* y, int method, double* hint_c = nullptr,
                       int* hint_s = nullptr, int* ritz_count = nullptr) {
   if (k < 1) {
@@ -546,6 +548,11 @@ ovl_status small_sign(int k, const cz* al, const cz* be, const cz* de, cz* y, in
     double chk = 0;
     ovl_status s = small_sign_ql(k, al, be, de, y, &chk);
     if (s == OVL_OK || method == 1 || s == OVL_EILLPOSED) return s;
+  }
+  if (method == 0 && k > kNewtonMaxK) {
+    set_error("small_sign: no route reached the accuracy check at k = %d (H_k too close to singular "
+              "or to the imaginary axis)", k);
+    return OVL_ENOCONV;
   }
   return small_sign_newton(k, al, be, de, y);
 }

@@ -565,6 +565,12 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
       for (int r : todo) {
         RhsState& s = rs[r];
         ovl_status es = es_r[r];
+        if (es != OVL_OK && !final_snapshot && w->h[q].status[r] == 0) {
+          // this H_j defeated every small-sign route (a Ritz value near the imaginary axis, which
+          // later steps may move away): keep the last good y and evaluate again later
+          s.trk.next = stop_next_eval(jq, chunk, -1.0);
+          continue;
+        }
         bool converged = false;
         if (es == OVL_OK && w->h[q].status[r] == 0) {
           stop_record(s.trk, s.k, s.est < 1e299 ? s.est : -1.0);

@@ -71,6 +71,19 @@ def critical_eigenpairs(ovl, lat, m_W, mu, m, tol=1e-10, solve_tol=1e-12, k_max=
     return lam, R, L, gap, info
 
 
+def smallest_modulus(ovl, lat, m_W, mu, tol=1e-4):
+    """|lambda|_min of H_W(mu): the largest-modulus eigenvalue of A^-1 by ARPACK, every A^-1
+    application a GPU multishift solve with the single pole (omega, sigma) = (1, 0)."""
+    import scipy.sparse.linalg as spla
+
+    n = ovl.ovl_lattice_n(lat)
+    mv, _, keep = _inverse_operator(ovl, lat, m_W, mu, 1e-8, 20000)
+    op = spla.LinearOperator((n, n), matvec=mv, dtype=np.complex128)
+    th = spla.eigs(op, k=1, which="LM", tol=tol, return_eigenvectors=False, v0=np.ones(n, np.complex128))
+    del keep
+    return float(1.0 / np.abs(th).max())
+
+
 def largest_modulus(ovl, lat, m_W, mu, tol=1e-6):
     """|lambda|_max of H_W(mu) by ARPACK with GPU matrix-vector products."""
     import scipy.sparse.linalg as spla
