@@ -32,7 +32,10 @@ struct MultiWS {
   MsDev gms;
   MsVecs gv;
   double* h_gout = nullptr;  // pinned [grp] squared residual norms
-  int* h_gst = nullptr;      // pinned [grp] statuses of the correction solves
+  int* h_gst = nullptr;      // pinned [2][grp] statuses of the correction solves (two chunks in flight)
+  cudaGraphExec_t rgraph = nullptr;  // one chunk of correction iterations for rg_gn systems
+  int rg_gn = -1, rg_chunk = 0, rg_lf = -1;
+  double rg_mw = 0, rg_mu = 0;
   MsDev ms;
   MsVecs v;
   char* dev = nullptr;
@@ -54,6 +57,7 @@ struct MultiWS {
 
 void free_multi_ws(MultiWS* w) {
   if (!w) return;
+  if (w->rgraph) cudaGraphExecDestroy(w->rgraph);
   for (int q = 0; q < 2; ++q) {
     if (w->graph[q]) cudaGraphExecDestroy(w->graph[q]);
     for (auto e : w->tev[q])
@@ -217,7 +221,7 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m,
       cudaMemsetAsync(w->rcount, 0, std::max<size_t>(1, gq) * 4, w->stream) != cudaSuccess ||
       (grp > 0 && cudaMemsetAsync(w->gms.count, 0, gq * 4, w->stream) != cudaSuccess) ||
       (grp > 0 && cudaMallocHost(&w->h_gout, gq * 8) != cudaSuccess) ||
-      (grp > 0 && cudaMallocHost(&w->h_gst, gq * 4) != cudaSuccess) ||
+      (grp > 0 && cudaMallocHost(&w->h_gst, 2 * gq * 4) != cudaSuccess) ||
       cudaMemcpy(w->one_zero, oz, 16, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMallocHost(&w->h_status, (size_t)4 * nrhs * sizeof(int)) != cudaSuccess ||
       cudaEventCreateWithFlags(&w->ev[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -461,19 +465,65 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
         OVL_CHECK_CUDA(launch_from_native(g, gn, true, w->res, true, w->ecan, st));
         OVL_CHECK_CUDA(launch_ms_start(g, false, gm, gvv, w->ecan, 0, nullptr, nullptr, nullptr, nullptr, st));
         launches += 2;
-        int it = 0;
-        while (it < p->k_max) {
-          int ns = std::min(chunk, p->k_max - it);
-          for (int q = 0; q < ns; ++q) OVL_CHECK_CUDA(launch_ms_step(g, U, lf, false, p->m_W, p->mu, gm, gvv, st));
+        // chunks of correction iterations, a CUDA graph per (batch size, chunk); two chunks in
+        // flight so the host's status check overlaps the next chunk (finished systems skip it)
+        const bool rg = p->use_graphs != 0 && chunk > 1;
+        if (rg && !(w->rgraph && w->rg_gn == gn && w->rg_chunk == chunk && w->rg_lf == lf && w->rg_mw == p->m_W &&
+                    w->rg_mu == p->mu)) {
+          if (w->rgraph) cudaGraphExecDestroy(w->rgraph);
+          w->rgraph = nullptr;
+          cudaGraph_t gr;
+          OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+          cudaError_t e = cudaSuccess;
+          for (int q = 0; q < chunk && e == cudaSuccess; ++q) e = launch_ms_step(g, U, lf, false, p->m_W, p->mu, gm, gvv, st);
+          cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+          OVL_CHECK_CUDA(e);
+          OVL_CHECK_CUDA(e2);
+          e = cudaGraphInstantiate(&w->rgraph, gr, 0);
+          cudaGraphDestroy(gr);
+          OVL_CHECK_CUDA(e);
+          w->rg_gn = gn;
+          w->rg_chunk = chunk;
+          w->rg_lf = lf;
+          w->rg_mw = p->m_W;
+          w->rg_mu = p->mu;
+        }
+        int it = 0, slot = 0;
+        std::vector<int> inflight;
+        auto queue_chunk = [&]() -> cudaError_t {
+          const int ns = std::min(chunk, p->k_max - it);
+          cudaError_t e = cudaSuccess;
+          if (rg && ns == chunk) {
+            e = cudaGraphLaunch(w->rgraph, st);
+          } else {
+            for (int q = 0; q < ns && e == cudaSuccess; ++q) e = launch_ms_step(g, U, lf, false, p->m_W, p->mu, gm, gvv, st);
+          }
+          if (e) return e;
           it += ns;
           launches += 4 * ns;
-          OVL_CHECK_CUDA(cudaMemcpyAsync(w->h_gst, gm.status, gn * 4, cudaMemcpyDeviceToHost, st));
-          OVL_CHECK_CUDA(cudaStreamSynchronize(st));
+          if ((e = cudaMemcpyAsync(w->h_gst + (size_t)slot * grp, gm.status, gn * 4, cudaMemcpyDeviceToHost, st)))
+            return e;
+          if ((e = cudaEventRecord(w->ev[slot], st))) return e;
+          inflight.push_back(slot);
+          slot ^= 1;
+          return cudaSuccess;
+        };
+        OVL_CHECK_CUDA(queue_chunk());
+        while (!inflight.empty()) {
+          if (it < p->k_max && inflight.size() < 2) OVL_CHECK_CUDA(queue_chunk());
+          const int q = inflight.front();
+          inflight.erase(inflight.begin());
+          OVL_CHECK_CUDA(cudaEventSynchronize(w->ev[q]));
           bool running = false;
-          for (int j = 0; j < gn; ++j) running = running || w->h_gst[j] == 0;
+          for (int j = 0; j < gn; ++j) running = running || w->h_gst[(size_t)q * grp + j] == 0;
           if (!running) break;
         }
-        ref_iters += it;
+        // iterations actually run (a chunk queued after the last system finished skips them all)
+        OVL_CHECK_CUDA(cudaMemcpyAsync(w->h_gst, gm.k, gn * 4, cudaMemcpyDeviceToHost, st));
+        OVL_CHECK_CUDA(cudaStreamSynchronize(st));
+        int kmax_run = 0;
+        for (int j = 0; j < gn; ++j) kmax_run = std::max(kmax_run, w->h_gst[j]);
+        ref_iters += kmax_run;
         OVL_CHECK_CUDA(launch_axpy_f64_masked(g, gn, gm.status, gvv.X, xg, st));
         launches += 1;
       }

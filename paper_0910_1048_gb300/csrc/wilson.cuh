@@ -178,27 +178,25 @@ struct HopCoef {
   R ks, ktf, ktb;
 };
 
-// acc += hop terms for one direction (forward and backward), input p loaded by `ld`.
-template <int MU, int LF, class R, class Load>
-OVL_HD void hop_dir(const Geom& g, const Links& U, int s, const Nbr& n, R kf, R kb, Load ld, Spin<R>& acc) {
+// acc += one hop term: forward (FWD, from site x + mu with U_mu(x)) or backward (from x - mu with
+// U_mu(x - mu)^H), coefficient k, input p loaded by `ld`.
+template <int MU, bool FWD, int LF, class R, class Load>
+OVL_HD void hop_one(const Geom& g, const Links& U, int s, const Nbr& n, R k, Load ld, Spin<R>& acc) {
   Mat3<R> u;
   Half<R> h, hu;
-  {
-    Spin<R> p;
-    ld(n.f[MU], p);
-    project<MU, true>(p, h);
-    load_link<LF>(U, MU, s, g.vol, u);
-    su3_mul<false>(u, h, hu);
-    reconstruct_add<MU, true>(acc, hu, kf);
-  }
-  {
-    Spin<R> p;
-    ld(n.b[MU], p);
-    project<MU, false>(p, h);
-    load_link<LF>(U, MU, n.b[MU], g.vol, u);
-    su3_mul<true>(u, h, hu);
-    reconstruct_add<MU, false>(acc, hu, kb);
-  }
+  Spin<R> p;
+  ld(FWD ? n.f[MU] : n.b[MU], p);
+  project<MU, FWD>(p, h);
+  load_link<LF>(U, MU, FWD ? s : n.b[MU], g.vol, u);
+  su3_mul<!FWD>(u, h, hu);
+  reconstruct_add<MU, FWD>(acc, hu, k);
+}
+
+// acc += hop terms for one direction (forward and backward).
+template <int MU, int LF, class R, class Load>
+OVL_HD void hop_dir(const Geom& g, const Links& U, int s, const Nbr& n, R kf, R kb, Load ld, Spin<R>& acc) {
+  hop_one<MU, true, LF>(g, U, s, n, kf, ld, acc);
+  hop_one<MU, false, LF>(g, U, s, n, kb, ld, acc);
 }
 
 // out = D_W psi at site s (psi loaded through `ld`), coefficients c.

@@ -3,6 +3,8 @@
   python -m paper_0910_1048_gb300.profile_cases dslash --L 28      FP32 / FP16-link stencil, 3 launches each
   python -m paper_0910_1048_gb300.profile_cases pair --L 8         fixed-k FP64 direct solve (pair stencil)
   python -m paper_0910_1048_gb300.profile_cases multishift --L 8   fixed-iteration FP64 multishift solve
+  python -m paper_0910_1048_gb300.profile_cases multishift --L 8 --prec f16   1e-8 FP16-link solve with
+                                                                    FP64 reliable updates
   python -m paper_0910_1048_gb300.profile_cases summarize launches.csv out.txt
 
 The cases hold at most a few GB on the device and a handful of launches, so that a capture with
@@ -42,7 +44,7 @@ def case_dslash(L: int):
     ovl.ovl_ctx_destroy(ctx)
 
 
-def case_pair(L: int, multishift: bool = False):
+def case_pair(L: int, multishift: bool = False, prec: str = "f64"):
     import torch
 
     import paper_0910_1048_gb300 as ovl
@@ -54,11 +56,17 @@ def case_pair(L: int, multishift: bool = False):
     ovl.ovl_set_links(lat, synth.gauge_links(dims, 0), ovl.OVL_F64)
     b = torch.from_numpy(synth.gaussian_source(dims, 1000)).cuda()
     x = torch.empty_like(b)
+    pr = {"f64": ovl.OVL_PREC_F64, "f32": ovl.OVL_PREC_F32, "f16": ovl.OVL_PREC_F32_F16LINKS}[prec]
+    if prec != "f64":
+        ovl.ovl_set_links(lat, synth.gauge_links(dims, 0), ovl.OVL_F64 | ovl.OVL_F32 | ovl.OVL_F16R12)
     if multishift:
-        p = ovl.ovl_sign_params_default(method=ovl.OVL_MULTISHIFT_BICG, mu=0.3, tol=0.0, k_max=30, spec_lo=0.06,
-                                        spec_hi=2.7, use_graphs=0)
+        # FP64: 30 iterations with the poles of tol 1e-15; reduced precision: a 1e-8 solve, whose
+        # FP64 reliable updates run batched correction solves after the main pass
+        p = ovl.ovl_sign_params_default(method=ovl.OVL_MULTISHIFT_BICG, mu=0.3, tol=0.0 if prec == "f64" else 1e-8,
+                                        k_max=30 if prec == "f64" else 3000, spec_lo=0.06, spec_hi=2.7, use_graphs=0,
+                                        precision=pr)
     else:
-        p = ovl.ovl_sign_params_default(mu=0.3, fixed_k=30, use_graphs=0)
+        p = ovl.ovl_sign_params_default(mu=0.3, fixed_k=30, use_graphs=0, precision=pr)
     ovl.ovl_apply_sign(lat, p, b, x)
     torch.cuda.synchronize()
     ovl.ovl_destroy_lattice(lat)
@@ -91,13 +99,14 @@ def main():
     ap.add_argument("case", choices=["dslash", "pair", "multishift", "summarize"])
     ap.add_argument("args", nargs="*")
     ap.add_argument("--L", type=int, default=8)
+    ap.add_argument("--prec", choices=["f64", "f32", "f16"], default="f64")
     a = ap.parse_args()
     if a.case == "dslash":
         case_dslash(a.L)
     elif a.case == "pair":
-        case_pair(a.L)
+        case_pair(a.L, prec=a.prec)
     elif a.case == "multishift":
-        case_pair(a.L, multishift=True)
+        case_pair(a.L, multishift=True, prec=a.prec)
     else:
         summarize(*a.args)
     print("ok")
