@@ -9,6 +9,11 @@ fused pair stencil) from CUDA events recorded around its launches inside the lib
 `--impl reference` times the oracle (plain FP64 CPU restatement of Algorithm 4) on the
 host cores on a bounded sample of the same workload.
 
+Beside the headline the line carries `mixed_precision` (the workload's mixed-precision companion,
+e.g. FP16-link multishift with FP64 reliable updates at the same 1e-8, and its speedup over the
+line's value), `dslash` (kernel-only stencil bandwidth on 32^4) and `serving` (a bounded sample of
+the serving stream: p50/p99 latency, solves/s, success rate); `--no-extras` skips them.
+
 Multi-GPU: replicas only (each rank solves its own copies, no collective on the data path);
 value = solves of all ranks / max over ranks of the timed region.
 """
@@ -61,6 +66,18 @@ WORKLOADS = {
                                                                k_max=8000, rational="zolotarev", s=20),
     "lattice12_mu0.3_direct_f32": dict(dims=(12, 12, 12, 12), mus=(0.3,), m=0, method="direct", precision="f32",
                                        tol=1e-5, k_max=3000),
+    # the plain FP64 two-sided Lanczos path on the same 12^4 problem at 1e-8, with the mixed-precision
+    # multishift line above as its companion (speedup reported in the line)
+    "lattice12_mu0.3_direct_f64": dict(dims=(12, 12, 12, 12), mus=(0.3,), m=0, method="direct", precision="f64",
+                                       tol=1e-8, k_max=3000, mixed="lattice12_mu0.3_multishift_zolo20_f16links_f64rel"),
+    # 16^4, mu = 0.2 at 1e-8: FP64 direct on batches of 4 sources (16 sources at this k do not fit in
+    # HBM: the basis is nrhs x k x 12.6 MB) against the mixed-precision multishift on all 16 at once
+    "lattice16_mu0.2_nrhs4_direct_f64": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0, method="direct",
+                                             precision="f64", tol=1e-8, k_max=2500, nrhs=4,
+                                             mixed="lattice16_mu0.2_nrhs16_multishift_f16links_f64rel"),
+    "lattice16_mu0.2_nrhs16_multishift_f16links_f64rel": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0,
+                                                               method="multishift", precision="f16", tol=1e-8,
+                                                               k_max=8000, rational="zolotarev", s=20, nrhs=16),
     # 16^4, mu = 0.2, 16 Gaussian sources in one batch sharing the links, FP32 vectors with FP64
     # recurrence scalars and sign(H_k); FP32 vectors bound the attainable accuracy near 1e-5
     "lattice16_mu0.2_nrhs16_direct_f32": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0, method="direct",
@@ -71,11 +88,19 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "lattice8_mu0-0.1-0.3_defl16_direct_f64"
 
-# Algorithmic traffic / work of one launch of the fused pair stencil per site:
-# two spinors in (neighbours read once each: 2 x 24 reals), 4 links per site (18 reals each;
-# FP16 12-real: 12 halves), two spinors out; flops: 2 x 1368 per site.
-PAIR_BYTES_PER_SITE = {"f64": 2 * 192 + 576 + 2 * 192, "f32": 2 * 96 + 288 + 2 * 96, "f16": 2 * 96 + 96 + 2 * 96}
+# Algorithmic traffic / work of one launch of the fused pair stencil per site: per right-hand
+# side two spinors in (neighbours read once each: 2 x 24 reals) and two out; the 4 links of a site
+# (18 reals each; FP16 12-real: 12 halves) once per launch, shared by all right-hand sides of a
+# batch; flops: 2 x 1368 per site and right-hand side.
+PAIR_LINK_BYTES_PER_SITE = {"f64": 576, "f32": 288, "f16": 96}
+PAIR_SPINOR_BYTES_PER_SITE = {"f64": 4 * 192, "f32": 4 * 96, "f16": 4 * 96}
+PAIR_BYTES_PER_SITE = {k: PAIR_LINK_BYTES_PER_SITE[k] + PAIR_SPINOR_BYTES_PER_SITE[k] for k in PAIR_LINK_BYTES_PER_SITE}
 PAIR_FLOPS_PER_SITE = 2 * 1368
+
+
+def pair_bytes(prec, vol, nrhs):
+    """Algorithmic bytes of one pair-stencil launch over `nrhs` right-hand sides."""
+    return vol * (PAIR_LINK_BYTES_PER_SITE[prec] + nrhs * PAIR_SPINOR_BYTES_PER_SITE[prec])
 
 # FP64 FMA throughput of this pool's GB300 in TFLOP/s (the FMA-chain probe in csrc/probe/; the
 # bench runs the probe itself and uses this value only when the probe library is missing)
@@ -387,9 +412,9 @@ def _roofline(wl, infos, fp64_peak, fp64_src):
         return {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
                 "frac": (ach / fp64_peak) if ach else None, "traffic": traffic, "peak_source": fp64_src,
                 "algorithmic_flops_per_launch": flops,
-                "algorithmic_bytes_per_launch": PAIR_BYTES_PER_SITE["f64"] * vol * nr,
+                "algorithmic_bytes_per_launch": pair_bytes("f64", vol, nr),
                 "note": "FP64 kernels are bound by GB300's FP64 pipe (ncu: FP64 pipe 65-74% active)"}
-    byts = PAIR_BYTES_PER_SITE[prec] * vol * nr
+    byts = pair_bytes(prec, vol, nr)
     ach = byts / (t_pair * 1e-3) / 1e9 if t_pair else None
     return {"kernel": kernel, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": ach / peaks["hbm_gbs"] if ach else None, "traffic": traffic,
@@ -467,14 +492,16 @@ def run_ours(args, wl):
         wm = WORKLOADS[mixed]
         lat_m, _, _, pm = _setup(ovl, ctx, wm, cache=args.setup_cache)
         ovl.ovl_destroy_lattice(lat_m)
+        bm = _sources(wm)  # the companion's own batch (it may hold more right-hand sides)
+        sps_m = len(pm) * wm.get("nrhs", 1)
         with ClockSampler(local) as clk2:
-            tm, em, im, am = _time_workload(ovl, ctx, args, wm, u, pm, b, flush, world)
-        vm = throughput(args.steps, solves_per_step, world, tm)
+            tm, em, im, am = _time_workload(ovl, ctx, args, wm, u, pm, bm, flush, world)
+        vm = throughput(args.steps, sps_m, world, tm)
         _, pms, stm, lm = _summary(wm, pm, im, am)
         res["mixed_precision"] = {
             "workload": mixed, "method": wm["method"], "precision": wm["precision"], "tol": wm["tol"],
-            "value": vm, "unit": UNIT, "ms_per_step": tm / args.steps,
-            "speedup_vs_line_value": vm / value, "e2e_value": solves / em, "statuses": stm,
+            "nrhs": wm.get("nrhs", 1), "value": vm, "unit": UNIT, "ms_per_step": tm / args.steps,
+            "speedup_vs_line_value": vm / value, "e2e_value": args.steps * sps_m * world / em, "statuses": stm,
             "accuracy_half_sign2b_minus_b": am, "per_mu": pms, "gpu_launches": int(lm),
             "roofline": _roofline(wm, im, fp64_peak, fp64_src), "clocks": clk2.summary()}
     if not args.no_extras:

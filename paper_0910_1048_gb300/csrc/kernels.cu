@@ -307,13 +307,18 @@ __global__ void __launch_bounds__(2 * kPairSites) k_lz_pair(Geom g, Links U, Hop
     if (!is_w) {
       dslash_site<LF, R>(g, U, s, cp, Loader<R, true>{vj, g.vol, false}, ov);
       const R sv = (R)lz.sv[o + j];
+      // all loads of w_j before the stores of Av (the compiler cannot reorder them across stores
+      // that might alias, which would serialise twelve memory round trips)
+      cplx<R> wv[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) wv[c] = ldc<R>(wj, (size_t)c * g.vol + s);
       cplx<R> a = mk<R>(0, 0);
 #pragma unroll
       for (int c = 0; c < 12; ++c) {
         cplx<R> x = sv * ov.c[c / 3][c % 3];
         if (c >= 6) x = -x;  // gamma5
         stc<R>(av + (size_t)rhs * n, (size_t)c * g.vol + s, x);
-        a = a + cdot(ldc<R>(wj, (size_t)c * g.vol + s), x);
+        a = a + cdot(wv[c], x);
       }
       acc[0].add(a.re);
       acc[1].add(a.im);
@@ -363,13 +368,16 @@ __global__ void __launch_bounds__(8 * kSplitSites) k_lz_pair_split(Geom g, Links
   Red<R> acc[2];
   pair_split<R, LF>(g, U, cp, cm, vj, wj, sm, [&](int which, int s, Spin<R>& out) {
     if (which == 0) {
+      cplx<R> wv[12];  // loads first (see k_lz_pair)
+#pragma unroll
+      for (int c = 0; c < 12; ++c) wv[c] = ldc<R>(wj, (size_t)c * g.vol + s);
       cplx<R> a = mk<R>(0, 0);
 #pragma unroll
       for (int c = 0; c < 12; ++c) {
         cplx<R> x = sv * out.c[c / 3][c % 3];
         if (c >= 6) x = -x;  // gamma5
         stc<R>(av + (size_t)rhs * n, (size_t)c * g.vol + s, x);
-        a = a + cdot(ldc<R>(wj, (size_t)c * g.vol + s), x);
+        a = a + cdot(wv[c], x);
       }
       acc[0].add(a.re);
       acc[1].add(a.im);
@@ -474,48 +482,48 @@ cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64,
                                 const LzDev& lz, const LzVecs& vec, cudaStream_t st, int variant) {
   if (variant < 0) variant = tuned_pair_variant(g.vol, f64 ? 0 : lf);
   if (variant < 0) variant = use_split(g) ? 1 : 0;
+  const HopCoef<double> dp = hop_coef<double>(m_w, mu), dm = hop_coef<double>(m_w, -mu);
+  const HopCoef<float> fp = hop_coef<float>(m_w, mu), fm = hop_coef<float>(m_w, -mu);
+  const double2 *dv = (const double2*)vec.vh, *dw = (const double2*)vec.wh;
+  const float2 *fv = (const float2*)vec.vh, *fw = (const float2*)vec.wh;
+  cudaError_t e;
   if (variant == 1) {
-    dim3 sgrid((g.vol + kSplitSites - 1) / kSplitSites, lz.nrhs), sblock(kSplitSites, 8);
+    dim3 grid((g.vol + kSplitSites - 1) / kSplitSites, lz.nrhs), block(kSplitSites, 8);
     if (f64)
-      k_lz_pair_split<double, LINK_F64><<<sgrid, sblock, 0, st>>>(
-          g, U, hop_coef<double>(m_w, mu), hop_coef<double>(m_w, -mu), lz, (const double2*)vec.vh,
-          (const double2*)vec.wh, (double2*)vec.av, (double2*)vec.aw);
+      e = launch_plain(k_lz_pair_split<double, LINK_F64>, grid, block, st, g, U, dp, dm, lz, dv, dw, (double2*)vec.av,
+                     (double2*)vec.aw);
     else if (lf == LINK_F16R12)
-      k_lz_pair_split<float, LINK_F16R12><<<sgrid, sblock, 0, st>>>(
-          g, U, hop_coef<float>(m_w, mu), hop_coef<float>(m_w, -mu), lz, (const float2*)vec.vh,
-          (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
+      e = launch_plain(k_lz_pair_split<float, LINK_F16R12>, grid, block, st, g, U, fp, fm, lz, fv, fw, (float2*)vec.av,
+                     (float2*)vec.aw);
     else
-      k_lz_pair_split<float, LINK_F32><<<sgrid, sblock, 0, st>>>(
-          g, U, hop_coef<float>(m_w, mu), hop_coef<float>(m_w, -mu), lz, (const float2*)vec.vh,
-          (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
-    return cudaGetLastError();
+      e = launch_plain(k_lz_pair_split<float, LINK_F32>, grid, block, st, g, U, fp, fm, lz, fv, fw, (float2*)vec.av,
+                     (float2*)vec.aw);
+  } else {
+    dim3 grid((g.vol + kPairSites - 1) / kPairSites, lz.nrhs), block(kPairSites, 2);
+    if (f64)
+      e = launch_plain(k_lz_pair<double, LINK_F64>, grid, block, st, g, U, dp, dm, lz, dv, dw, (double2*)vec.av,
+                     (double2*)vec.aw);
+    else if (lf == LINK_F16R12)
+      e = launch_plain(k_lz_pair<float, LINK_F16R12>, grid, block, st, g, U, fp, fm, lz, fv, fw, (float2*)vec.av,
+                     (float2*)vec.aw);
+    else
+      e = launch_plain(k_lz_pair<float, LINK_F32>, grid, block, st, g, U, fp, fm, lz, fv, fw, (float2*)vec.av,
+                     (float2*)vec.aw);
   }
-  dim3 pgrid((g.vol + kPairSites - 1) / kPairSites, lz.nrhs), pblock(kPairSites, 2);
-  if (f64)
-    k_lz_pair<double, LINK_F64><<<pgrid, pblock, 0, st>>>(g, U, hop_coef<double>(m_w, mu), hop_coef<double>(m_w, -mu),
-                                                           lz, (const double2*)vec.vh, (const double2*)vec.wh,
-                                                           (double2*)vec.av, (double2*)vec.aw);
-  else if (lf == LINK_F16R12)
-    k_lz_pair<float, LINK_F16R12><<<pgrid, pblock, 0, st>>>(g, U, hop_coef<float>(m_w, mu), hop_coef<float>(m_w, -mu),
-                                                             lz, (const float2*)vec.vh, (const float2*)vec.wh,
-                                                             (float2*)vec.av, (float2*)vec.aw);
-  else
-    k_lz_pair<float, LINK_F32><<<pgrid, pblock, 0, st>>>(g, U, hop_coef<float>(m_w, mu), hop_coef<float>(m_w, -mu),
-                                                          lz, (const float2*)vec.vh, (const float2*)vec.wh,
-                                                          (float2*)vec.av, (float2*)vec.aw);
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_lanczos_update(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, cudaStream_t st) {
   const int elt = vec_elts(g, lz.nrhs, f64);
   dim3 grid(vec_blocks(g, elt), lz.nrhs);
+  cudaError_t e;
   if (f64)
-    k_lz_update<double><<<grid, kVecBlock, 0, st>>>(g, lz, (double2*)vec.vh, (double2*)vec.wh,
-                                                     (const double2*)vec.av, (const double2*)vec.aw, elt);
+    e = launch_plain(k_lz_update<double>, grid, dim3(kVecBlock), st, g, lz, (double2*)vec.vh, (double2*)vec.wh,
+                   (const double2*)vec.av, (const double2*)vec.aw, elt);
   else
-    k_lz_update<float><<<grid, kVecBlock, 0, st>>>(g, lz, (float2*)vec.vh, (float2*)vec.wh, (const float2*)vec.av,
-                                                    (const float2*)vec.aw, elt);
-  return cudaGetLastError();
+    e = launch_plain(k_lz_update<float>, grid, dim3(kVecBlock), st, g, lz, (float2*)vec.vh, (float2*)vec.wh,
+                   (const float2*)vec.av, (const float2*)vec.aw, elt);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_lanczos_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, const LzDev& lz,
@@ -564,13 +572,15 @@ __global__ void __launch_bounds__(256) k_lz_combine(int vol, int kmax, const int
 // stopping estimate, whose terms are all of the size of the change itself.
 template <class R>
 __global__ void __launch_bounds__(256) k_lz_vnorms(int vol, int kmax, const int* kr, const typename V2<R>::T* vh,
-                                                   const double2* d1, const double2* d2, int kcoef, double* part,
-                                                   unsigned* count, double* out) {
+                                                   const double2* d1, const double2* d2, int kcoef, int stride,
+                                                   double* part, unsigned* count, double* out) {
   __shared__ float2 c1[256], c2[256];
   const int rhs = blockIdx.y;
   const int k = kr[rhs];
   const size_t n = (size_t)12 * vol;
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // sampled element: runs of 32 consecutive elements, one run every 32 * stride (stride 1: all)
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t e = (t >> 5) * 32 * (size_t)stride + (t & 31);
   const typename V2<R>::T* base = vh + (size_t)rhs * (kmax + 1) * n;
   cplx<float> a1 = mk<float>(0, 0), a2 = mk<float>(0, 0);
   for (int j0 = 0; j0 < k; j0 += 256) {
@@ -606,14 +616,16 @@ __global__ void __launch_bounds__(256) k_lz_vnorms(int vol, int kmax, const int*
 cudaError_t launch_lanczos_vnorms(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, const int* kr,
                                   const double2* d1, const double2* d2, int kcoef, double* part, unsigned* count,
                                   double* out, cudaStream_t st) {
-  size_t n = (size_t)12 * g.vol;
-  dim3 grid((unsigned)((n + 255) / 256), lz.nrhs);
+  const size_t n = (size_t)12 * g.vol;
+  const int stride = vnorm_stride(g);
+  const size_t ns = (n + stride - 1) / stride;  // sampled elements (upper bound)
+  dim3 grid((unsigned)((ns + 255) / 256), lz.nrhs);
   if (f64)
-    k_lz_vnorms<double><<<grid, 256, 0, st>>>(g.vol, lz.kmax, kr, (const double2*)vec.vh, d1, d2, kcoef, part, count,
-                                               out);
+    k_lz_vnorms<double><<<grid, 256, 0, st>>>(g.vol, lz.kmax, kr, (const double2*)vec.vh, d1, d2, kcoef, stride, part,
+                                               count, out);
   else
-    k_lz_vnorms<float><<<grid, 256, 0, st>>>(g.vol, lz.kmax, kr, (const float2*)vec.vh, d1, d2, kcoef, part, count,
-                                              out);
+    k_lz_vnorms<float><<<grid, 256, 0, st>>>(g.vol, lz.kmax, kr, (const float2*)vec.vh, d1, d2, kcoef, stride, part,
+                                              count, out);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,22 @@ constexpr int kBlock = 128;     // threads per block of the site-parallel kernel
 constexpr int kPairSites = 64;  // sites per block of the pair stencil (x2 threads)
 constexpr int kSplitVolume = 32768;  // below this many sites the pair stencils split each site over 8 threads
 inline bool use_split(const Geom& g) { return g.vol < kSplitVolume; }
+// Plain launch through cudaLaunchKernelEx (one call site per kernel shape, error returned).
+// Programmatic dependent launch was measured here and dropped: blocks of a waiting successor
+// hold SM slots that the concurrent solves of a step would otherwise use (8^4 FP64 pair stencil
+// 50 -> 75 us inside the step).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_plain(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cfg.attrs = nullptr;
+  cfg.numAttrs = 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Pair-stencil variant chosen by the autotuner for (volume, precision): -1 none yet,
 // 0 one thread per site, 1 split over 8 threads. Thread-safe, process-wide. (A 16-thread split,
 // one hop per thread, measured 54 us against 32 us for FP64 at 8^4: more index and reduction
@@ -94,6 +110,17 @@ cudaError_t launch_lanczos_step(const Geom& g, const Links& U, int lf, bool f64,
                                 const LzDev& lz, const LzVecs& vec, cudaStream_t st);
 // out[rhs][0..1] = ||sum_{j<k_r} d1_j vhat_j||^2, ||sum_{j<k_r} d2_j vhat_j||^2 (own scratch part,
 // count: part >= nrhs * 2 * ceil(12V/256) doubles, count >= nrhs zeros).
+// Element sampling of the stopping estimate: the norms ||V c|| of the change and of the iterate
+// enter only as a ratio, so on large lattices they are taken over runs of 32 consecutive
+// elements, one run in every 32 * stride (about 10^5 elements sampled; a fixed pattern, so the
+// estimate is deterministic); the full basis read per evaluation would otherwise cost more than
+// the steps between evaluations (16^4, 16 sources: 79 GB).
+inline int vnorm_stride(const Geom& g) {
+  const size_t n = 12 * (size_t)g.vol;
+  int st = 1;
+  while (st < 64 && n / (2 * st) >= 98304) st *= 2;
+  return st;
+}
 cudaError_t launch_lanczos_vnorms(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, const int* kr,
                                   const double2* d1, const double2* d2, int kcoef, double* part, unsigned* count,
                                   double* out, cudaStream_t st);
@@ -139,7 +166,8 @@ struct MsVecs {
   void* ps = nullptr;          // [nrhs][s][12][V] shifted directions
   double2* X = nullptr;        // [nrhs][12][V] FP64 sum_i omega_i x^(i)
   double2* xp = nullptr;       // [nrhs][12][V] FP64 x_P (nullptr without deflation)
-  double2* xs = nullptr;       // [nrhs][s][12][V] FP64 per-shift solutions (refinement only; else X)
+  double2* xs = nullptr;       // [nrhs][s][12][V] per-shift solutions (refinement only; else X): float-float
+                               // in the FP32 pass, FP64 after launch_ff_to_f64
   double2* r64 = nullptr;      // [nrhs][12][V] FP64 deflated residual r (refinement only)
 };
 
@@ -162,6 +190,8 @@ cudaError_t launch_ms_residual_batch(const Geom& g, int j0, int gn, int s, const
 cudaError_t launch_axpy_f64_masked(const Geom& g, int gn, const int* status, const double2* e, double2* x,
                                    cudaStream_t st);
 cudaError_t launch_axpy_f64(const Geom& g, int nrhs, const double2* e, double2* x, cudaStream_t st);
+// n complex values held as float-float (re hi, re lo, im hi, im lo) -> complex double, in place.
+cudaError_t launch_ff_to_f64(size_t n, double2* x, cudaStream_t st);
 cudaError_t launch_ms_combine_shifts(const Geom& g, int nrhs, int s, const double* omega, const double2* xs,
                                      double2* X, cudaStream_t st);
 // x (canonical complex128) = x_P + AX (AX native FP64, = H_W(mu) X)

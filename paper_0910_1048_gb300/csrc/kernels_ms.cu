@@ -149,14 +149,24 @@ __global__ void __launch_bounds__(2 * kPairSites) k_ms_pair(Geom g, Links U, Hop
     const R s1 = (R)(ms.sig1v ? ms.sig1v[rhs] : ms.sigma1);
     const T* pp = (const T*)(is_t ? v.pt : v.p) + voff<R>(rhs, n);
     const T* ptl = (const T*)v.pt + voff<R>(rhs, n);
+    // MODE 1: every load before the first store (stores that might alias would otherwise
+    // serialise twelve memory round trips)
+    cplx<R> pv[12], tv[12];
+    if (MODE == 1) {
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        pv[c] = ldc<R>(pp, (size_t)c * g.vol + s);
+        tv[c] = is_t ? mk<R>(0, 0) : ldc<R>(ptl, (size_t)c * g.vol + s);
+      }
+    }
     cplx<R> a = mk<R>(0, 0);
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
       cplx<R> x = o.c[c / 3][c % 3];
       if (c >= 6) x = -x;  // gamma5
       if (MODE == 1) {
-        x = x - s1 * ldc<R>(pp, (size_t)c * g.vol + s);
-        if (!is_t) a = a + cdot(ldc<R>(ptl, (size_t)c * g.vol + s), x);
+        x = x - s1 * pv[c];
+        if (!is_t) a = a + cdot(tv[c], x);
       }
       stc<R>(out, (size_t)c * g.vol + s, x);
     }
@@ -192,14 +202,22 @@ __global__ void __launch_bounds__(8 * kSplitSites) k_ms_pair_split(Geom g, Links
     T* out = (T*)(MODE == 0 ? (which ? v.tt : v.t) : (which ? v.qt : v.q)) + voff<R>(rhs, n);
     const T* pp = (const T*)(which ? v.pt : v.p) + voff<R>(rhs, n);
     const T* ptl = (const T*)v.pt + voff<R>(rhs, n);
+    cplx<R> pv[12], tv[12];  // loads first (see k_ms_pair)
+    if (MODE == 1) {
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        pv[c] = ldc<R>(pp, (size_t)c * g.vol + s);
+        tv[c] = which ? mk<R>(0, 0) : ldc<R>(ptl, (size_t)c * g.vol + s);
+      }
+    }
     cplx<R> a = mk<R>(0, 0);
 #pragma unroll
     for (int c = 0; c < 12; ++c) {
       cplx<R> x = o.c[c / 3][c % 3];
       if (c >= 6) x = -x;  // gamma5
       if (MODE == 1) {
-        x = x - s1 * ldc<R>(pp, (size_t)c * g.vol + s);
-        if (!which) a = a + cdot(ldc<R>(ptl, (size_t)c * g.vol + s), x);
+        x = x - s1 * pv[c];
+        if (!which) a = a + cdot(tv[c], x);
       }
       stc<R>(out, (size_t)c * g.vol + s, x);
     }
@@ -301,8 +319,9 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_update(Geom g, MsDev ms, MsVec
 // dirs: X += sum_i omega_i alpha^i p^i; p^i = zeta^i r + beta^i p^i; p, p~ updates.
 // FP64 kernels accumulate X term by term in double. FP32 kernels sum the iteration's terms
 // over the shifts in float-float and add that sum to the FP64 X once (the FP64 pipe is 1/64 of
-// the FP32 rate); with per-shift solutions kept (refinement), each FP32 increment alpha^i p^i
-// is added to the FP64 x^(i), whose error the FP64 residual corrections remove afterwards.
+// the FP32 rate); with per-shift solutions kept (refinement), x^(i) is held in float-float
+// (re hi, re lo, im hi, im lo: the 16 bytes of a complex double) during the pass, so the
+// increments alpha^i p^i need no FP64 arithmetic; it is converted to FP64 in place afterwards.
 template <class R>
 __global__ void __launch_bounds__(kVecBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs v) {
   using T = typename V2<R>::T;
@@ -311,16 +330,24 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs 
   if (st != 0 && st != 4) return;
   const size_t n = (size_t)12 * g.vol;
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // one vector element per thread
-  __shared__ double2 coefx[kMaxShifts], coefz[kMaxShifts], coefb[kMaxShifts], coefa[kMaxShifts];
+  // the shift coefficients in the kernel's own precision (FP32 kernels convert them once per
+  // block here, not per element: a double -> float conversion runs on the FP64 pipe)
+  using T2 = typename V2<R>::T;
+  __shared__ T2 coefx[kMaxShifts], coefz[kMaxShifts], coefb[kMaxShifts], coefa[kMaxShifts];
   __shared__ int act[kMaxShifts];
   for (int i = threadIdx.x; i < ms.s; i += blockDim.x) {
     const size_t si = (size_t)rhs * ms.s + i;
     act[i] = ms.active[si];
-    zd ai = ldc<double>(ms.ash, si);
-    coefa[i] = make_double2(ai.re, ai.im);
-    coefx[i] = make_double2(ms.omega[i] * ai.re, ms.omega[i] * ai.im);
-    coefz[i] = ms.zeta[si * 3 + 1];  // zeta_{k+1} after the rotation in update
-    coefb[i] = ms.bsh[si];
+    const zd ai = ldc<double>(ms.ash, si);
+    const double2 z = ms.zeta[si * 3 + 1], b = ms.bsh[si];  // zeta_{k+1} after the rotation in update
+    coefa[i].x = (R)ai.re;
+    coefa[i].y = (R)ai.im;
+    coefx[i].x = (R)(ms.omega[i] * ai.re);
+    coefx[i].y = (R)(ms.omega[i] * ai.im);
+    coefz[i].x = (R)z.x;
+    coefz[i].y = (R)z.y;
+    coefb[i].x = (R)b.x;
+    coefb[i].y = (R)b.y;
   }
   __syncthreads();
   if (e >= n) return;
@@ -334,44 +361,47 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs 
   double2* X = v.X + voff<R>(rhs, n);
   {
     const cplx<R> rv = ldc<R>(r, e);
-    zd xa = ldc<double>(X, e);
+    zd xa = v.xs ? mk(0.0, 0.0) : ldc<double>(X, e);  // X is not used when x^(i) are kept
     Red<R> sre, sim;  // FP32: this iteration's sum over the shifts
     for (int i = 0; i < ms.s; ++i) {
       if (!act[i]) continue;
       T* pi = ps + (size_t)i * n;
       const cplx<R> pv = ldc<R>(pi, e);
-      if (v.xs) {  // keep x^(i) itself (FP64): x^(i) += alpha^i p^i
-        double2* xi = v.xs + ((size_t)rhs * ms.s + i) * n;
-        const double2 ca = coefa[i];
+      if (v.xs) {  // keep x^(i) itself: x^(i) += alpha^i p^i
+        const T2 ca = coefa[i];
         if constexpr (sizeof(R) == 8) {
+          double2* xi = v.xs + ((size_t)rhs * ms.s + i) * n;
           stc<double>(xi, e, ldc<double>(xi, e) + mk(ca.x, ca.y) * pv);
         } else {
-          const cplx<R> inc = mk<R>((R)ca.x, (R)ca.y) * pv;
-          stc<double>(xi, e, ldc<double>(xi, e) + mk((double)inc.re, (double)inc.im));
+          float4* xi = reinterpret_cast<float4*>(v.xs + ((size_t)rhs * ms.s + i) * n);
+          const cplx<R> inc = mk<R>(ca.x, ca.y) * pv;
+          float4 x4 = xi[e];
+          const FF re = ff_add(FF{x4.x, x4.y}, FF{inc.re, 0.f}), im = ff_add(FF{x4.z, x4.w}, FF{inc.im, 0.f});
+          xi[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
         }
       } else {
-        const double2 cx = coefx[i];
+        const T2 cx = coefx[i];
         if constexpr (sizeof(R) == 8) {
           xa = xa + mk(cx.x, cx.y) * pv;
         } else {
-          const cplx<R> c = mk<R>((R)cx.x, (R)cx.y);
+          const cplx<R> c = mk<R>(cx.x, cx.y);
           sre.add(fma(c.re, pv.re, -(c.im * pv.im)));
           sim.add(fma(c.re, pv.im, c.im * pv.re));
         }
       }
       if (act[i] == 1) {
-        double2 cz = coefz[i], cb = coefb[i];
-        cplx<R> nv = mk<R>((R)cz.x, (R)cz.y) * rv + mk<R>((R)cb.x, (R)cb.y) * pv;
+        const T2 cz = coefz[i], cb = coefb[i];
+        cplx<R> nv = mk<R>(cz.x, cz.y) * rv + mk<R>(cb.x, cb.y) * pv;
         stc<R>(pi, e, nv);
       }
     }
-    if constexpr (sizeof(R) == 4) {
-      if (!v.xs) {
+    if (!v.xs) {
+      if constexpr (sizeof(R) == 4) {
         xa.re += sre.get();
         xa.im += sim.get();
       }
+      stc<double>(X, e, xa);
     }
-    stc<double>(X, e, xa);
     if (st == 0) {
       stc<R>(p, e, rv + b * ldc<R>(p, e));
       stc<R>(pt, e, ldc<R>(rt, e) + bc * ldc<R>(pt, e));
@@ -402,20 +432,19 @@ static cudaError_t ms_step_t(const Geom& g, const Links& U, double m_w, double m
   dim3 sgrid((g.vol + kSplitSites - 1) / kSplitSites, ms.nrhs), sblock(kSplitSites, 8);
   const int tv = tuned_pair_variant(g.vol, sizeof(R) == 8 ? 0 : LF);
   const bool split = tv < 0 ? use_split(g) : tv == 1;
-  if (ev) cudaEventRecord(ev[0], st);
-  if (split)
-    k_ms_pair_split<R, LF, 0><<<sgrid, sblock, 0, st>>>(g, U, cp, cm, ms, v);
-  else
-    k_ms_pair<R, LF, 0><<<pgrid, pblock, 0, st>>>(g, U, cp, cm, ms, v);
-  if (ev) cudaEventRecord(ev[1], st);
-  if (split)
-    k_ms_pair_split<R, LF, 1><<<sgrid, sblock, 0, st>>>(g, U, cp, cm, ms, v);
-  else
-    k_ms_pair<R, LF, 1><<<pgrid, pblock, 0, st>>>(g, U, cp, cm, ms, v);
   const int elt = vec_elts(g, ms.nrhs, sizeof(R) == 8);
-  k_ms_update<R><<<dim3(vec_blocks(g, elt), ms.nrhs), kVecBlock, 0, st>>>(g, ms, v, elt);
+  cudaError_t e;
+  if (ev) cudaEventRecord(ev[0], st);
+  e = split ? launch_plain(k_ms_pair_split<R, LF, 0>, sgrid, sblock, st, g, U, cp, cm, ms, v)
+            : launch_plain(k_ms_pair<R, LF, 0>, pgrid, pblock, st, g, U, cp, cm, ms, v);
+  if (e) return e;
+  if (ev) cudaEventRecord(ev[1], st);
+  e = split ? launch_plain(k_ms_pair_split<R, LF, 1>, sgrid, sblock, st, g, U, cp, cm, ms, v)
+            : launch_plain(k_ms_pair<R, LF, 1>, pgrid, pblock, st, g, U, cp, cm, ms, v);
+  if (e) return e;
+  if ((e = launch_plain(k_ms_update<R>, dim3(vec_blocks(g, elt), ms.nrhs), dim3(kVecBlock), st, g, ms, v, elt))) return e;
   if (ev) cudaEventRecord(ev[2], st);
-  k_ms_dirs<R><<<grid, kVecBlock, 0, st>>>(g, ms, v);
+  if ((e = launch_plain(k_ms_dirs<R>, grid, dim3(kVecBlock), st, g, ms, v))) return e;
   if (ev) cudaEventRecord(ev[3], st);
   return cudaGetLastError();
 }
@@ -493,6 +522,19 @@ cudaError_t launch_axpy_f64_masked(const Geom& g, int gn, const int* status, con
   size_t n = (size_t)12 * g.vol;
   dim3 grid((unsigned)((n + 255) / 256), gn);
   k_axpy_f64_masked<<<grid, 256, 0, st>>>(n, status, e, x);
+  return cudaGetLastError();
+}
+
+// Float-float complex (re hi, re lo, im hi, im lo) -> complex double, in place.
+__global__ void k_ff_to_f64(size_t n, double2* x) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 f = reinterpret_cast<const float4*>(x)[i];
+  x[i] = make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w);
+}
+
+cudaError_t launch_ff_to_f64(size_t n, double2* x, cudaStream_t st) {
+  k_ff_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x);
   return cudaGetLastError();
 }
 

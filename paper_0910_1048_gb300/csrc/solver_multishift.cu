@@ -427,6 +427,8 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
     // (A^2 - sigma_i) e = r^(i) (each system its own shift and relative target), x^(i) += e.
     // Systems already converged get a zero right-hand side, which the solve skips.
     const int total = nrhs * s, grp = w->grp;
+    OVL_CHECK_CUDA(launch_ff_to_f64((size_t)total * n, v.xs, st));
+    launches += 1;
     MsDev gm = w->gms;
     MsVecs gvv = w->gv;
     gvv.xs = gvv.r64 = gvv.xp = nullptr;

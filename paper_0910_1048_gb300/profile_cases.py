@@ -2,6 +2,7 @@
 
   python -m paper_0910_1048_gb300.profile_cases dslash --L 28      FP32 / FP16-link stencil, 3 launches each
   python -m paper_0910_1048_gb300.profile_cases pair --L 8         fixed-k FP64 direct solve (pair stencil)
+  python -m paper_0910_1048_gb300.profile_cases pair --L 16 --prec f32 --nrhs 16   the batched FP32 step
   python -m paper_0910_1048_gb300.profile_cases multishift --L 8   fixed-iteration FP64 multishift solve
   python -m paper_0910_1048_gb300.profile_cases multishift --L 8 --prec f16   1e-8 FP16-link solve with
                                                                     FP64 reliable updates
@@ -44,7 +45,7 @@ def case_dslash(L: int):
     ovl.ovl_ctx_destroy(ctx)
 
 
-def case_pair(L: int, multishift: bool = False, prec: str = "f64"):
+def case_pair(L: int, multishift: bool = False, prec: str = "f64", nrhs: int = 1):
     import torch
 
     import paper_0910_1048_gb300 as ovl
@@ -54,7 +55,7 @@ def case_pair(L: int, multishift: bool = False, prec: str = "f64"):
     dims = (L, L, L, L)
     lat = ovl.ovl_create_lattice(ctx, dims, -1)
     ovl.ovl_set_links(lat, synth.gauge_links(dims, 0), ovl.OVL_F64)
-    b = torch.from_numpy(synth.gaussian_source(dims, 1000)).cuda()
+    b = torch.from_numpy(synth.gaussian_source(dims, 1000, nrhs=nrhs if nrhs > 1 else None)).cuda()
     x = torch.empty_like(b)
     pr = {"f64": ovl.OVL_PREC_F64, "f32": ovl.OVL_PREC_F32, "f16": ovl.OVL_PREC_F32_F16LINKS}[prec]
     if prec != "f64":
@@ -100,13 +101,14 @@ def main():
     ap.add_argument("args", nargs="*")
     ap.add_argument("--L", type=int, default=8)
     ap.add_argument("--prec", choices=["f64", "f32", "f16"], default="f64")
+    ap.add_argument("--nrhs", type=int, default=1)
     a = ap.parse_args()
     if a.case == "dslash":
         case_dslash(a.L)
     elif a.case == "pair":
-        case_pair(a.L, prec=a.prec)
+        case_pair(a.L, prec=a.prec, nrhs=a.nrhs)
     elif a.case == "multishift":
-        case_pair(a.L, multishift=True, prec=a.prec)
+        case_pair(a.L, multishift=True, prec=a.prec, nrhs=a.nrhs)
     else:
         summarize(*a.args)
     print("ok")

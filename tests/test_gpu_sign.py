@@ -265,3 +265,20 @@ def test_equal_k_parity_1616(ovl, ctx, prec, tol):
     assert np.abs(de - sto["delta"]).max() < tol * np.abs(sto["delta"]).max()
     assert _rel(x, xo) < tol
     ovl.ovl_destroy_lattice(lat)
+
+
+def test_sampled_stopping_estimate_1212(ovl, ctx):
+    """12^4 FP32 direct with the stopping estimate taken over sampled elements (large lattices):
+    it must still stop with the paper's accuracy measure at the FP32 level, 0.5 |s^2 b - b| / |b|."""
+    dims = (12, 12, 12, 12)
+    u = synth.gauge_links(dims, 0)
+    lat = _lat(ovl, ctx, dims, u, ovl.OVL_F64 | ovl.OVL_F32)
+    b = synth.gaussian_source(dims, 1000)
+    kw = dict(mu=0.3, tol=1e-5, k_max=3000, check_every=25, precision=ovl.OVL_PREC_F32)
+    st, info, x = _solve(ovl, lat, b, **kw)
+    assert st == ovl.OVL_OK, info
+    st2, info2, x2 = _solve(ovl, lat, x, **kw)
+    assert st2 == ovl.OVL_OK, info2
+    acc = 0.5 * np.linalg.norm(x2 - b) / np.linalg.norm(b)
+    assert acc < 3e-5, (acc, info[0]["iterations"], info2[0]["iterations"])
+    ovl.ovl_destroy_lattice(lat)
