@@ -244,9 +244,10 @@ typedef struct {
   const void* b;            /* host complex128 [nrhs][n]; copied during ovl_submit */
 } ovl_request;
 
-/* A request loop on its own host thread: requests are admitted when their device
- * footprint fits the memory budget and a slot is free; admitted requests run
- * concurrently (continuous batching across streams). */
+/* A request loop on worker threads: requests are admitted when their device footprint fits
+ * the memory budget and a slot is free, the least estimated work first (sites x nrhs x k_max)
+ * unless the oldest request has waited more than 2 s; admitted requests run concurrently
+ * (continuous batching across streams). The admission order does not change any result. */
 ovl_status ovl_server_create(ovl_ctx* ctx, const ovl_server_cfg* cfg, ovl_server** out);
 ovl_status ovl_server_add_field(ovl_server* srv, ovl_lattice* lat, int32_t* field_id);
 /* Enqueue; *ticket identifies the request. EINVAL for a request that can never fit. */

@@ -140,8 +140,9 @@ namespace ovl {
 constexpr int kMaxShifts = 128;
 constexpr double kFp32Floor = 2e-6;   // relative residual the FP32 iteration reaches by itself
 constexpr int kMaxRefineSweeps = 8;   // FP64 residual / FP32 correction rounds per shifted system
-constexpr int kRefineGroup = 64;      // correction systems solved together in one batch
-constexpr size_t kRefineBytes = (size_t)8 << 30;  // buffer budget of that batch
+constexpr int kRefineGroup = 1024;    // correction systems solved together in one batch
+constexpr size_t kRefineBytes = (size_t)48 << 30;  // buffer budget of that batch (at most a quarter
+                                                    // of the free device memory)
 struct MsDev {
   int nrhs = 0, s = 0, nblk = 0;
   int* k = nullptr;           // [nrhs] iterations done

@@ -1,13 +1,17 @@
 // Request server: sign(H_W(mu)) b solves of mixed lattices, mu and tolerances as they arrive.
 //
-// Requests queue in arrival order. `max_slots` worker threads each take the oldest request
-// whose device footprint (Krylov basis and work vectors of a direct two-sided Lanczos
-// solve, Algorithm 4) fits in what the memory budget has left; requests that arrive while
-// others run are admitted as soon as a slot and memory free up, and their work overlaps on
-// the device (every slot solves on its own streams through a view of the field that shares
-// the field's links but not its workspace). Workspaces are allocated and released
+// Requests queue as they arrive. `max_slots` worker threads each take, among the queued
+// requests whose device footprint (Krylov basis and work vectors of a direct two-sided Lanczos
+// solve, Algorithm 4) fits in what the memory budget has left, the one with the least
+// estimated work (sites x right-hand sides x k_max, FP32 at half weight) - unless the oldest
+// request has waited longer than kMaxWait, which is then served first (no starvation of large
+// requests; while it does not fit, smaller ones are not admitted past it). Requests that
+// arrive while others run are admitted as soon as a slot and memory free up, and their work
+// overlaps on the device (every slot solves on its own streams through a view of the field
+// that shares the field's links but not its workspace). Workspaces are allocated and released
 // stream-ordered, so admitting or retiring one request never stalls another. Each request's
 // arithmetic is independent of what else runs: results are the same alone and in the mix.
+#include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -30,6 +34,8 @@ struct ovl_server {
     std::vector<double> b, x;  // interleaved complex128
     std::vector<ovl_sign_info> info;
     size_t footprint = 0;
+    double work = 0;  // estimated: sites x nrhs x k_max (FP32 at half weight)
+    std::chrono::steady_clock::time_point arrived;
     ovl_status status = OVL_PENDING;
     bool done = false;
   };
@@ -54,21 +60,38 @@ size_t footprint(const ovl_server* s, const ovl_request& r) {
   return ovl::direct_footprint(lat->g.vol, r.nrhs, r.k_max, r.precision == OVL_PREC_F64);
 }
 
+constexpr double kMaxWait = 2.0;  // seconds after which the oldest request goes first
+
+// Queue position of the next request to admit, or -1 (caller holds the lock).
+long pick(ovl_server* s) {
+  if (s->queue.empty()) return -1;
+  const size_t budget = (size_t)s->cfg.mem_budget_bytes;
+  ovl_server::Request* oldest = s->reqs[s->queue.front()].get();
+  const double waited =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - oldest->arrived).count();
+  if (waited > kMaxWait) return s->in_use + oldest->footprint <= budget ? 0 : -1;
+  long best = -1;
+  double best_work = 0;
+  for (size_t i = 0; i < s->queue.size(); ++i) {
+    ovl_server::Request* r = s->reqs[s->queue[i]].get();
+    if (s->in_use + r->footprint > budget) continue;
+    if (best < 0 || r->work < best_work) best = (long)i, best_work = r->work;
+  }
+  return best;
+}
+
 void worker(ovl_server* s, int slot) {
   cudaSetDevice(s->ctx->device);
   for (;;) {
     ovl_server::Request* job = nullptr;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv.wait(lk, [&] {
-        if (s->stop) return true;
-        if (s->queue.empty()) return false;
-        ovl_server::Request* f = s->reqs[s->queue.front()].get();
-        return s->in_use + f->footprint <= (size_t)s->cfg.mem_budget_bytes;
-      });
+      long at = -1;
+      // re-checked at least every 100 ms so that a request passing kMaxWait is seen
+      while (!s->stop && (at = pick(s)) < 0) s->cv.wait_for(lk, std::chrono::milliseconds(100));
       if (s->stop) return;
-      job = s->reqs[s->queue.front()].get();
-      s->queue.pop_front();
+      job = s->reqs[s->queue[at]].get();
+      s->queue.erase(s->queue.begin() + at);
       s->in_use += job->footprint;
     }
     const ovl_request& r = job->req;
@@ -152,6 +175,8 @@ ovl_status ovl_submit(ovl_server* s, const ovl_request* r, uint64_t* ticket) {
   const size_t nd = (size_t)2 * 12 * lat->g.vol * r->nrhs;
   job->b.assign((const double*)r->b, (const double*)r->b + nd);
   job->req.b = nullptr;
+  job->work = (double)lat->g.vol * r->nrhs * r->k_max * (r->precision == OVL_PREC_F64 ? 1.0 : 0.5);
+  job->arrived = std::chrono::steady_clock::now();
   job->ticket = s->next_ticket++;
   *ticket = job->ticket;
   s->queue.push_back(job->ticket);

@@ -122,8 +122,15 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m,
   // correction batch: at most kRefineGroup systems and about kRefineBytes of buffers
   // (per system 9 FP32 vectors + 5 FP64 vectors)
   const size_t per_sys = n * (9 * 8 + 5 * 16);
+  size_t ref_bytes = kRefineBytes;
+  if (refine) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) ref_bytes = std::min(ref_bytes, free_b / 4);
+  }
+  // one batch for all (rhs, shift) systems when they fit: converged systems cost nothing, so the
+  // batch runs as long as its hardest system, once
   const int grp = refine ? (int)std::max<size_t>(1, std::min<size_t>({(size_t)nrhs * s, (size_t)kRefineGroup,
-                                                                       kRefineBytes / per_sys}))
+                                                                       ref_bytes / per_sys}))
                          : 0;
   const size_t gq = (size_t)grp;
   size_t o_xs = take((size_t)nrhs * s * rn * 16), o_r64 = take((size_t)nrhs * rn * 16);
