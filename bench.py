@@ -51,7 +51,7 @@ WORKLOADS = {
                                                          method="multishift", precision="f64", tol=1e-8,
                                                          k_max=5000),
     # the same step in mixed precision: multishift BiCG with FP16 12-real links and FP32 vectors,
-    # FP64 reliable updates down to the metric's 1e-8 (SURVEY's precision item (1))
+    # FP64 reliable updates down to the metric's 1e-8
     "lattice8_mu0-0.1-0.3_defl16_multishift_f16links_f64rel": dict(dims=(8, 8, 8, 8), mus=(0.0, 0.1, 0.3), m=16,
                                                                      method="multishift", precision="f16",
                                                                      tol=1e-8, k_max=5000),
@@ -78,6 +78,13 @@ WORKLOADS = {
     "lattice16_mu0.2_nrhs16_multishift_f16links_f64rel": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0,
                                                                method="multishift", precision="f16", tol=1e-8,
                                                                k_max=8000, rational="zolotarev", s=20, nrhs=16),
+    # the same two mixed-precision solves with FP32 links (FP32 vectors, FP64 reliable updates)
+    "lattice12_mu0.3_multishift_zolo20_f32_f64rel": dict(dims=(12, 12, 12, 12), mus=(0.3,), m=0,
+                                                          method="multishift", precision="f32", tol=1e-8,
+                                                          k_max=8000, rational="zolotarev", s=20),
+    "lattice16_mu0.2_nrhs16_multishift_f32_f64rel": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0,
+                                                          method="multishift", precision="f32", tol=1e-8,
+                                                          k_max=8000, rational="zolotarev", s=20, nrhs=16),
     # 16^4, mu = 0.2, 16 Gaussian sources in one batch sharing the links, FP32 vectors with FP64
     # recurrence scalars and sign(H_k); FP32 vectors bound the attainable accuracy near 1e-5
     "lattice16_mu0.2_nrhs16_direct_f32": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0, method="direct",

@@ -434,6 +434,9 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
     // (A^2 - sigma_i) e = r^(i) (each system its own shift and relative target), x^(i) += e.
     // Systems already converged get a zero right-hand side, which the solve skips.
     const int total = nrhs * s, grp = w->grp;
+    // the correction solves run with FP32 links when the field has them: with FP16 12-real links
+    // the operator itself is off by ~1e-3, which would cap what one correction sweep can gain
+    const int lf_ref = lat->u32 ? LINK_F32 : lf;
     OVL_CHECK_CUDA(launch_ff_to_f64((size_t)total * n, v.xs, st));
     launches += 1;
     MsDev gm = w->gms;
@@ -477,14 +480,15 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
         // chunks of correction iterations, a CUDA graph per (batch size, chunk); two chunks in
         // flight so the host's status check overlaps the next chunk (finished systems skip it)
         const bool rg = p->use_graphs != 0 && chunk > 1;
-        if (rg && !(w->rgraph && w->rg_gn == gn && w->rg_chunk == chunk && w->rg_lf == lf && w->rg_mw == p->m_W &&
+        if (rg && !(w->rgraph && w->rg_gn == gn && w->rg_chunk == chunk && w->rg_lf == lf_ref && w->rg_mw == p->m_W &&
                     w->rg_mu == p->mu)) {
           if (w->rgraph) cudaGraphExecDestroy(w->rgraph);
           w->rgraph = nullptr;
           cudaGraph_t gr;
           OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
           cudaError_t e = cudaSuccess;
-          for (int q = 0; q < chunk && e == cudaSuccess; ++q) e = launch_ms_step(g, U, lf, false, p->m_W, p->mu, gm, gvv, st);
+          for (int q = 0; q < chunk && e == cudaSuccess; ++q)
+            e = launch_ms_step(g, U, lf_ref, false, p->m_W, p->mu, gm, gvv, st);
           cudaError_t e2 = cudaStreamEndCapture(st, &gr);
           OVL_CHECK_CUDA(e);
           OVL_CHECK_CUDA(e2);
@@ -493,7 +497,7 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
           OVL_CHECK_CUDA(e);
           w->rg_gn = gn;
           w->rg_chunk = chunk;
-          w->rg_lf = lf;
+          w->rg_lf = lf_ref;
           w->rg_mw = p->m_W;
           w->rg_mu = p->mu;
         }
@@ -505,7 +509,8 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
           if (rg && ns == chunk) {
             e = cudaGraphLaunch(w->rgraph, st);
           } else {
-            for (int q = 0; q < ns && e == cudaSuccess; ++q) e = launch_ms_step(g, U, lf, false, p->m_W, p->mu, gm, gvv, st);
+            for (int q = 0; q < ns && e == cudaSuccess; ++q)
+              e = launch_ms_step(g, U, lf_ref, false, p->m_W, p->mu, gm, gvv, st);
           }
           if (e) return e;
           it += ns;

@@ -1,0 +1,32 @@
+"""Host logic of bench.py (no GPU): workload table consistency and the roofline's algorithmic
+bytes / flops per pair-stencil launch."""
+import bench
+
+
+def test_workloads_consistent():
+    for name, wl in bench.WORKLOADS.items():
+        assert len(wl["dims"]) == 4 and all(d % 2 == 0 for d in wl["dims"]), name
+        assert wl["method"] in ("direct", "multishift") and wl["precision"] in ("f64", "f32", "f16"), name
+        if wl["precision"] == "f16":
+            assert wl["method"] == "multishift", "FP16 links only under the multishift's FP64 reliable updates"
+        if "mixed" in wl:
+            m = bench.WORKLOADS[wl["mixed"]]
+            # the companion solves the same problem to at least the same accuracy
+            assert m["dims"] == wl["dims"] and m["mus"] == wl["mus"] and m["m"] == wl["m"], name
+            assert m["tol"] <= wl["tol"], name
+    assert bench.DEFAULT_WORKLOAD in bench.WORKLOADS
+
+
+def test_pair_bytes_count_links_once_per_batch():
+    vol = 16 ** 4
+    one = bench.pair_bytes("f32", vol, 1)
+    assert one == vol * bench.PAIR_BYTES_PER_SITE["f32"] == vol * (2 * 96 + 4 * 72 + 2 * 96)
+    # 16 right-hand sides share the links: 16 x spinor traffic, links once
+    assert bench.pair_bytes("f32", vol, 16) == vol * (4 * 72 + 16 * 4 * 96)
+    assert bench.pair_bytes("f16", vol, 1) == vol * (4 * 12 * 2 + 4 * 96)
+    assert bench.pair_bytes("f64", vol, 1) == vol * (4 * 144 + 4 * 192)
+    assert bench.PAIR_FLOPS_PER_SITE == 2 * 1368
+
+
+def test_throughput_counts_every_rank():
+    assert bench.throughput(steps=5, solves_per_step=3, world=2, max_ms=1000.0) == 30.0
