@@ -10,7 +10,7 @@ fused pair stencil) from CUDA events recorded around its launches inside the lib
 host cores on a bounded sample of the same workload.
 
 Beside the headline the line carries `mixed_precision` (the workload's mixed-precision companion,
-e.g. FP16-link multishift with FP64 reliable updates at the same 1e-8, and its speedup over the
+e.g. the FP32 multishift with FP64 reliable updates at the same 1e-8, and its speedup over the
 line's value), `dslash` (kernel-only stencil bandwidth on 32^4) and `serving` (a bounded sample of
 the serving stream: p50/p99 latency, solves/s, success rate); `--no-extras` skips them.
 
@@ -45,13 +45,14 @@ WORKLOADS = {
     # k_max is 2000 and the k actually used is reported.
     "lattice8_mu0-0.1-0.3_defl16_direct_f64": dict(dims=(8, 8, 8, 8), mus=(0.0, 0.1, 0.3), m=16, method="direct",
                                                      precision="f64", tol=1e-8, k_max=2000,
-                                                     mixed="lattice8_mu0-0.1-0.3_defl16_multishift_f16links_f64rel"),
+                                                     mixed="lattice8_mu0-0.1-0.3_defl16_multishift_f32_f64rel"),
     # same lattice and deflation, rational variant (Algorithm 3 + Neuberger, Eq. no_of_poles)
     "lattice8_mu0-0.1-0.3_defl16_multishift_f64": dict(dims=(8, 8, 8, 8), mus=(0.0, 0.1, 0.3), m=16,
                                                          method="multishift", precision="f64", tol=1e-8,
                                                          k_max=5000),
-    # the same step in mixed precision: multishift BiCG with FP16 12-real links and FP32 vectors,
-    # FP64 reliable updates down to the metric's 1e-8
+    # the same step in mixed precision: multishift BiCG with FP16 12-real links (or FP32 links,
+    # the `_f32_f64rel` line, the faster one) and FP32 vectors, FP64 reliable updates down to the
+    # metric's 1e-8
     "lattice8_mu0-0.1-0.3_defl16_multishift_f16links_f64rel": dict(dims=(8, 8, 8, 8), mus=(0.0, 0.1, 0.3), m=16,
                                                                      method="multishift", precision="f16",
                                                                      tol=1e-8, k_max=5000),
@@ -69,12 +70,12 @@ WORKLOADS = {
     # the plain FP64 two-sided Lanczos path on the same 12^4 problem at 1e-8, with the mixed-precision
     # multishift line above as its companion (speedup reported in the line)
     "lattice12_mu0.3_direct_f64": dict(dims=(12, 12, 12, 12), mus=(0.3,), m=0, method="direct", precision="f64",
-                                       tol=1e-8, k_max=3000, mixed="lattice12_mu0.3_multishift_zolo20_f16links_f64rel"),
+                                       tol=1e-8, k_max=3000, mixed="lattice12_mu0.3_multishift_zolo20_f32_f64rel"),
     # 16^4, mu = 0.2 at 1e-8: FP64 direct on batches of 4 sources (16 sources at this k do not fit in
     # HBM: the basis is nrhs x k x 12.6 MB) against the mixed-precision multishift on all 16 at once
     "lattice16_mu0.2_nrhs4_direct_f64": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0, method="direct",
                                              precision="f64", tol=1e-8, k_max=2500, nrhs=4,
-                                             mixed="lattice16_mu0.2_nrhs16_multishift_f16links_f64rel"),
+                                             mixed="lattice16_mu0.2_nrhs16_multishift_f32_f64rel"),
     "lattice16_mu0.2_nrhs16_multishift_f16links_f64rel": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0,
                                                                method="multishift", precision="f16", tol=1e-8,
                                                                k_max=8000, rational="zolotarev", s=20, nrhs=16),
@@ -492,7 +493,7 @@ def run_ours(args, wl):
         "roofline": _roofline(wl, infos, fp64_peak, fp64_src), "e2e": e2e, "clocks": clocks,
         "gpu_launches": int(launches),
     }
-    # the same step in mixed precision (FP32 vectors / FP16 12-real links, FP64 reliable
+    # the same step in mixed precision (FP32 vectors and links, FP64 reliable
     # updates), at the same accuracy, and its speedup over this line's value
     mixed = wl.get("mixed")
     if mixed and not args.no_extras:
