@@ -178,11 +178,8 @@ cudaError_t launch_ms_start(const Geom& g, bool f64, const MsDev& ms, const MsVe
 // pair stencil, ev[1] after it, ev[2] before the direction update, ev[3] after it.
 cudaError_t launch_ms_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, const MsDev& ms,
                            const MsVecs& v, cudaStream_t st, cudaEvent_t* ev = nullptr);
-// Refinement helpers (one rhs `rhs`, one shift): res = r64 - (t2 - sigma x) with t2 = A^2 x
-// (native FP64), |res|^2 in out[0] (part/count scratch); x += e; X = sum_i omega_i xs_i.
-cudaError_t launch_ms_residual(const Geom& g, const double2* r64, const double2* t2, const double2* x, double sigma,
-                               double2* res, double* part, unsigned* count, double* out, cudaStream_t st);
-// Batched form for the systems j0 .. j0+gn-1 of the flattened (rhs, shift) index j = rhs*s + i:
+// Reliable-update helpers. Residuals of the systems j0 .. j0+gn-1 of the flattened (rhs, shift)
+// index j = rhs*s + i:
 // res_j = r64[rhs] - (t2_j - sigma[i] x_j), |res_j|^2 -> out[j - j0]. t2, x, res hold gn vectors.
 cudaError_t launch_ms_residual_batch(const Geom& g, int j0, int gn, int s, const double2* r64, const double2* t2,
                                      const double2* x, const double* sigma, double2* res, double* part,
@@ -190,9 +187,9 @@ cudaError_t launch_ms_residual_batch(const Geom& g, int j0, int gn, int s, const
 // x_j += e_j for the gn vectors whose status[j] is not a breakdown (1).
 cudaError_t launch_axpy_f64_masked(const Geom& g, int gn, const int* status, const double2* e, double2* x,
                                    cudaStream_t st);
-cudaError_t launch_axpy_f64(const Geom& g, int nrhs, const double2* e, double2* x, cudaStream_t st);
 // n complex values held as float-float (re hi, re lo, im hi, im lo) -> complex double, in place.
 cudaError_t launch_ff_to_f64(size_t n, double2* x, cudaStream_t st);
+// X = sum_i omega_i xs_i per rhs.
 cudaError_t launch_ms_combine_shifts(const Geom& g, int nrhs, int s, const double* omega, const double2* xs,
                                      double2* X, cudaStream_t st);
 // x (canonical complex128) = x_P + AX (AX native FP64, = H_W(mu) X)

@@ -456,31 +456,6 @@ cudaError_t launch_ms_step(const Geom& g, const Links& U, int lf, bool f64, doub
   return ms_step_t<float, LINK_F32>(g, U, m_w, mu, ms, v, st, ev);
 }
 
-// res = r64 - (t2 - sigma x), |res|^2 -> out[0] (last block)
-__global__ void __launch_bounds__(kVecBlock) k_ms_residual(int vol, const double2* r64, const double2* t2,
-                                                           const double2* x, double sigma, double2* res,
-                                                           double* part, unsigned* count, double* out) {
-  const size_t n = (size_t)12 * vol;
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[1] = {0};
-  if (e < n) {
-    zd a = ldc<double>(r64, e) - (ldc<double>(t2, e) - sigma * ldc<double>(x, e));
-    stc<double>(res, e, a);
-    acc[0] = norm2(a);
-  }
-  block_sum<1>(acc);
-  if (publish_partials<1>(acc, part, count)) {
-    reduce_partials<1>(part, gridDim.x, acc);
-    if (lin_tid() == 0) out[0] = acc[0];
-  }
-}
-
-cudaError_t launch_ms_residual(const Geom& g, const double2* r64, const double2* t2, const double2* x, double sigma,
-                               double2* res, double* part, unsigned* count, double* out, cudaStream_t st) {
-  k_ms_residual<<<vec_blocks(g), kVecBlock, 0, st>>>(g.vol, r64, t2, x, sigma, res, part, count, out);
-  return cudaGetLastError();
-}
-
 __global__ void __launch_bounds__(kVecBlock) k_ms_residual_batch(int vol, int j0, int s, const double2* r64,
                                                                  const double2* t2, const double2* x,
                                                                  const double* sigma, double2* res, double* part,
@@ -535,17 +510,6 @@ __global__ void k_ff_to_f64(size_t n, double2* x) {
 
 cudaError_t launch_ff_to_f64(size_t n, double2* x, cudaStream_t st) {
   k_ff_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x);
-  return cudaGetLastError();
-}
-
-__global__ void k_axpy_f64(size_t n, const double2* e, double2* x) {
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) stc<double>(x, i, ldc<double>(x, i) + ldc<double>(e, i));
-}
-
-cudaError_t launch_axpy_f64(const Geom& g, int nrhs, const double2* e, double2* x, cudaStream_t st) {
-  size_t n = (size_t)12 * g.vol * nrhs;
-  k_axpy_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, e, x);
   return cudaGetLastError();
 }
 
