@@ -16,12 +16,15 @@ import ctypes
 import numpy as np
 
 
-def _inverse_operator(ovl, lat, m_W, mu, tol, k_max):
+def _inverse_operator(ovl, lat, m_W, mu, tol, k_max, precision=None):
+    """A^-1 as a host matvec. precision: OVL_PREC_F64 (default) or OVL_PREC_F32 (FP32 links and
+    vectors with FP64 reliable updates to the same tol; the lattice needs FP32 links)."""
     n = ovl.ovl_lattice_n(lat)
     om = np.array([1.0])
     sg = np.array([0.0])
+    prec = ovl.OVL_PREC_F64 if precision is None else precision
     p = ovl.ovl_sign_params_default(method=ovl.OVL_MULTISHIFT_BICG, m_W=m_W, mu=mu, tol=tol, k_max=k_max,
-                                    rational_kind=ovl.OVL_RAT_CUSTOM, s=1, check_every=50)
+                                    rational_kind=ovl.OVL_RAT_CUSTOM, s=1, check_every=50, precision=prec)
     p.omega = om.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     p.sigma = sg.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     calls = [0]
@@ -38,16 +41,18 @@ def _inverse_operator(ovl, lat, m_W, mu, tol, k_max):
     return matvec, calls, (om, sg)
 
 
-def critical_eigenpairs(ovl, lat, m_W, mu, m, tol=1e-10, solve_tol=1e-12, k_max=20000, extra=2, ncv=None):
+def critical_eigenpairs(ovl, lat, m_W, mu, m, tol=1e-10, solve_tol=1e-12, k_max=20000, extra=2, ncv=None,
+                        precision=None):
     """(lam[m], R[m][n], L[m][n], gap, info): the m eigenvalues of H_W(mu) smallest in modulus,
-    canonical-layout right/left eigenvectors with L^H R = I, and gap = |lambda_{m+1}|."""
+    canonical-layout right/left eigenvectors with L^H R = I, and gap = |lambda_{m+1}|.
+    precision selects the inverse solves (see _inverse_operator); both reach solve_tol."""
     import scipy.sparse.linalg as spla
 
     n = ovl.ovl_lattice_n(lat)
     nev = m + extra
     ncv = ncv or max(2 * nev + 8, 40)
-    mv_r, calls_r, keep_r = _inverse_operator(ovl, lat, m_W, mu, solve_tol, k_max)
-    mv_l, calls_l, keep_l = _inverse_operator(ovl, lat, m_W, -mu, solve_tol, k_max)
+    mv_r, calls_r, keep_r = _inverse_operator(ovl, lat, m_W, mu, solve_tol, k_max, precision)
+    mv_l, calls_l, keep_l = _inverse_operator(ovl, lat, m_W, -mu, solve_tol, k_max, precision)
     op_r = spla.LinearOperator((n, n), matvec=mv_r, dtype=np.complex128)
     op_l = spla.LinearOperator((n, n), matvec=mv_l, dtype=np.complex128)
     v0 = np.ones(n, dtype=np.complex128)
@@ -71,13 +76,13 @@ def critical_eigenpairs(ovl, lat, m_W, mu, m, tol=1e-10, solve_tol=1e-12, k_max=
     return lam, R, L, gap, info
 
 
-def smallest_modulus(ovl, lat, m_W, mu, tol=1e-4):
+def smallest_modulus(ovl, lat, m_W, mu, tol=1e-4, precision=None):
     """|lambda|_min of H_W(mu): the largest-modulus eigenvalue of A^-1 by ARPACK, every A^-1
     application a GPU multishift solve with the single pole (omega, sigma) = (1, 0)."""
     import scipy.sparse.linalg as spla
 
     n = ovl.ovl_lattice_n(lat)
-    mv, _, keep = _inverse_operator(ovl, lat, m_W, mu, 1e-8, 20000)
+    mv, _, keep = _inverse_operator(ovl, lat, m_W, mu, 1e-8, 20000, precision)
     op = spla.LinearOperator((n, n), matvec=mv, dtype=np.complex128)
     th = spla.eigs(op, k=1, which="LM", tol=tol, return_eigenvectors=False, v0=np.ones(n, np.complex128))
     del keep
