@@ -146,7 +146,9 @@ typedef struct {
   int32_t host_io;        /* 1: b and x are host pointers (copies inside the call) */
   int32_t use_graphs;     /* direct: capture the iteration chunks in CUDA graphs (default 1) */
   int32_t fixed_k;        /* direct: > 0 runs exactly this many steps (no convergence test) */
-  int32_t reserved;
+  int32_t priority;       /* CUDA stream priority of the solve, 0 default, p > 0 p levels more
+                             urgent (clamped to the device's range); lets concurrent solves favour
+                             the longest one. No effect on results. */
 } ovl_sign_params;
 
 typedef struct {

@@ -25,7 +25,7 @@ ovl_status small_sign(int k, const std::complex<double>* al, const std::complex<
 void set_sign_concurrency(int n);
 
 struct DirectWS {
-  int nrhs = 0, kmax = 0, f64 = -1, m = 0, vol = 0;
+  int nrhs = 0, kmax = 0, f64 = -1, m = 0, vol = 0, prio = 0;
   LzDev lz;
   LzVecs vec;
   void* dev_block = nullptr;  // one allocation for everything
@@ -92,10 +92,11 @@ void free_direct_ws(DirectWS* w) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int m) {
+static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int m, int prio) {
   DirectWS* w = lat->dws;
   const int vol = lat->g.vol;
-  if (w && w->nrhs == nrhs && w->kmax == kmax && w->f64 == (int)f64 && w->m >= m && w->vol == vol) return OVL_OK;
+  if (w && w->nrhs == nrhs && w->kmax == kmax && w->f64 == (int)f64 && w->m >= m && w->vol == vol && w->prio == prio)
+    return OVL_OK;
   free_direct_ws(w);
   lat->dws = nullptr;
   w = new DirectWS();
@@ -104,6 +105,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   w->f64 = f64;
   w->m = m;
   w->vol = vol;
+  w->prio = prio;
   const size_t n = (size_t)12 * vol;
   const size_t elt = f64 ? 16 : 8;
   const int nblk = partial_slots(lat->g);  // the most blocks of any reduction kernel
@@ -140,8 +142,13 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   size_t o_n1 = take((size_t)nrhs * kmax * 16), o_n2 = take((size_t)nrhs * kmax * 16);
   size_t o_nk = take((size_t)nrhs * 4), o_np = take((size_t)nrhs * 2 * vec_blocks(lat->g) * 8);
   size_t o_nc = take((size_t)nrhs * 4), o_no = take((size_t)nrhs * 2 * 8);
-  if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&w->nstream, cudaStreamNonBlocking) != cudaSuccess) {
+  // stream priority: 0 the default; p > 0 asks for p levels more urgent (numerically lower,
+  // clamped to the device's range), so that concurrent solves can favour the longest one
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  const int sp = std::max(greatest, least - std::max(0, prio));
+  if (cudaStreamCreateWithPriority(&w->stream, cudaStreamNonBlocking, sp) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&w->nstream, cudaStreamNonBlocking, sp) != cudaSuccess) {
     delete w;
     set_error("apply_sign: cannot create a stream");
     return OVL_ECUDA;
@@ -352,7 +359,7 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
     m = lat->defl.m;
   }
   const int kmax = p->fixed_k > 0 ? p->fixed_k : p->k_max;
-  OVL_TRY(ensure_ws(lat, nrhs, kmax, f64, m));
+  OVL_TRY(ensure_ws(lat, nrhs, kmax, f64, m, p->priority));
   DirectWS* w = lat->dws;
   cudaStream_t st = w->stream;
   const Geom& g = lat->g;

@@ -19,7 +19,7 @@ double neuberger_bound(int s, double d);
 double zolotarev(int n, double lo, double hi, double* omega, double* sigma);
 
 struct MultiWS {
-  int nrhs = 0, s = 0, f64 = -1, vol = 0, m = 0;
+  int nrhs = 0, s = 0, f64 = -1, vol = 0, m = 0, prio = 0;
   bool refine = false;
   // refinement (reliable updates): the correction systems (A^2 - sigma_i) e = r^(i) of up to
   // `grp` (rhs, shift) pairs are solved as one batch; per system: FP64 residual, two stencil
@@ -75,10 +75,11 @@ void free_multi_ws(MultiWS* w) {
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m, bool refine) {
+static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m, bool refine, int prio) {
   MultiWS* w = lat->mws;
   const int vol = lat->g.vol;
-  if (w && w->nrhs == nrhs && w->s == s && w->f64 == (int)f64 && w->vol == vol && w->m >= m && w->refine == refine)
+  if (w && w->nrhs == nrhs && w->s == s && w->f64 == (int)f64 && w->vol == vol && w->m >= m && w->refine == refine &&
+      w->prio == prio)
     return OVL_OK;
   free_multi_ws(w);
   lat->mws = nullptr;
@@ -89,6 +90,7 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m,
   w->vol = vol;
   w->m = m;
   w->refine = refine;
+  w->prio = prio;
   const size_t n = (size_t)12 * vol, elt = f64 ? 16 : 8;
   const int nblk = partial_slots(lat->g);
   size_t off = 0;
@@ -143,7 +145,10 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m,
          o_gz = take(gq * 3 * 16), o_ga = take(gq * 16), o_gb = take(gq * 16), o_gact = take(gq * 4),
          o_gpa = take(gq * nblk * 4 * 8), o_gcn = take(gq * 4), o_sga = take((size_t)s * 8), o_gsig = take(gq * 8),
          o_gtol = take(gq * 8);
-  if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  int least = 0, greatest = 0;  // stream priority as in the direct driver
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (cudaStreamCreateWithPriority(&w->stream, cudaStreamNonBlocking, std::max(greatest, least - std::max(0, prio))) !=
+      cudaSuccess) {
     delete w;
     set_error("apply_sign: cannot create a stream");
     return OVL_ECUDA;
@@ -300,7 +305,7 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
   // residuals (reliable updates): x^(i) kept in FP64, r^(i) = r - (A^2 - sigma_i) x^(i) from the
   // FP64 stencil, corrections from FP32 single-shift BiCG solves on the same kernels
   const bool refine = !f64 && p->tol < kFp32Floor;
-  OVL_TRY(ensure_mws(lat, nrhs, s, f64, m, refine));
+  OVL_TRY(ensure_mws(lat, nrhs, s, f64, m, refine, p->priority));
   MultiWS* w = lat->mws;
   cudaStream_t st = w->stream;
   const Geom& g = lat->g;
