@@ -20,6 +20,7 @@
 #include <mutex>
 #include <thread>
 
+#include "admission.h"
 #include "common.h"
 
 namespace ovl {
@@ -62,22 +63,19 @@ size_t footprint(const ovl_server* s, const ovl_request& r) {
 
 constexpr double kMaxWait = 2.0;  // seconds after which the oldest request goes first
 
-// Queue position of the next request to admit, or -1 (caller holds the lock).
+// Queue position of the next request to admit, or -1 (caller holds the lock); the policy is
+// admission_pick (admission.h).
 long pick(ovl_server* s) {
   if (s->queue.empty()) return -1;
-  const size_t budget = (size_t)s->cfg.mem_budget_bytes;
-  ovl_server::Request* oldest = s->reqs[s->queue.front()].get();
+  std::vector<ovl::PendingRequest> q(s->queue.size());
+  for (size_t i = 0; i < q.size(); ++i) {
+    const ovl_server::Request* r = s->reqs[s->queue[i]].get();
+    q[i] = {r->footprint, r->work};
+  }
+  const ovl_server::Request* oldest = s->reqs[s->queue.front()].get();
   const double waited =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - oldest->arrived).count();
-  if (waited > kMaxWait) return s->in_use + oldest->footprint <= budget ? 0 : -1;
-  long best = -1;
-  double best_work = 0;
-  for (size_t i = 0; i < s->queue.size(); ++i) {
-    ovl_server::Request* r = s->reqs[s->queue[i]].get();
-    if (s->in_use + r->footprint > budget) continue;
-    if (best < 0 || r->work < best_work) best = (long)i, best_work = r->work;
-  }
-  return best;
+  return ovl::admission_pick(q.data(), q.size(), s->in_use, (size_t)s->cfg.mem_budget_bytes, waited, kMaxWait);
 }
 
 void worker(ovl_server* s, int slot) {
