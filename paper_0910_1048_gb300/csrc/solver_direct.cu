@@ -2,10 +2,11 @@
 //   x_P = R f(Lambda) L^H b;  r = b - R L^H b;  r~ = b - L R^H b;  v_1 = r/beta, w_1 ~ r~;
 //   k steps of two-sided Lanczos (Eqs. 2sided1/2);  x = x_P + beta V_k f(H_k) e_1.
 // The paper fixes k a priori; this driver also stops early: the scalars of every chunk of
-// `check_every` steps are copied to the host, and (once j has grown 10% past the previous
-// evaluation j') y_j = sign(H_j) e_1 is evaluated; it stops when
-//   ||V_j (y_j - [y_j'; 0])|| <= tol ||V_j y_j||,
-// both norms computed on the GPU on a side stream.
+// `check_every` steps are copied to the host, and at each right-hand side's own evaluation
+// points (stoprule.h) y_j = sign(H_j) e_1 is evaluated and the relative change
+//   ||V_j (y_j - [y_j'; 0])|| / ||V_j y_j||
+// since the previous evaluation j' (both norms on the GPU, side stream) feeds the rate-corrected
+// error estimate that decides the stop and the next evaluation point.
 // All per-step scalars stay on the device (no host round trip inside a chunk), so a chunk
 // of steps is one CUDA graph, replayed; the next chunk is queued before the host checks
 // the previous one, overlapping sign(H_j) e_1 with device work.
