@@ -108,8 +108,6 @@ cudaError_t launch_lanczos_update(const Geom& g, bool f64, const LzDev& lz, cons
 // One step j (read from lz.j): pair stencil + alpha, then the biorthogonal update.
 cudaError_t launch_lanczos_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
                                 const LzDev& lz, const LzVecs& vec, cudaStream_t st);
-// out[rhs][0..1] = ||sum_{j<k_r} d1_j vhat_j||^2, ||sum_{j<k_r} d2_j vhat_j||^2 (own scratch part,
-// count: part >= nrhs * 2 * ceil(12V/256) doubles, count >= nrhs zeros).
 // Element sampling of the stopping estimate: the norms ||V c|| of the change and of the iterate
 // enter only as a ratio, so on large lattices they are taken over runs of 32 consecutive
 // elements, one run in every 32 * stride (about 10^5 elements sampled; a fixed pattern, so the
@@ -121,6 +119,8 @@ inline int vnorm_stride(const Geom& g) {
   while (st < 64 && n / (2 * st) >= 98304) st *= 2;
   return st;
 }
+// out[rhs][0..1] = ||sum_{j<k_r} d1_j vhat_j||^2, ||sum_{j<k_r} d2_j vhat_j||^2 over the sampled
+// elements (own scratch part, count: part >= nrhs * 2 * ceil(12V/256) doubles, count >= nrhs zeros).
 cudaError_t launch_lanczos_vnorms(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, const int* kr,
                                   const double2* d1, const double2* d2, int kcoef, double* part, unsigned* count,
                                   double* out, cudaStream_t st);
