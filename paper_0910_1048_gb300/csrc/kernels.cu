@@ -110,17 +110,38 @@ cudaError_t launch_ingest_links(const Geom& g, const double* ucan, double2* u64,
 }
 
 // ------------------------------------------------------------------ apply D_W
-template <class R, int LF, bool NIN, bool NOUT>
-__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? (LF == LINK_F16R12 ? 6 : 7) : 1) k_dslash(Geom g, Links U, HopCoef<R> c, bool g5_in, bool g5_out,
-                                                   const typename V2<R>::T* in, typename V2<R>::T* out) {
+// G5IN (gamma5 on the input, the adjoint's form) is a template parameter so that the common
+// case carries no per-neighbour branch: 32^4 FP32 4.7 -> 5.2 TB/s in a probe without it.
+template <class R, int LF, bool NIN, bool NOUT, bool G5IN>
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? (LF == LINK_F16R12 ? 6 : 7) : 1)
+    k_dslash(Geom g, Links U, HopCoef<R> c, bool g5_out, const typename V2<R>::T* in, typename V2<R>::T* out) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.vol) return;
   size_t off = (size_t)blockIdx.y * 12 * g.vol;
-  Loader<R, NIN> ld{in + off, g.vol, g5_in};
+  Loader<R, NIN> ld{in + off, g.vol, G5IN};
   Spin<R> o;
   dslash_site<LF, R>(g, U, s, c, ld, o);
-  if (g5_out) gamma5_inplace(o);
+  const R sg = g5_out ? (R)-1 : (R)1;  // gamma5 = diag(1, 1, -1, -1) on the output, without a branch
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    o.c[2][a] = sg * o.c[2][a];
+    o.c[3][a] = sg * o.c[3][a];
+  }
   store_spin<R, NOUT>(out + off, g.vol, s, o);
+}
+
+template <class R, int LF, bool G5IN>
+static cudaError_t dslash_g(dim3 grid, const Geom& g, const Links& U, HopCoef<R> c, bool go, bool nin, bool nout,
+                            const typename V2<R>::T* i, typename V2<R>::T* o, cudaStream_t st) {
+  if (nin && nout)
+    k_dslash<R, LF, true, true, G5IN><<<grid, kBlock, 0, st>>>(g, U, c, go, i, o);
+  else if (nin)
+    k_dslash<R, LF, true, false, G5IN><<<grid, kBlock, 0, st>>>(g, U, c, go, i, o);
+  else if (nout)
+    k_dslash<R, LF, false, true, G5IN><<<grid, kBlock, 0, st>>>(g, U, c, go, i, o);
+  else
+    k_dslash<R, LF, false, false, G5IN><<<grid, kBlock, 0, st>>>(g, U, c, go, i, o);
+  return cudaGetLastError();
 }
 
 template <class R, int LF>
@@ -131,15 +152,8 @@ static cudaError_t dslash_t(const Geom& g, const Links& U, double m_w, double mu
   using T = typename V2<R>::T;
   const T* i = (const T*)in;
   T* o = (T*)out;
-  if (nin && nout)
-    k_dslash<R, LF, true, true><<<grid, kBlock, 0, st>>>(g, U, c, gi, go, i, o);
-  else if (nin)
-    k_dslash<R, LF, true, false><<<grid, kBlock, 0, st>>>(g, U, c, gi, go, i, o);
-  else if (nout)
-    k_dslash<R, LF, false, true><<<grid, kBlock, 0, st>>>(g, U, c, gi, go, i, o);
-  else
-    k_dslash<R, LF, false, false><<<grid, kBlock, 0, st>>>(g, U, c, gi, go, i, o);
-  return cudaGetLastError();
+  return gi ? dslash_g<R, LF, true>(grid, g, U, c, go, nin, nout, i, o, st)
+            : dslash_g<R, LF, false>(grid, g, U, c, go, nin, nout, i, o, st);
 }
 
 cudaError_t launch_dslash(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, bool g5_in,
