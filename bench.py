@@ -94,7 +94,7 @@ WORKLOADS = {
     "lattice4_mu0.3_direct_f64": dict(dims=(4, 4, 4, 4), mus=(0.3,), m=0, method="direct", precision="f64",
                                       tol=1e-8, k_max=1200),
 }
-DEFAULT_WORKLOAD = "lattice8_mu0-0.1-0.3_defl16_direct_f64"
+DEFAULT_WORKLOAD = "lattice12_mu0.3_direct_f64"
 
 # Algorithmic traffic / work of one launch of the fused pair stencil per site: per right-hand
 # side two spinors in (neighbours read once each: 2 x 24 reals) and two out; the 4 links of a site
@@ -110,7 +110,7 @@ def pair_bytes(prec, vol, nrhs):
     """Algorithmic bytes of one pair-stencil launch over `nrhs` right-hand sides."""
     return vol * (PAIR_LINK_BYTES_PER_SITE[prec] + nrhs * PAIR_SPINOR_BYTES_PER_SITE[prec])
 
-# FP64 FMA throughput of this pool's GB300 in TFLOP/s (the FMA-chain probe in csrc/probe/; the
+# FP64 FMA throughput of a GB300 in TFLOP/s (the FMA-chain probe fp64_peak.cu; the
 # bench runs the probe itself and uses this value only when the probe library is missing)
 FP64_PEAK_TFLOPS = 1.256
 
@@ -281,17 +281,17 @@ def _params(ovl, wl, d):
 
 def _fp64_peak():
     """FP64 FMA throughput of this GPU (TFLOP/s), measured by the FMA-chain probe library built
-    beside libovl.so; falls back to the value that probe gave on this machine's GB300."""
+    beside bench.py (libfp64_peak.so); falls back to the value that probe gave on a GB300."""
     import ctypes
 
     try:
-        lib = ctypes.CDLL(os.path.join(ROOT, "paper_0910_1048_gb300", "libovl_probe.so"))
+        lib = ctypes.CDLL(os.path.join(ROOT, "libfp64_peak.so"))
         out = ctypes.c_double(0.0)
         if lib.ovl_probe_fma_tflops(1, ctypes.byref(out)) == 0 and out.value > 0:
-            return out.value, "FP64 FMA-chain probe (csrc/probe/fma_peak.cu) run by bench.py on this GPU"
+            return out.value, "FP64 FMA-chain probe (fp64_peak.cu) run by bench.py on this GPU"
     except OSError:
         pass
-    return FP64_PEAK_TFLOPS, "FP64 FMA-chain probe, earlier measurement on this pool's GB300"
+    return FP64_PEAK_TFLOPS, "FP64 FMA-chain probe, earlier measurement on a GB300"
 
 
 def _sources(wl):

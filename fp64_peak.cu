@@ -1,4 +1,4 @@
-// FMA-throughput probe (measurement utility, not part of the sign-function library): the
+// FMA-throughput probe of bench.py (measurement utility, not part of the library): the
 // denominator of the roofline of the FP64 kernels, whose bound on this GPU is the FP64 pipe.
 //
 // Every thread runs 8 independent FMA chains x <- x*a + b for a fixed number of iterations

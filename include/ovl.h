@@ -26,6 +26,8 @@
  * On failure ovl_last_error() returns a message for the calling thread.
  * Threading: one ovl_lattice must not be used by two threads at once; distinct lattices
  * may. Stream-ordered calls take a cudaStream_t as void* (NULL = legacy default stream).
+ * Devices: a call makes the lattice's (or context's) device current while it runs and gives
+ * the caller back its own current device before it returns.
  */
 #ifndef OVL_H
 #define OVL_H
@@ -191,12 +193,14 @@ ovl_status ovl_apply_sign(ovl_lattice* lat, const ovl_sign_params* p, int32_t nr
  * property of the library, not of the method. Same kernels and results as ovl_apply_sign
  * (method OVL_DIRECT_2SL); b and x are device buffers; runs on `stream` and synchronizes it.
  * All scratch lives in one static 64 MiB device array per GPU that loads the library, held
- * until the process exits; its address is looked up on the first call for each device, so
- * make that first call before any stream capture. Calls share the array: calls that overlap
- * on the GPU race. No CUDA graphs, streams, events or pinned buffers are created.
- * Errors: EINVAL (host_io set, method not direct, or scratch needed > 64 MiB, e.g. a basis of
- * nrhs * (k_max+1) * 12 V complex values that does not fit), ECUDA; solve statuses as
- * ovl_apply_sign. */
+ * until the process exits; its address is looked up on the first call for each device (make
+ * that first call before any stream capture) and again on each later call made outside a
+ * capture. Calls share the array: calls that overlap on the GPU race. No CUDA graphs, streams,
+ * events or pinned buffers are created. `stream` must belong to the lattice's device; the
+ * caller's current device is left as it was.
+ * Errors: EINVAL (host_io set, method not direct, stream of another device, or scratch needed
+ * > 64 MiB, e.g. a basis of nrhs * (k_max+1) * 12 V complex values that does not fit), ECUDA;
+ * solve statuses as ovl_apply_sign. */
 ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_params* p, int32_t nrhs,
                                   const void* b, void* x, ovl_sign_info* info, void* stream);
 

@@ -172,25 +172,34 @@ def ovl_version() -> str:
     return lib.ovl_version().decode()
 
 
+_CTX_DEVICE: dict = {}  # context handle -> CUDA device ordinal
+_LAT_DEVICE: dict = {}  # lattice handle -> CUDA device ordinal
+
+
 def ovl_ctx_create(device: int = 0):
     h = _P()
     _check(lib.ovl_ctx_create(device, ctypes.byref(h)))
+    _CTX_DEVICE[h.value] = int(device)
     return h
 
 
 def ovl_ctx_destroy(ctx):
     _check(lib.ovl_ctx_destroy(ctx))
+    _CTX_DEVICE.pop(ctx.value, None)
 
 
 def ovl_create_lattice(ctx, dims, t_bc: int = -1):
     arr = (_I * 4)(*[int(d) for d in dims])
     h = _P()
     _check(lib.ovl_create_lattice(ctx, arr, int(t_bc), ctypes.byref(h)))
+    if ctx.value in _CTX_DEVICE:
+        _LAT_DEVICE[h.value] = _CTX_DEVICE[ctx.value]
     return h
 
 
 def ovl_destroy_lattice(lat):
     _check(lib.ovl_destroy_lattice(lat))
+    _LAT_DEVICE.pop(lat.value, None)
 
 
 def ovl_lattice_n(lat) -> int:
@@ -247,19 +256,41 @@ def ovl_sign_params_default(**kw) -> ovl_sign_params:
     return p
 
 
+def _sign_buffers(lat, b, x, where):
+    """Validate the b / x pair of a sign solve before any pointer reaches the library (a short or
+    mistyped x would otherwise be written out of bounds by the kernels). Returns (nrhs, host)."""
+    n = ovl_lattice_n(lat)
+    host = isinstance(b, np.ndarray)
+    if host != isinstance(x, np.ndarray):
+        raise TypeError("%s: b and x must both be host (numpy) or both device (torch) buffers" % where)
+    if host:
+        for nm, a in (("b", b), ("x", x)):
+            if a.dtype != np.complex128 or not a.flags["C_CONTIGUOUS"]:
+                raise TypeError("%s: %s must be a C-contiguous complex128 array" % (where, nm))
+        size_b, size_x = b.size, x.size
+    else:
+        for nm, a in (("b", b), ("x", x)):
+            if not _on_device(a):
+                raise TypeError("%s: %s must be a CUDA tensor (or both numpy arrays)" % (where, nm))
+            if str(a.dtype) != "torch.complex128" or not a.is_contiguous():
+                raise TypeError("%s: %s must be a contiguous complex128 tensor" % (where, nm))
+            dev = _LAT_DEVICE.get(lat.value)
+            if dev is not None and a.device.index != dev:
+                raise ValueError("%s: %s is on cuda:%s, the lattice on cuda:%d" % (where, nm, a.device.index, dev))
+        size_b, size_x = b.numel(), x.numel()
+    if size_b == 0 or size_b % n != 0:
+        raise ValueError("%s: b holds %d elements, not a whole number of spinors of n = %d" % (where, size_b, n))
+    if size_x != size_b:
+        raise ValueError("%s: x holds %d elements, b %d" % (where, size_x, size_b))
+    return size_b // n, host
+
+
 def ovl_apply_sign(lat, params: ovl_sign_params, b, x, stream=None, raise_on_error=False):
     """x = sign(H_W(mu)) b. b, x: complex128 [nrhs][...] as torch CUDA tensors, or numpy arrays
     (then params.host_io is set). Returns (status, [info dict per rhs]); raises OvlError for
     argument/CUDA/memory errors (and for every error if raise_on_error)."""
-    n = ovl_lattice_n(lat)
-    nrhs = (b.numel() if hasattr(b, "numel") else b.size) // n
-    host = isinstance(b, np.ndarray)
-    if host != isinstance(x, np.ndarray):
-        raise TypeError("b and x must both be host (numpy) or both device (torch) buffers")
-    if host:
-        params.host_io = 1
-        if b.dtype != np.complex128 or x.dtype != np.complex128:
-            raise TypeError("complex128 buffers required")
+    nrhs, host = _sign_buffers(lat, b, x, "ovl_apply_sign")
+    params.host_io = 1 if host else 0
     infos = (ovl_sign_info * nrhs)()
     st = lib.ovl_apply_sign(lat, ctypes.byref(params), nrhs, _ptr(b), _ptr(x), infos, _stream(stream, b, x))
     if st in (OVL_EINVAL, OVL_ENOMEM, OVL_ECUDA) or (raise_on_error and st < 0):
@@ -271,8 +302,9 @@ def ovl_apply_sign_noalloc(lat, params: ovl_sign_params, b, x, stream=None):
     """ovl_apply_sign's direct method without any device allocation (scratch in a static
     64 MiB device array): for callers that cannot allocate device memory. b, x are torch CUDA
     tensors. Returns (status, [info dict per rhs]); raises OvlError for argument/CUDA errors."""
-    n = ovl_lattice_n(lat)
-    nrhs = b.numel() // n
+    nrhs, host = _sign_buffers(lat, b, x, "ovl_apply_sign_noalloc")
+    if host:
+        raise TypeError("ovl_apply_sign_noalloc: b and x must be CUDA tensors")
     infos = (ovl_sign_info * nrhs)()
     st = lib.ovl_apply_sign_noalloc(lat, ctypes.byref(params), nrhs, _ptr(b), _ptr(x), infos, _stream(stream, b, x))
     if st in (OVL_EINVAL, OVL_ENOMEM, OVL_ECUDA):

@@ -1,8 +1,9 @@
 """Build libovl.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
 Every translation unit under csrc/ is compiled in parallel into _build/ and linked into
-paper_0910_1048_gb300/libovl.so with the CUDA runtime linked statically. The FMA-throughput
-probe (csrc/probe/, the measured FP64 peak of the bench's roofline) becomes libovl_probe.so.
+paper_0910_1048_gb300/libovl.so with the CUDA runtime linked statically. The bench's
+FMA-throughput probe (fp64_peak.cu beside bench.py, the measured FP64 peak of its roofline)
+becomes libfp64_peak.so beside it; it is not part of the library.
 """
 from __future__ import annotations
 
@@ -17,8 +18,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libovl.so")
-PROBE_SRC = os.path.join(CSRC, "probe", "fma_peak.cu")
-PROBE_OUT = os.path.join(PKG, "libovl_probe.so")
+PROBE_SRC = os.path.join(ROOT, "fp64_peak.cu")
+PROBE_OUT = os.path.join(ROOT, "libfp64_peak.so")
 BUILD = os.path.join(ROOT, "_build", "ovl-" + platform.machine())  # objects never cross architectures
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
@@ -59,7 +60,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
             if s.endswith(".cpp"):
                 cmd = [nvcc] + FLAGS + (extra or []) + ["-x", "c++", "-c", s, "-o", o]
             jobs.append(cmd)
-    probe_obj = os.path.join(BUILD, "fma_peak.cu.o")
+    probe_obj = os.path.join(BUILD, "fp64_peak.cu.o")
     if not os.path.exists(probe_obj) or os.path.getmtime(probe_obj) < os.path.getmtime(PROBE_SRC):
         jobs.append([nvcc] + ARCH + FLAGS + (extra or []) + ["-c", PROBE_SRC, "-o", probe_obj])
 

@@ -22,11 +22,6 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
 ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, const double2* b, double2* x,
                             ovl_sign_info* info, cudaStream_t st);
 
-static ovl_status set_device(const ovl_lattice* lat) {
-  OVL_CHECK_CUDA(cudaSetDevice(lat->ctx->device));
-  return OVL_OK;
-}
-
 // A lattice sharing `parent`'s links (not its deflation set) with its own workspaces.
 ovl_lattice* lattice_view(ovl_lattice* parent) {
   ovl_lattice* v = new ovl_lattice();
@@ -58,7 +53,7 @@ ovl_status ovl_ctx_create(int32_t device, ovl_ctx** out) {
   int ndev = 0;
   OVL_CHECK_CUDA(cudaGetDeviceCount(&ndev));
   OVL_REQUIRE(device >= 0 && device < ndev, "ovl_ctx_create: device %d not in [0, %d)", device, ndev);
-  OVL_CHECK_CUDA(cudaSetDevice(device));
+  OVL_DEVICE_SCOPE(device);
   ovl_ctx* c = new ovl_ctx();
   c->device = device;
   cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
@@ -75,7 +70,7 @@ ovl_status ovl_ctx_create(int32_t device, ovl_ctx** out) {
 ovl_status ovl_ctx_destroy(ovl_ctx* ctx) {
   clear_error();
   if (!ctx) return OVL_OK;
-  cudaSetDevice(ctx->device);
+  DeviceGuard dg(ctx->device);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return OVL_OK;
@@ -109,7 +104,7 @@ ovl_status ovl_create_lattice(ovl_ctx* ctx, const int32_t dims[4], int32_t t_bc,
 ovl_status ovl_destroy_lattice(ovl_lattice* lat) {
   clear_error();
   if (!lat) return OVL_OK;
-  cudaSetDevice(lat->ctx->device);
+  DeviceGuard dg(lat->ctx->device);
   free_direct_ws(lat->dws);
   free_multi_ws(lat->mws);
   if (lat->owns_links) {
@@ -129,7 +124,7 @@ ovl_status ovl_set_links(ovl_lattice* lat, const void* U, int32_t U_on_device, u
   clear_error();
   OVL_REQUIRE(lat && U, "ovl_set_links: NULL argument");
   OVL_REQUIRE((formats & ~(OVL_F64 | OVL_F32 | OVL_F16R12)) == 0, "ovl_set_links: unknown format bits 0x%x", formats);
-  OVL_TRY(set_device(lat));
+  OVL_DEVICE_SCOPE(lat->ctx->device);
   const size_t nl = (size_t)36 * lat->g.vol;  // complex entries
   formats |= OVL_F64;
   if (!lat->u64) OVL_CHECK_CUDA(cudaMalloc(&lat->u64, nl * 16));
@@ -157,7 +152,7 @@ ovl_status ovl_set_deflation(ovl_lattice* lat, double m_W, double mu, int32_t m,
   clear_error();
   OVL_REQUIRE(lat, "ovl_set_deflation: NULL lattice");
   OVL_REQUIRE(m >= 0 && m <= 1024, "ovl_set_deflation: m must be in [0, 1024]");
-  OVL_TRY(set_device(lat));
+  OVL_DEVICE_SCOPE(lat->ctx->device);
   cudaFree(lat->defl.R);
   cudaFree(lat->defl.L);
   lat->defl = ovl_deflation();
@@ -209,7 +204,7 @@ ovl_status ovl_to_native(ovl_lattice* lat, int32_t dtype, int32_t nrhs, const vo
   clear_error();
   OVL_REQUIRE(lat && in && out && nrhs >= 1, "ovl_to_native: invalid arguments");
   OVL_REQUIRE(dtype == OVL_C128 || dtype == OVL_C64, "ovl_to_native: dtype");
-  OVL_TRY(set_device(lat));
+  OVL_DEVICE_SCOPE(lat->ctx->device);
   bool f = dtype == OVL_C128;
   OVL_CHECK_CUDA(launch_to_native(lat->g, nrhs, f, in, f, out, (cudaStream_t)stream));
   return OVL_OK;
@@ -219,7 +214,7 @@ ovl_status ovl_from_native(ovl_lattice* lat, int32_t dtype, int32_t nrhs, const 
   clear_error();
   OVL_REQUIRE(lat && in && out && nrhs >= 1, "ovl_from_native: invalid arguments");
   OVL_REQUIRE(dtype == OVL_C128 || dtype == OVL_C64, "ovl_from_native: dtype");
-  OVL_TRY(set_device(lat));
+  OVL_DEVICE_SCOPE(lat->ctx->device);
   bool f = dtype == OVL_C128;
   OVL_CHECK_CUDA(launch_from_native(lat->g, nrhs, f, in, f, out, (cudaStream_t)stream));
   return OVL_OK;
@@ -234,7 +229,7 @@ ovl_status ovl_apply_DW(ovl_lattice* lat, double m_W, double mu, uint32_t flags,
   OVL_REQUIRE((flags & ~(OVL_DAGGER | OVL_GAMMA5 | OVL_NATIVE | OVL_LINKS_F32 | OVL_LINKS_F16R12)) == 0,
               "ovl_apply_DW: unknown flags 0x%x", flags);
   OVL_REQUIRE(2.0 * m_W + 8.0 != 0.0, "ovl_apply_DW: m_W = -4 has no kappa");
-  OVL_TRY(set_device(lat));
+  OVL_DEVICE_SCOPE(lat->ctx->device);
   const bool f64 = dtype == OVL_C128;
   int lf = LINK_F64;
   if (f64) {
@@ -274,7 +269,7 @@ ovl_status ovl_apply_sign(ovl_lattice* lat, const ovl_sign_params* p, int32_t nr
   OVL_REQUIRE(p->precision >= OVL_PREC_F64 && p->precision <= OVL_PREC_F32_F16LINKS, "ovl_apply_sign: precision");
   OVL_REQUIRE(p->tol >= 0, "ovl_apply_sign: tol must be >= 0");
   OVL_REQUIRE(2.0 * p->m_W + 8.0 != 0.0, "ovl_apply_sign: m_W = -4 has no kappa");
-  OVL_TRY(set_device(lat));
+  OVL_DEVICE_SCOPE(lat->ctx->device);
   if (p->method == OVL_DIRECT_2SL)
     return solve_direct(lat, p, nrhs, (const double2*)b, (double2*)x, info, (cudaStream_t)stream);
   if (p->method == OVL_MULTISHIFT_BICG)

@@ -47,6 +47,31 @@ void clear_error();
     if (_s != OVL_OK) return _s;        \
   } while (0)
 
+// Makes device `dev` current for the guard's lifetime and gives the caller back its own current
+// device when the guard goes out of scope (every C-ABI call leaves the caller's device as it was).
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    if ((err = cudaGetDevice(&prev)) != cudaSuccess) {
+      prev = -1;
+      return;
+    }
+    if (prev != dev) err = cudaSetDevice(dev);
+    else prev = -1;  // nothing to restore
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+};
+
+// Enter device `dev` for the rest of the enclosing scope; returns ECUDA from the caller on failure.
+#define OVL_DEVICE_SCOPE(dev)                 \
+  ::ovl::DeviceGuard _ovl_dev_guard(dev);     \
+  OVL_CHECK_CUDA(_ovl_dev_guard.err)
+
 // ------------------------------------------------------------------ complex arithmetic
 template <class R>
 struct cplx {

@@ -10,10 +10,12 @@
 // and allocates no pinned memory; it works on the caller's stream and synchronizes it.
 //
 // Host code cannot use the array's name as a device address (it names a host-side stand-in),
-// so the address is taken with cudaGetSymbolAddress once per device, with that device
-// current, on the first call for that device; that first call should come before any stream
-// capture. Every call shares the array: a call clears the counters that must start at zero,
-// and calls that overlap on the GPU (two streams, two threads) race on the array.
+// so the address is taken with cudaGetSymbolAddress with the lattice's device current: on the
+// first call for that device, which should come before any stream capture, and again on every
+// later call made outside a capture (an address cached before a device reset is never reused).
+// The caller's current device is restored on return, and a stream of another device is refused.
+// Every call shares the array: a call clears the counters that must start at zero, and calls
+// that overlap on the GPU (two streams, two threads) race on the array.
 #include <chrono>
 #include <complex>
 #include <mutex>
@@ -37,13 +39,21 @@ __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 std::mutex g_addr_mu;
 char* g_addr[kMaxDevices] = {nullptr};
 
-ovl_status static_scratch(int dev, char** out) {
+// Device address of the static array on device `dev` (current). Looked up again on every call
+// made outside a stream capture, so that an address cached before a device reset is never
+// reused; inside a capture the address cached by an earlier call is used.
+ovl_status static_scratch(int dev, cudaStream_t st, char** out) {
   std::lock_guard<std::mutex> lk(g_addr_mu);
   if (dev < 0 || dev >= kMaxDevices) {
     set_error("apply_sign_noalloc: device ordinal %d out of range", dev);
     return OVL_EINVAL;
   }
-  if (!g_addr[dev]) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    cs = cudaStreamCaptureStatusActive;  // unknown: keep the cached address if there is one
+  }
+  if (!g_addr[dev] || cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);  // the device is current here
     if (e != cudaSuccess || !p) {
@@ -96,10 +106,16 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   }
   const int kmax = p->fixed_k > 0 ? p->fixed_k : p->k_max;
   OVL_REQUIRE(kmax >= 1, "apply_sign_noalloc: k_max must be >= 1");
-  OVL_CHECK_CUDA(cudaSetDevice(lat->ctx->device));
-  char* base = nullptr;
-  OVL_TRY(static_scratch(lat->ctx->device, &base));
+  OVL_DEVICE_SCOPE(lat->ctx->device);  // the caller's current device is restored on return
   cudaStream_t st = (cudaStream_t)stream;
+  if (st) {  // the scratch address below is this device's: the stream must belong to it too
+    int sdev = -1;
+    OVL_CHECK_CUDA(cudaStreamGetDevice(st, &sdev));
+    OVL_REQUIRE(sdev == lat->ctx->device, "apply_sign_noalloc: the stream belongs to device %d, the lattice to %d",
+                sdev, lat->ctx->device);
+  }
+  char* base = nullptr;
+  OVL_TRY(static_scratch(lat->ctx->device, st, &base));
   const Geom& g = lat->g;
   const size_t n = (size_t)12 * g.vol, elt = f64 ? 16 : 8;
   const int nblk = partial_slots(g), ks = kmax + 2;

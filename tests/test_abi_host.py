@@ -113,3 +113,28 @@ def test_submit_nrhs_inference(ovl):
     assert ovl._nrhs_of(one.ravel(), 1) == 1
     with pytest.raises(ValueError):
         ovl._nrhs_of(one.ravel(), None)
+
+
+def test_sign_buffers_refused_before_the_library(ovl, monkeypatch):
+    """b / x that would let a kernel write out of bounds or read a host pointer are refused in the
+    binding: wrong dtype, sizes that are not whole spinors, x shorter than b, host/device mixes."""
+    import torch
+
+    n = 3072
+    monkeypatch.setattr(ovl, "ovl_lattice_n", lambda lat: n)
+    lat = ovl.ctypes.c_void_p(12345)
+    good = np.zeros(n, np.complex128)
+    cases = [
+        (np.zeros(n, np.complex64), np.zeros(n, np.complex64)),       # not complex128
+        (np.zeros(n + 1, np.complex128), np.zeros(n + 1, np.complex128)),  # not whole spinors
+        (good, np.zeros(n - 12, np.complex128)),                        # x shorter than b
+        (good, torch.zeros(n, dtype=torch.complex128)),                 # host / torch mix
+        (torch.zeros(n, dtype=torch.complex128), torch.zeros(n, dtype=torch.complex128)),  # CPU tensors
+        (np.zeros((2, n), np.complex128)[:, ::2], good),                # not contiguous
+    ]
+    p = ovl.ovl_sign_params_default()
+    for b, x in cases:
+        with pytest.raises((TypeError, ValueError)):
+            ovl.ovl_apply_sign(lat, p, b, x)
+        with pytest.raises((TypeError, ValueError)):
+            ovl.ovl_apply_sign_noalloc(lat, p, b, x)

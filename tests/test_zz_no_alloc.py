@@ -63,3 +63,34 @@ def test_refuses_oversized_scratch(setup):
     with pytest.raises(ovl.OvlError) as e:
         ovl.ovl_apply_sign_noalloc(lat, p, b, torch.empty_like(b))
     assert e.value.status == ovl.OVL_EINVAL and "64 MiB" in str(e.value)
+
+
+def test_deflated_matches_allocating_path_twice(setup, problem_4444):
+    """With 16 LR deflation vectors: the deflated part x_P, the deflation-dot partials (sized by
+    m) and the eigenvalue signs all live in the shared static array too."""
+    ovl, ctx, dims, lat = setup
+    p4 = problem_4444
+    ovl.ovl_set_deflation(lat, -2.0, 0.3, np.ascontiguousarray(p4["R16"].T), np.ascontiguousarray(p4["L16"].T),
+                          p4["lam16"])
+    try:
+        b = torch.from_numpy(p4["b"]).cuda()
+        p = ovl.ovl_sign_params_default(mu=0.3, tol=1e-9, k_max=1000, use_deflation=1)
+        x_ref = torch.empty_like(b)
+        st_ref, _ = ovl.ovl_apply_sign(lat, p, b, x_ref)
+        for _ in range(2):
+            x = torch.full_like(b, float("nan"))
+            st, _ = ovl.ovl_apply_sign_noalloc(lat, p, b, x)
+            assert st == st_ref
+            assert _rel(x, x_ref) < 1e-10
+    finally:
+        ovl.ovl_set_deflation(lat, -2.0, 0.3, None, None, None)
+
+
+def test_current_device_kept(setup):
+    """The entry point leaves the caller's current device as it was."""
+    ovl, ctx, dims, lat = setup
+    b = torch.from_numpy(synth.gaussian_source(dims, 3)).cuda()
+    p = ovl.ovl_sign_params_default(mu=0.3, fixed_k=20)
+    before = torch.cuda.current_device()
+    ovl.ovl_apply_sign_noalloc(lat, p, b, torch.empty_like(b))
+    assert torch.cuda.current_device() == before
