@@ -18,6 +18,8 @@ Modules
   lanczos    direct two-sided Lanczos-LR (Algorithm 4) and multishift iterates
              V_k (T_k - sigma_i)^-1 e1 (Section 2.2, Algorithm 3)
   deflation  critical eigenpairs, x_P (Eq. exact_proj), r, modified shadow vector
+  fom        restarted FOM-LR(m, k) with a rational function, Algorithm 1 (Arnoldi by modified
+             Gram-Schmidt, one basis for all shifts, restarts through the collinear residuals)
   krylov     plain C (OpenMP) FP64 matrix-free H_W(mu) and two-sided Lanczos, Algorithm 4 at
              any lattice size (krylov.c, compiled with gcc on first use or by build_lib())
 
