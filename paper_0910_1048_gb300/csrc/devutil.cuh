@@ -84,6 +84,13 @@ template <> struct Red<double> {
     r.v = __shfl_down_sync(0xffffffffu, v, off);
     return r;
   }
+  __device__ __forceinline__ Red shfl_xor(int m) const {
+    Red r;
+    r.v = __shfl_xor_sync(0xffffffffu, v, m);
+    return r;
+  }
+  // v += a b + c d with two fused operations
+  __device__ __forceinline__ void dot2(double a, double b, double c, double d) { v = fma(a, b, fma(c, d, v)); }
   __device__ __forceinline__ double get() const { return v; }
 };
 template <> struct Red<float> {
@@ -96,6 +103,14 @@ template <> struct Red<float> {
     r.v.lo = __shfl_down_sync(0xffffffffu, v.lo, off);
     return r;
   }
+  __device__ __forceinline__ Red shfl_xor(int m) const {
+    Red r;
+    r.v.hi = __shfl_xor_sync(0xffffffffu, v.hi, m);
+    r.v.lo = __shfl_xor_sync(0xffffffffu, v.lo, m);
+    return r;
+  }
+  // v += a b + c d (the product pair rounded in FP32, the sum kept in float-float)
+  __device__ __forceinline__ void dot2(float a, float b, float c, float d) { add(fmaf(a, b, c * d)); }
   __device__ __forceinline__ double get() const { return (double)v.hi + (double)v.lo; }
 };
 
@@ -125,6 +140,41 @@ __device__ __forceinline__ void block_reduce(Red<R> (&a)[NV], double (&out)[NV])
   __syncthreads();
 }
 
+// Sum 4 accumulators over the block with fewer shuffles: in the first two butterfly levels each
+// lane keeps half of its values and sends the other half (4 -> 2 -> 1 value per lane), then one
+// value per lane finishes the warp; out valid in thread 0. Block size a multiple of 32, <= 1024.
+template <class R>
+__device__ __forceinline__ void block_reduce4(Red<R> (&a)[4], double (&out)[4]) {
+  __shared__ Red<R> sm[4][32];
+  const int t = lin_tid();
+  const int lane = t & 31, warp = t >> 5, nw = lin_nthreads() >> 5;
+  // level 1 (offset 16): lanes < 16 keep values 0, 1; lanes >= 16 keep 2, 3
+  const bool hi16 = lane & 16;
+  Red<R> k0 = hi16 ? a[2] : a[0], k1 = hi16 ? a[3] : a[1];
+  Red<R> s0 = hi16 ? a[0] : a[2], s1 = hi16 ? a[1] : a[3];
+  k0.add(s0.shfl_xor(16));
+  k1.add(s1.shfl_xor(16));
+  // level 2 (offset 8): lanes with bit 8 clear keep k0, set keep k1
+  const bool hi8 = lane & 8;
+  Red<R> k = hi8 ? k1 : k0, sd = hi8 ? k0 : k1;
+  k.add(sd.shfl_xor(8));
+#pragma unroll
+  for (int off = 4; off > 0; off >>= 1) k.add(k.shfl_xor(off));
+  // lane 0 holds value 0, lane 8 value 1, lane 16 value 2, lane 24 value 3 of this warp
+  if ((lane & 7) == 0) sm[lane >> 3][warp] = k;
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      Red<R> v = lane < nw ? sm[i][lane] : Red<R>();
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v.add(v.shfl_down(off));
+      out[i] = v.get();
+    }
+  }
+  __syncthreads();
+}
+
 // Write this block's NV partials; returns true in every thread of the last block to arrive.
 // The counter is reset to 0 by the last block so the next launch starts clean.
 template <int NV>
@@ -148,9 +198,22 @@ __device__ __forceinline__ void reduce_partials(const double* part, int nblk, do
   __threadfence();
 #pragma unroll
   for (int i = 0; i < NV; ++i) v[i] = 0.0;
-  for (int b = lin_tid(); b < nblk; b += lin_nthreads())
+  // four partials per thread per pass, loaded before they are added (one memory round trip per
+  // pass instead of one per partial)
+  const int nt = lin_nthreads();
+  for (int b0 = lin_tid(); b0 < nblk; b0 += 4 * nt) {
+    double x[4][NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] += __ldcg(part + (size_t)b * NV + i);
+    for (int u = 0; u < 4; ++u) {
+      const int b = b0 + u * nt;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) x[u][i] = b < nblk ? __ldcg(part + (size_t)b * NV + i) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) v[i] += x[u][i];
+  }
   block_sum<NV>(v);
 }
 
@@ -183,14 +246,17 @@ __device__ __forceinline__ void store_spin(typename V2<R>::T* p, int vol, int s,
 // ------------------------------------------------------------------ split-site pair stencil
 // For small lattices (too few sites to fill 152 SMs with one thread per site) every site is
 // shared by 8 threads: threadIdx.y = which * 4 + dir, `which` selecting input 0 (coefficients
-// c0) or input 1 (c1), `dir` one direction's forward and backward hops. Directions 1..3 leave
-// their partial spinors in shared memory; the dir-0 thread of each (site, which) adds them to
-// its own hops and the diagonal term and hands the full D_W(+-mu) psi to `emit`.
+// c0) or input 1 (c1), `dir` one direction's forward and backward hops. After the hops each
+// thread finalises one spin of its site (spin = dir, the three colours): the other three
+// directions leave their contributions to that spin in shared memory, and the finalising thread
+// adds them to its own and to the diagonal term, then hands D_W(+-mu) psi at (spin, colours
+// 0..2) to `emit(which, site, spin, x[3])`. The epilogue (scaling, stores, reductions) is thus
+// spread over all eight warps of the block instead of the two that held the first direction.
 constexpr int kSplitSites = 32;
 
 template <class R>
 struct SplitSmem {
-  cplx<R> part[2][3][12][kSplitSites];
+  cplx<R> part[2][3][12][kSplitSites];  // [which][slot of the contributing direction][component][site]
 };
 
 template <class R, int LF, class Emit>
@@ -203,35 +269,43 @@ __device__ __forceinline__ void pair_split(const Geom& g, const Links& U, const 
   const HopCoef<R>& c = which ? c1 : c0;
   Loader<R, true> ld{in, g.vol, false};
   Spin<R> acc;
+#pragma unroll
+  for (int q = 0; q < 12; ++q) acc.c[q / 3][q % 3] = mk<R>(0, 0);
   if (s < g.vol) {
     Nbr n;
     neighbours(g, s, n);
     if (dir == 0) {
-      ld(s, acc);  // diagonal term
       hop_dir<0, LF>(g, U, s, n, c.ks, c.ks, ld, acc);
+    } else if (dir == 1) {
+      hop_dir<1, LF>(g, U, s, n, c.ks, c.ks, ld, acc);
+    } else if (dir == 2) {
+      hop_dir<2, LF>(g, U, s, n, c.ks, c.ks, ld, acc);
     } else {
-#pragma unroll
-      for (int q = 0; q < 12; ++q) acc.c[q / 3][q % 3] = mk<R>(0, 0);
-      if (dir == 1) {
-        hop_dir<1, LF>(g, U, s, n, c.ks, c.ks, ld, acc);
-      } else if (dir == 2) {
-        hop_dir<2, LF>(g, U, s, n, c.ks, c.ks, ld, acc);
-      } else {
-        R ktf = (n.t == g.lt - 1) ? (R)g.t_bc * c.ktf : c.ktf;
-        R ktb = (n.t == 0) ? (R)g.t_bc * c.ktb : c.ktb;
-        hop_dir<3, LF>(g, U, s, n, ktf, ktb, ld, acc);
-      }
-#pragma unroll
-      for (int q = 0; q < 12; ++q) sm.part[which][dir - 1][q][tx] = acc.c[q / 3][q % 3];
+      R ktf = (n.t == g.lt - 1) ? (R)g.t_bc * c.ktf : c.ktf;
+      R ktb = (n.t == 0) ? (R)g.t_bc * c.ktb : c.ktb;
+      hop_dir<3, LF>(g, U, s, n, ktf, ktb, ld, acc);
     }
+    // contributions to the spins finalised by the other three threads; slot = this direction's
+    // index among the three
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+      if (sp != dir)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sm.part[which][dir < sp ? dir : dir - 1][sp * 3 + a][tx] = acc.c[sp][a];
   }
   __syncthreads();
-  if (dir == 0 && s < g.vol) {
+  if (s < g.vol) {
+    cplx<R> x[3];
 #pragma unroll
-    for (int q = 0; q < 12; ++q)
-      acc.c[q / 3][q % 3] = acc.c[q / 3][q % 3] + sm.part[which][0][q][tx] + sm.part[which][1][q][tx] +
-                            sm.part[which][2][q][tx];
-    emit(which, s, acc);
+    for (int sp = 0; sp < 4; ++sp)
+      if (sp == dir)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int q = sp * 3 + a;
+          x[a] = ldc<R>(in, (size_t)q * g.vol + s) + acc.c[sp][a] + sm.part[which][0][q][tx] +
+                 sm.part[which][1][q][tx] + sm.part[which][2][q][tx];
+        }
+    emit(which, s, dir, x);
   }
 }
 

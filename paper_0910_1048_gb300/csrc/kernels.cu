@@ -10,6 +10,7 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
 
 #include "devutil.cuh"
 #include "kernels.h"
@@ -130,6 +131,41 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? (LF == LINK_F16R12 ? 
   store_spin<R, NOUT>(out + off, g.vol, s, o);
 }
 
+// The FP32 operator on a batch of sources, native layout in and out. A thread applies the links of
+// its site to a group of G sources (each link loaded once per group), and the grid is ordered
+// group-fastest (block b: site tile b / ngroups, group b % ngroups), so that the blocks of all
+// groups of one site tile run together and a tile's link lines come from DRAM once and from L2
+// for the other groups. G = 1 is the single-source kernel in that order.
+template <int LF, bool G5IN, int G>
+__global__ void __launch_bounds__(kBlock, G == 1 ? 7 : (G == 2 ? 4 : 2))
+    k_dslash_group(Geom g, Links U, HopCoef<float> c, bool g5_out, int nrhs,
+                                                         const float2* in, float2* out) {
+  const int ngroups = (nrhs + G - 1) / G;
+  const int tile = blockIdx.x / ngroups, grp = blockIdx.x % ngroups;
+  const int s = tile * blockDim.x + threadIdx.x;
+  if (s >= g.vol) return;
+  const int r0 = grp * G;
+  const int nact = min(G, nrhs - r0);
+  const size_t n = (size_t)12 * g.vol;
+  Loader<float, true> ld[G];
+#pragma unroll
+  for (int r = 0; r < G; ++r) ld[r] = Loader<float, true>{in + (size_t)(r0 + (r < nact ? r : 0)) * n, g.vol, G5IN};
+  Spin<float> o[G];
+  dslash_site_g<LF, G>(g, U, s, c, ld, nact, o);
+  const float sg = g5_out ? -1.f : 1.f;
+#pragma unroll
+  for (int r = 0; r < G; ++r) {
+    if (r < nact) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        o[r].c[2][a] = sg * o[r].c[2][a];
+        o[r].c[3][a] = sg * o[r].c[3][a];
+      }
+      store_spin<float, true>(out + (size_t)(r0 + r) * n, g.vol, s, o[r]);
+    }
+  }
+}
+
 template <class R, int LF, bool G5IN>
 static cudaError_t dslash_g(dim3 grid, const Geom& g, const Links& U, HopCoef<R> c, bool go, bool nin, bool nout,
                             const typename V2<R>::T* i, typename V2<R>::T* o, cudaStream_t st) {
@@ -156,17 +192,75 @@ static cudaError_t dslash_t(const Geom& g, const Links& U, double m_w, double mu
             : dslash_g<R, LF, false>(grid, g, U, c, go, nin, nout, i, o, st);
 }
 
+template <int LF, int G>
+static cudaError_t dslash_group_g(const Geom& g, const Links& U, HopCoef<float> c, bool gi, bool go, int nrhs,
+                                  const void* in, void* out, cudaStream_t st) {
+  const unsigned tiles = (unsigned)((g.vol + kBlock - 1) / kBlock), ngroups = (unsigned)((nrhs + G - 1) / G);
+  if (gi)
+    k_dslash_group<LF, true, G><<<tiles * ngroups, kBlock, 0, st>>>(g, U, c, go, nrhs, (const float2*)in, (float2*)out);
+  else
+    k_dslash_group<LF, false, G><<<tiles * ngroups, kBlock, 0, st>>>(g, U, c, go, nrhs, (const float2*)in,
+                                                                      (float2*)out);
+  return cudaGetLastError();
+}
+
+// Sources per link load of the batched stencil (1, 2 or 4), chosen per (volume, links, batch) by
+// timing the three on the first call (the real launch follows and rewrites `out`).
+static std::mutex g_group_mu;
+static std::map<std::tuple<int, int, int>, int> g_group;
+
+template <int LF>
+static cudaError_t dslash_group_t(const Geom& g, const Links& U, double m_w, double mu, bool gi, bool go, int nrhs,
+                                  const void* in, void* out, cudaStream_t st) {
+  const HopCoef<float> c = hop_coef<float>(m_w, mu);
+  auto run = [&](int G) {
+    return G == 4 ? dslash_group_g<LF, 4>(g, U, c, gi, go, nrhs, in, out, st)
+                  : G == 2 ? dslash_group_g<LF, 2>(g, U, c, gi, go, nrhs, in, out, st)
+                           : dslash_group_g<LF, 1>(g, U, c, gi, go, nrhs, in, out, st);
+  };
+  int G = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_group_mu);
+    auto it = g_group.find({g.vol, LF, nrhs});
+    if (it != g_group.end()) G = it->second;
+    if (!G) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) {
+        float best = 1e30f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; ++rep)
+          for (int cand : {1, 2, 4}) {
+            ok = ok && cudaEventRecord(a, st) == cudaSuccess && run(cand) == cudaSuccess &&
+                 cudaEventRecord(b, st) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess;
+            float ms = 0;
+            if (ok && rep > 0 && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best) best = ms, G = cand;
+          }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        if (!ok) G = 0;
+      }
+      cudaGetLastError();
+      if (G) g_group[{g.vol, LF, nrhs}] = G;
+    }
+  }
+  return run(G ? G : kLinkGroup);
+}
+
 cudaError_t launch_dslash(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, bool g5_in,
                           bool g5_out, bool native_in, bool native_out, int nrhs, const void* in, void* out,
                           cudaStream_t st) {
   if (f64) return dslash_t<double, LINK_F64>(g, U, m_w, mu, g5_in, g5_out, native_in, native_out, nrhs, in, out, st);
+  if (nrhs > 1 && native_in && native_out) {  // a batch: links once per group of sources
+    if (lf == LINK_F16R12) return dslash_group_t<LINK_F16R12>(g, U, m_w, mu, g5_in, g5_out, nrhs, in, out, st);
+    return dslash_group_t<LINK_F32>(g, U, m_w, mu, g5_in, g5_out, nrhs, in, out, st);
+  }
   if (lf == LINK_F16R12)
     return dslash_t<float, LINK_F16R12>(g, U, m_w, mu, g5_in, g5_out, native_in, native_out, nrhs, in, out, st);
   return dslash_t<float, LINK_F32>(g, U, m_w, mu, g5_in, g5_out, native_in, native_out, nrhs, in, out, st);
 }
 
 // ------------------------------------------------------------------ Lanczos: start
-// part layout for this kernel: [nrhs][nblk][4] = (|r|^2, Re r^H r~, Im r^H r~, unused)
+// part layout for this kernel: [nrhs][nblk][4] = (|r|^2, Re r^H r~, Im r^H r~, |r~|^2)
 template <class R>
 __global__ void __launch_bounds__(kBlock) k_lz_start(Geom g, LzDev lz, typename V2<R>::T* vh, typename V2<R>::T* wh,
                                                      double2* xp, const double2* b, int m, const double2* Rv,
@@ -199,6 +293,7 @@ __global__ void __launch_bounds__(kBlock) k_lz_start(Geom g, LzDev lz, typename 
       zd ip = cdot(r, rt);
       acc[1] += ip.re;
       acc[2] += ip.im;
+      acc[3] += norm2(rt);
     }
   }
   block_sum<4>(acc);
@@ -216,9 +311,11 @@ __global__ void __launch_bounds__(kBlock) k_lz_start(Geom g, LzDev lz, typename 
       lz.sv[o + 1] = 1.0 / b0;
       lz.sw[o + 1] = make_double2(b0 * ip.re / den, -b0 * ip.im / den);
       lz.vnorm[o + 1] = 1.0;
-      lz.j[rhs] = 1;
-      // 3: r = 0 (b lies in the deflated space, x = x_P); 1: r^H r~ = 0 (breakdown at start)
-      lz.status[rhs] = nr2 == 0.0 ? 3 : (den > 0.0 ? 0 : 1);
+      // 3: r = 0 (b lies in the deflated space, x = x_P); 1: |r^H r~| <= 1e-14 |r| |r~| (breakdown
+      // at the start, the same relative test as every later step; j = 0: no Krylov part, x = x_P)
+      const int st = nr2 == 0.0 ? 3 : (sqrt(den) > 1e-14 * sqrt(nr2 * acc[3]) && den < 1e300 ? 0 : 1);
+      lz.status[rhs] = st;
+      lz.j[rhs] = st == 1 ? 0 : 1;
     }
   }
 }
@@ -295,13 +392,38 @@ cudaError_t launch_lanczos_start(const Geom& g, bool f64, const LzDev& lz, const
 }
 
 // ------------------------------------------------------------------ Lanczos: one step
+// Last block of the pair stencil of step j: alpha_j = conj(sw_j) sum what_j^H A vhat_j (pv[0..1],
+// the partials of the product with the scaled A v_j), and the coefficients of the update that
+// follows, so that its threads only load them:
+//   vhat_{j+1} = A v_j - (sv_j alpha_j) vhat_j - (sv_{j-1} beta_{j-1}) vhat_{j-1},
+//   what_{j+1} = A^H w_j - (sw_j conj(alpha_j)) what_j - (delta_{j-1} sw_{j-1}) what_{j-1}.
+__device__ __forceinline__ void lz_alpha_finish(const LzDev& lz, int rhs, size_t o, int j, double2 swd,
+                                                const double (&pv)[4]) {
+  const zd sw = mk(swd.x, swd.y);
+  const zd alpha = conj(sw) * mk(pv[0], pv[1]);
+  lz.alpha[o + j] = make_double2(alpha.re, alpha.im);
+  const zd a1 = lz.sv[o + j] * alpha, b1 = sw * conj(alpha);
+  zd a2 = mk(0.0, 0.0), b2 = mk(0.0, 0.0);
+  if (j > 1) {
+    a2 = lz.sv[o + j - 1] * ldc<double>(lz.beta, o + j - 1);
+    b2 = lz.delta[o + j - 1] * ldc<double>(lz.sw, o + j - 1);
+  }
+  double2* u = lz.ucoef + (size_t)rhs * 4;
+  u[0] = make_double2(a1.re, a1.im);
+  u[1] = make_double2(a2.re, a2.im);
+  u[2] = make_double2(b1.re, b1.im);
+  u[3] = make_double2(b2.re, b2.im);
+}
+
 // Pair stencil: Av_j = sv_j H(mu) vhat_j, Aw_j = sw_j H(-mu) what_j (H(mu)^H = H(-mu)),
 // alpha_j = w_j^H A v_j = conj(sw_j) sum_x what_j(x)^H Av_j(x).
-// Block (kPairSites, 2): threadIdx.y = 0 applies H(mu) to vhat, = 1 applies H(-mu) to what,
-// for the same kPairSites sites, so each thread holds one stencil's registers and the two
-// halves of the block share the link lines in L1.
-template <class R, int LF>
-__global__ void __launch_bounds__(2 * kPairSites) k_lz_pair(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm, LzDev lz,
+// Block (PS, 2): threadIdx.y = 0 applies H(mu) to vhat, = 1 applies H(-mu) to what, for the same
+// PS sites, so each thread holds one stencil's registers and the two halves of the block share
+// the link lines in L1. PS (64, 48 or 32 sites) sets how evenly the blocks spread over the SMs:
+// 12^4 FP64 with 64 sites is 324 blocks, three on 20 SMs and two on the other 132 (the SMs sat
+// idle a third of the time under ncu); with 48 sites it is 432 blocks, 2.84 per SM.
+template <class R, int LF, int PS>
+__global__ void __launch_bounds__(2 * PS) k_lz_pair(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm, LzDev lz,
                                                             const typename V2<R>::T* vh, const typename V2<R>::T* wh,
                                                             typename V2<R>::T* av, typename V2<R>::T* aw) {
   using T = typename V2<R>::T;
@@ -313,7 +435,7 @@ __global__ void __launch_bounds__(2 * kPairSites) k_lz_pair(Geom g, Links U, Hop
   const double2 swd = lz.sw[o + j];
   const T* vj = vh + ((size_t)rhs * (lz.kmax + 1) + (j - 1)) * n;
   const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
-  const int s = blockIdx.x * kPairSites + threadIdx.x;
+  const int s = blockIdx.x * PS + threadIdx.x;
   const bool is_w = threadIdx.y == 1;
   Red<R> acc[2];
   if (s < g.vol) {
@@ -353,15 +475,13 @@ __global__ void __launch_bounds__(2 * kPairSites) k_lz_pair(Geom g, Links U, Hop
   double pv[4] = {tot[0], tot[1], 0, 0};
   if (publish_partials<4>(pv, part, lz.count + rhs)) {
     reduce_partials<4>(part, gridDim.x, pv);
-    if (lin_tid() == 0) {
-      zd sum = mk(pv[0], pv[1]);
-      zd alpha = conj(mk(swd.x, swd.y)) * sum;
-      lz.alpha[o + j] = make_double2(alpha.re, alpha.im);
-    }
+    if (lin_tid() == 0) lz_alpha_finish(lz, rhs, o, j, swd, pv);
   }
 }
 
-// The same step with 8 threads per site (small lattices): see pair_split.
+// The same step with 8 threads per site (small lattices): see pair_split. Each thread finishes
+// one spin (three colours) of its site: scale, gamma5, store, and for the v half the partial of
+// alpha_j.
 template <class R, int LF>
 __global__ void __launch_bounds__(8 * kSplitSites) k_lz_pair_split(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm,
                                                                    LzDev lz, const typename V2<R>::T* vh,
@@ -380,28 +500,22 @@ __global__ void __launch_bounds__(8 * kSplitSites) k_lz_pair_split(Geom g, Links
   const R sv = (R)lz.sv[o + j];
   const cplx<R> sw = mk<R>((R)swd.x, (R)swd.y);
   Red<R> acc[2];
-  pair_split<R, LF>(g, U, cp, cm, vj, wj, sm, [&](int which, int s, Spin<R>& out) {
+  pair_split<R, LF>(g, U, cp, cm, vj, wj, sm, [&](int which, int s, int sp, cplx<R> (&x)[3]) {
+    const R g5 = sp >= 2 ? (R)-1 : (R)1;
     if (which == 0) {
-      cplx<R> wv[12];  // loads first (see k_lz_pair)
+      cplx<R> wv[3];  // loads first (see k_lz_pair)
 #pragma unroll
-      for (int c = 0; c < 12; ++c) wv[c] = ldc<R>(wj, (size_t)c * g.vol + s);
-      cplx<R> a = mk<R>(0, 0);
+      for (int a = 0; a < 3; ++a) wv[a] = ldc<R>(wj, (size_t)(sp * 3 + a) * g.vol + s);
 #pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        cplx<R> x = sv * out.c[c / 3][c % 3];
-        if (c >= 6) x = -x;  // gamma5
-        stc<R>(av + (size_t)rhs * n, (size_t)c * g.vol + s, x);
-        a = a + cdot(wv[c], x);
+      for (int a = 0; a < 3; ++a) {
+        const cplx<R> y = (g5 * sv) * x[a];
+        stc<R>(av + (size_t)rhs * n, (size_t)(sp * 3 + a) * g.vol + s, y);
+        acc[0].dot2(wv[a].re, y.re, wv[a].im, y.im);
+        acc[1].dot2(wv[a].re, y.im, -wv[a].im, y.re);
       }
-      acc[0].add(a.re);
-      acc[1].add(a.im);
     } else {
 #pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        cplx<R> y = sw * out.c[c / 3][c % 3];
-        if (c >= 6) y = -y;
-        stc<R>(aw + (size_t)rhs * n, (size_t)c * g.vol + s, y);
-      }
+      for (int a = 0; a < 3; ++a) stc<R>(aw + (size_t)rhs * n, (size_t)(sp * 3 + a) * g.vol + s, g5 * (sw * x[a]));
     }
   });
   double tot[2];
@@ -410,37 +524,33 @@ __global__ void __launch_bounds__(8 * kSplitSites) k_lz_pair_split(Geom g, Links
   double pv[4] = {tot[0], tot[1], 0, 0};
   if (publish_partials<4>(pv, part, lz.count + rhs)) {
     reduce_partials<4>(part, gridDim.x, pv);
-    if (lin_tid() == 0) {
-      zd alpha = conj(mk(swd.x, swd.y)) * mk(pv[0], pv[1]);
-      lz.alpha[o + j] = make_double2(alpha.re, alpha.im);
-    }
+    if (lin_tid() == 0) lz_alpha_finish(lz, rhs, o, j, swd, pv);
   }
 }
 
 // vhat_{j+1} = Av_j - alpha_j v_j - beta_{j-1} v_{j-1}
 // what_{j+1} = Aw_j - conj(alpha_j) w_j - conj(delta_{j-1}) w_{j-1}    (Eqs. 2sided1/2)
 // then delta_j = sqrt|what^H vhat|, beta_j = what^H vhat / delta_j (scaling reading).
-// One thread per vector element (component, site): 12 V threads per rhs.
+// Element-parallel, grid-stride: each thread takes two elements per pass, both loaded before
+// either is used. FP64 grids have one pass (256 elements per block): FP64 makes this kernel bound
+// by the FP64 pipe, and only many short blocks, which the hardware hands to whichever SM is free,
+// give every SM the same share (324 blocks of six passes at 12^4 left the SMs idle half the time);
+// a block's partial sums sit at its own index, so the reductions keep a fixed order. The
+// coefficients come ready from the pair stencil's last block.
 template <class R>
 __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typename V2<R>::T* vh,
                                                          typename V2<R>::T* wh, const typename V2<R>::T* av,
-                                                         const typename V2<R>::T* aw, int elt) {
+                                                         const typename V2<R>::T* aw) {
   using T = typename V2<R>::T;
   const int rhs = blockIdx.y;
   if (lz.status[rhs]) return;
   const int j = lz.j[rhs];
   const size_t n = (size_t)12 * g.vol;
   const size_t o = (size_t)rhs * (lz.kmax + 2);
-  const zd alpha = ldc<double>(lz.alpha, o + j);
-  const double svj = lz.sv[o + j];
-  const zd swj = ldc<double>(lz.sw, o + j);
-  zd cv1 = svj * alpha, cw1 = swj * conj(alpha), cv2 = mk(0.0, 0.0), cw2 = mk(0.0, 0.0);
-  if (j > 1) {
-    cv2 = lz.sv[o + j - 1] * ldc<double>(lz.beta, o + j - 1);
-    cw2 = lz.delta[o + j - 1] * ldc<double>(lz.sw, o + j - 1);
-  }
-  const cplx<R> a1 = mk<R>((R)cv1.re, (R)cv1.im), a2 = mk<R>((R)cv2.re, (R)cv2.im);
-  const cplx<R> b1 = mk<R>((R)cw1.re, (R)cw1.im), b2 = mk<R>((R)cw2.re, (R)cw2.im);
+  const double2* uc = lz.ucoef + (size_t)rhs * 4;
+  const double2 u0 = uc[0], u1 = uc[1], u2 = uc[2], u3 = uc[3];
+  const cplx<R> a1 = mk<R>((R)u0.x, (R)u0.y), a2 = mk<R>((R)u1.x, (R)u1.y);
+  const cplx<R> b1 = mk<R>((R)u2.x, (R)u2.y), b2 = mk<R>((R)u3.x, (R)u3.y);
   const T* vj = vh + ((size_t)rhs * (lz.kmax + 1) + (j - 1)) * n;
   const T* vjm = vh + ((size_t)rhs * (lz.kmax + 1) + (j > 1 ? j - 2 : 0)) * n;
   T* vnew = vh + ((size_t)rhs * (lz.kmax + 1) + j) * n;
@@ -448,26 +558,50 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typen
   T* wnew = wh + ((size_t)((j + 1) & 1) * lz.nrhs + rhs) * n;  // holds what_{j-1} until overwritten
   const T* avr = av + (size_t)rhs * n;
   const T* awr = aw + (size_t)rhs * n;
+  const bool prev = j > 1;
   Red<R> acc[4];
-  // elt elements per thread, block-contiguous per pass (coalesced)
-  for (int q = 0; q < elt; ++q) {
-    const size_t e = ((size_t)blockIdx.x * elt + q) * blockDim.x + threadIdx.x;
-    if (e >= n) break;
-    cplx<R> x = cmsub(ldc<R>(avr, e), a1, ldc<R>(vj, e));
-    cplx<R> y = cmsub(ldc<R>(awr, e), b1, ldc<R>(wj, e));
-    if (j > 1) {
-      x = cmsub(x, a2, ldc<R>(vjm, e));
-      y = cmsub(y, b2, ldc<R>(wnew, e));
+  const size_t step = (size_t)gridDim.x * blockDim.x * 2;
+  for (size_t e0 = (size_t)blockIdx.x * blockDim.x * 2 + threadIdx.x; e0 < n; e0 += step) {
+    const size_t e1 = e0 + blockDim.x;
+    const bool has1 = e1 < n;
+    const cplx<R> z = mk<R>(0, 0);
+    const cplx<R> A0 = ldc<R>(avr, e0), W0 = ldc<R>(awr, e0), v0 = ldc<R>(vj, e0), w0 = ldc<R>(wj, e0);
+    const cplx<R> A1 = has1 ? ldc<R>(avr, e1) : z, W1 = has1 ? ldc<R>(awr, e1) : z;
+    const cplx<R> v1 = has1 ? ldc<R>(vj, e1) : z, w1 = has1 ? ldc<R>(wj, e1) : z;
+    cplx<R> pv0 = z, pw0 = z, pv1 = z, pw1 = z;
+    if (prev) {
+      pv0 = ldc<R>(vjm, e0);
+      pw0 = ldc<R>(wnew, e0);
+      if (has1) {
+        pv1 = ldc<R>(vjm, e1);
+        pw1 = ldc<R>(wnew, e1);
+      }
     }
-    stc<R>(vnew, e, x);
-    stc<R>(wnew, e, y);
-    acc[0].add(fma(y.re, x.re, y.im * x.im));  // (y^H x).re
-    acc[1].add(fma(y.re, x.im, -(y.im * x.re)));
-    acc[2].add(fma(x.re, x.re, x.im * x.im));
-    acc[3].add(fma(y.re, y.re, y.im * y.im));
+    cplx<R> x0 = cmsub(A0, a1, v0), y0 = cmsub(W0, b1, w0);
+    cplx<R> x1 = cmsub(A1, a1, v1), y1 = cmsub(W1, b1, w1);
+    if (prev) {
+      x0 = cmsub(x0, a2, pv0);
+      y0 = cmsub(y0, b2, pw0);
+      x1 = cmsub(x1, a2, pv1);
+      y1 = cmsub(y1, b2, pw1);
+    }
+    stc<R>(vnew, e0, x0);
+    stc<R>(wnew, e0, y0);
+    acc[0].dot2(y0.re, x0.re, y0.im, x0.im);  // (y^H x).re
+    acc[1].dot2(y0.re, x0.im, -y0.im, x0.re);  // (y^H x).im
+    acc[2].dot2(x0.re, x0.re, x0.im, x0.im);
+    acc[3].dot2(y0.re, y0.re, y0.im, y0.im);
+    if (has1) {
+      stc<R>(vnew, e1, x1);
+      stc<R>(wnew, e1, y1);
+      acc[0].dot2(y1.re, x1.re, y1.im, x1.im);
+      acc[1].dot2(y1.re, x1.im, -y1.im, x1.re);
+      acc[2].dot2(x1.re, x1.re, x1.im, x1.im);
+      acc[3].dot2(y1.re, y1.re, y1.im, y1.im);
+    }
   }
   double tot[4];
-  block_reduce<R, 4>(acc, tot);
+  block_reduce4<R>(acc, tot);
   double* part = lz.part + (size_t)rhs * lz.nblk * 4;
   if (publish_partials<4>(tot, part, lz.count + rhs)) {
     double sums[4];
@@ -492,6 +626,21 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typen
   }
 }
 
+template <int PS>
+static cudaError_t pair_unsplit(const Geom& g, const Links& U, int lf, bool f64, HopCoef<double> dp, HopCoef<double> dm,
+                                HopCoef<float> fp, HopCoef<float> fm, const LzDev& lz, const LzVecs& vec,
+                                cudaStream_t st) {
+  dim3 grid((g.vol + PS - 1) / PS, lz.nrhs), block(PS, 2);
+  if (f64)
+    return launch_plain(k_lz_pair<double, LINK_F64, PS>, grid, block, st, g, U, dp, dm, lz, (const double2*)vec.vh,
+                        (const double2*)vec.wh, (double2*)vec.av, (double2*)vec.aw);
+  if (lf == LINK_F16R12)
+    return launch_plain(k_lz_pair<float, LINK_F16R12, PS>, grid, block, st, g, U, fp, fm, lz, (const float2*)vec.vh,
+                        (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
+  return launch_plain(k_lz_pair<float, LINK_F32, PS>, grid, block, st, g, U, fp, fm, lz, (const float2*)vec.vh,
+                      (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
+}
+
 cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
                                 const LzDev& lz, const LzVecs& vec, cudaStream_t st, int variant) {
   if (variant < 0) variant = tuned_pair_variant(g.vol, f64 ? 0 : lf);
@@ -512,31 +661,28 @@ cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64,
     else
       e = launch_plain(k_lz_pair_split<float, LINK_F32>, grid, block, st, g, U, fp, fm, lz, fv, fw, (float2*)vec.av,
                      (float2*)vec.aw);
+  } else if (variant == 2) {
+    e = pair_unsplit<48>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
+  } else if (variant == 3) {
+    e = pair_unsplit<32>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
   } else {
-    dim3 grid((g.vol + kPairSites - 1) / kPairSites, lz.nrhs), block(kPairSites, 2);
-    if (f64)
-      e = launch_plain(k_lz_pair<double, LINK_F64>, grid, block, st, g, U, dp, dm, lz, dv, dw, (double2*)vec.av,
-                     (double2*)vec.aw);
-    else if (lf == LINK_F16R12)
-      e = launch_plain(k_lz_pair<float, LINK_F16R12>, grid, block, st, g, U, fp, fm, lz, fv, fw, (float2*)vec.av,
-                     (float2*)vec.aw);
-    else
-      e = launch_plain(k_lz_pair<float, LINK_F32>, grid, block, st, g, U, fp, fm, lz, fv, fw, (float2*)vec.av,
-                     (float2*)vec.aw);
+    e = pair_unsplit<kPairSites>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
   }
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_lanczos_update(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, cudaStream_t st) {
-  const int elt = vec_elts(g, lz.nrhs, f64);
+  // FP64: two elements per thread, one pass (see k_lz_update); FP32: enough elements per thread to
+  // amortise the block reduction, at least four blocks per SM over the batch
+  const int elt = f64 ? 2 : std::max(2, (vec_elts(g, lz.nrhs, false) + 1) & ~1);
   dim3 grid(vec_blocks(g, elt), lz.nrhs);
   cudaError_t e;
   if (f64)
     e = launch_plain(k_lz_update<double>, grid, dim3(kVecBlock), st, g, lz, (double2*)vec.vh, (double2*)vec.wh,
-                   (const double2*)vec.av, (const double2*)vec.aw, elt);
+                   (const double2*)vec.av, (const double2*)vec.aw);
   else
     e = launch_plain(k_lz_update<float>, grid, dim3(kVecBlock), st, g, lz, (float2*)vec.vh, (float2*)vec.wh,
-                   (const float2*)vec.av, (const float2*)vec.aw, elt);
+                   (const float2*)vec.av, (const float2*)vec.aw);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 

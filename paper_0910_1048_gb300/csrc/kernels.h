@@ -9,6 +9,7 @@ namespace ovl {
 
 constexpr int kBlock = 128;     // threads per block of the site-parallel kernels
 constexpr int kPairSites = 64;  // sites per block of the pair stencil (x2 threads)
+constexpr int kLinkGroup = 4;     // sources that share one load of a site's links in the batched FP32 kernels
 constexpr int kSplitVolume = 32768;  // below this many sites the pair stencils split each site over 8 threads
 inline bool use_split(const Geom& g) { return g.vol < kSplitVolume; }
 // Plain launch through cudaLaunchKernelEx (one call site per kernel shape, error returned).
@@ -28,21 +29,25 @@ inline cudaError_t launch_plain(void (*kern)(KArgs...), dim3 grid, dim3 block, c
 }
 
 // Pair-stencil variant chosen by the autotuner for (volume, precision): -1 none yet,
-// 0 one thread per site, 1 split over 8 threads. Thread-safe, process-wide. (A 16-thread split,
+// 0 one thread per site (64 sites per block), 1 split over 8 threads, 2 / 3 one thread per site
+// with 48 / 32 sites per block (the multishift kernels run variants 0, 2, 3 as 0). Thread-safe,
+// process-wide. (A 16-thread split,
 // one hop per thread, measured 54 us against 32 us for FP64 at 8^4: more index and reduction
 // work than the extra warps hide.)
+constexpr int kPairVariants = 4;
 int tuned_pair_variant(int vol, int prec);
 // Returns the variant for the key, running `measure` (which returns 0 or 1) under the table's
 // lock the first time, so that every solve in the process uses one decision per key.
 int tune_pair_variant(int vol, int prec, int (*measure)(void*), void* arg);
 constexpr int kVecBlock = 128;  // threads per block of the element-parallel vector kernels
 inline unsigned vec_blocks(const Geom& g) { return (unsigned)((12 * (size_t)g.vol + kVecBlock - 1) / kVecBlock); }
-// Elements per thread of the FP32 element-parallel kernels: enough to amortise the block
-// reduction, while keeping at least about four blocks per SM over the whole grid.
+// Elements per thread of the element-parallel kernels: enough to amortise the per-thread set-up and
+// the block reduction, while keeping at least about four (FP32) or two (FP64) blocks per SM over the
+// whole grid. FP64 threads take more elements: every FP64 instruction of the reduction tree costs
+// 64 FP32 ones on this GPU.
 inline int vec_elts(const Geom& g, int nrhs, bool f64) {
-  if (f64) return 1;
   const size_t total = 12 * (size_t)g.vol * (size_t)nrhs;
-  return (int)std::max<size_t>(1, std::min<size_t>(8, total / ((size_t)kVecBlock * 608)));
+  return (int)std::max<size_t>(1, std::min<size_t>(8, total / ((size_t)kVecBlock * (f64 ? 304 : 608))));
 }
 inline unsigned vec_blocks(const Geom& g, int elt) {
   return (unsigned)((12 * (size_t)g.vol + (size_t)kVecBlock * elt - 1) / ((size_t)kVecBlock * elt));
@@ -67,6 +72,8 @@ struct LzDev {
   double* beta0 = nullptr;  // [nrhs] ||r||
   double* part = nullptr;   // [nrhs][nblk][4] block partials
   unsigned* count = nullptr;// [nrhs] last-block counters (kept at 0 between launches)
+  double2* ucoef = nullptr; // [nrhs][4] coefficients of the next update, written with alpha_j:
+                            // sv_j alpha_j, sv_{j-1} beta_{j-1}, sw_j conj(alpha_j), delta_{j-1} sw_{j-1}
 };
 
 // Layout conversion canonical [nrhs][V][12] <-> native [nrhs][12][V]; element types by flag.

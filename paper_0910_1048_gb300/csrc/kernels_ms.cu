@@ -198,31 +198,32 @@ __global__ void __launch_bounds__(8 * kSplitSites) k_ms_pair_split(Geom g, Links
   const T* in1 = (const T*)(MODE == 0 ? v.pt : v.tt) + voff<R>(rhs, n);
   const R s1 = (R)(ms.sig1v ? ms.sig1v[rhs] : ms.sigma1);
   Red<R> acc[2];
-  pair_split<R, LF>(g, U, cp, cm, in0, in1, sm, [&](int which, int s, Spin<R>& o) {
+  // each thread finishes one spin (three colours) of its site: see pair_split
+  pair_split<R, LF>(g, U, cp, cm, in0, in1, sm, [&](int which, int s, int sp, cplx<R> (&o)[3]) {
     T* out = (T*)(MODE == 0 ? (which ? v.tt : v.t) : (which ? v.qt : v.q)) + voff<R>(rhs, n);
     const T* pp = (const T*)(which ? v.pt : v.p) + voff<R>(rhs, n);
     const T* ptl = (const T*)v.pt + voff<R>(rhs, n);
-    cplx<R> pv[12], tv[12];  // loads first (see k_ms_pair)
+    const R g5 = sp >= 2 ? (R)-1 : (R)1;
+    cplx<R> pv[3], tv[3];  // loads first (see k_ms_pair)
     if (MODE == 1) {
 #pragma unroll
-      for (int c = 0; c < 12; ++c) {
-        pv[c] = ldc<R>(pp, (size_t)c * g.vol + s);
-        tv[c] = which ? mk<R>(0, 0) : ldc<R>(ptl, (size_t)c * g.vol + s);
+      for (int a = 0; a < 3; ++a) {
+        pv[a] = ldc<R>(pp, (size_t)(sp * 3 + a) * g.vol + s);
+        tv[a] = which ? mk<R>(0, 0) : ldc<R>(ptl, (size_t)(sp * 3 + a) * g.vol + s);
       }
     }
-    cplx<R> a = mk<R>(0, 0);
 #pragma unroll
-    for (int c = 0; c < 12; ++c) {
-      cplx<R> x = o.c[c / 3][c % 3];
-      if (c >= 6) x = -x;  // gamma5
+    for (int a = 0; a < 3; ++a) {
+      cplx<R> x = g5 * o[a];
       if (MODE == 1) {
-        x = x - s1 * pv[c];
-        if (!which) a = a + cdot(tv[c], x);
+        x = x - s1 * pv[a];
+        if (!which) {
+          acc[0].dot2(tv[a].re, x.re, tv[a].im, x.im);
+          acc[1].dot2(tv[a].re, x.im, -tv[a].im, x.re);
+        }
       }
-      stc<R>(out, (size_t)c * g.vol + s, x);
+      stc<R>(out, (size_t)(sp * 3 + a) * g.vol + s, x);
     }
-    acc[0].add(a.re);
-    acc[1].add(a.im);
   });
   if (MODE == 0) return;
   double tot[2];

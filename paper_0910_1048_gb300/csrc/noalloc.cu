@@ -96,16 +96,17 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   OVL_REQUIRE(2.0 * p->m_W + 8.0 != 0.0, "apply_sign_noalloc: m_W = -4 has no kappa");
   const bool f64 = p->precision == OVL_PREC_F64;
   const int lf = p->precision == OVL_PREC_F32_F16LINKS ? LINK_F16R12 : (f64 ? LINK_F64 : LINK_F32);
-  OVL_REQUIRE(lat->u64 && (f64 || (lf == LINK_F32 ? lat->u32 != nullptr : lat->u16 != nullptr)),
+  OVL_REQUIRE(lat->src()->u64 && (f64 || (lf == LINK_F32 ? lat->src()->u32 != nullptr : lat->src()->u16 != nullptr)),
               "apply_sign_noalloc: links not set in the format this precision needs");
   int m = 0;
   if (p->use_deflation) {
-    OVL_REQUIRE(lat->defl.m > 0 && lat->defl.m_w == p->m_W && lat->defl.mu == p->mu,
+    OVL_REQUIRE(lat->src()->defl.m > 0 && lat->src()->defl.m_w == p->m_W && lat->src()->defl.mu == p->mu,
                 "apply_sign_noalloc: no deflation set for this (m_W, mu)");
-    m = lat->defl.m;
+    m = lat->src()->defl.m;
   }
   const int kmax = p->fixed_k > 0 ? p->fixed_k : p->k_max;
   OVL_REQUIRE(kmax >= 1, "apply_sign_noalloc: k_max must be >= 1");
+  std::shared_lock<std::shared_mutex> shared(lat->src()->guard);  // links / deflation set stay as they are
   OVL_DEVICE_SCOPE(lat->ctx->device);  // the caller's current device is restored on return
   cudaStream_t st = (cudaStream_t)stream;
   if (st) {  // the scratch address below is this device's: the stream must belong to it too
@@ -133,6 +134,7 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   size_t o_al = take((size_t)nrhs * ks * 16), o_be = take((size_t)nrhs * ks * 16);
   size_t o_de = take((size_t)nrhs * ks * 8), o_vn = take((size_t)nrhs * ks * 8), o_b0 = take((size_t)nrhs * 8);
   size_t o_pa = take((size_t)nrhs * std::max(m, 1) * nblk * 4 * 8), o_cn = take((size_t)nrhs * 4);
+  size_t o_uc = take((size_t)nrhs * 4 * 16);
   size_t o_do = take((size_t)nrhs * 2 * std::max(m, 1) * 16), o_ls = take((size_t)std::max(m, 1) * 8);
   size_t o_co = take((size_t)nrhs * kmax * 16), o_kr = take((size_t)nrhs * 4);
   // buffers of the stopping estimate (the same kernel and rule as ovl_apply_sign)
@@ -159,6 +161,7 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   lz.beta0 = (double*)(base + o_b0);
   lz.part = (double*)(base + o_pa);
   lz.count = (unsigned*)(base + o_cn);
+  lz.ucoef = (double2*)(base + o_uc);
   LzVecs vec;
   vec.vh = base + o_vh;
   vec.wh = base + o_wh;
@@ -178,11 +181,11 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   OVL_CHECK_CUDA(cudaMemsetAsync(lz.count, 0, (size_t)nrhs * 4, st));
   OVL_CHECK_CUDA(cudaMemsetAsync(ncount, 0, (size_t)nrhs * 4, st));
   std::vector<double> ls(std::max(m, 1));
-  for (int i = 0; i < m; ++i) ls[i] = lat->defl.lam[2 * i] >= 0 ? 1.0 : -1.0;
+  for (int i = 0; i < m; ++i) ls[i] = lat->src()->defl.lam[2 * i] >= 0 ? 1.0 : -1.0;
   if (m > 0) OVL_CHECK_CUDA(cudaMemcpyAsync(lam_sign, ls.data(), m * 8, cudaMemcpyHostToDevice, st));
-  OVL_CHECK_CUDA(launch_lanczos_start(g, f64, lz, vec, (const double2*)b, m, lat->defl.R, lat->defl.L, lam_sign,
+  OVL_CHECK_CUDA(launch_lanczos_start(g, f64, lz, vec, (const double2*)b, m, lat->src()->defl.R, lat->src()->defl.L, lam_sign,
                                       dots, st));
-  const Links U = lat->links();
+  const Links U = lat->src()->links();
   const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 20, kmax));
   const bool fixed = p->fixed_k > 0;
   // host copies of the scalars (pageable: the copies complete before the host reads them)

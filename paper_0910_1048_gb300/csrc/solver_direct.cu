@@ -134,6 +134,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   size_t o_b0 = take((size_t)nrhs * 8);
   size_t o_pa = take((size_t)nrhs * std::max(m, 1) * nblk * 4 * 8);
   size_t o_cn = take((size_t)nrhs * 4);
+  size_t o_uc = take((size_t)nrhs * 4 * 16);
   size_t o_do = take((size_t)nrhs * 2 * std::max(m, 1) * 16);
   size_t o_ls = take((size_t)std::max(m, 1) * 8);
   size_t o_co = take((size_t)nrhs * kmax * 16);
@@ -186,6 +187,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   lz.beta0 = (double*)(base + o_b0);
   lz.part = (double*)(base + o_pa);
   lz.count = (unsigned*)(base + o_cn);
+  lz.ucoef = (double2*)(base + o_uc);
   w->dots = (double2*)(base + o_do);
   w->lam_sign = (double*)(base + o_ls);
   w->coef = (double2*)(base + o_co);
@@ -349,15 +351,15 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   const bool f64 = p->precision == OVL_PREC_F64;
   const int lf = p->precision == OVL_PREC_F32_F16LINKS ? LINK_F16R12 : (f64 ? LINK_F64 : LINK_F32);
   OVL_REQUIRE(p->k_max >= 1 && p->k_max <= 100000, "apply_sign: k_max must be in [1, 100000]");
-  OVL_REQUIRE(lat->u64, "apply_sign: links not set");
-  OVL_REQUIRE(f64 || (lf == LINK_F32 ? lat->u32 != nullptr : lat->u16 != nullptr),
+  OVL_REQUIRE(lat->src()->u64, "apply_sign: links not set");
+  OVL_REQUIRE(f64 || (lf == LINK_F32 ? lat->src()->u32 != nullptr : lat->src()->u16 != nullptr),
               "apply_sign: links not set in the format this precision needs (ovl_set_links formats)");
   int m = 0;
   if (p->use_deflation) {
-    OVL_REQUIRE(lat->defl.m > 0, "apply_sign: use_deflation but no deflation set");
-    OVL_REQUIRE(lat->defl.m_w == p->m_W && lat->defl.mu == p->mu,
-                "apply_sign: deflation set was computed for (m_W, mu) = (%g, %g)", lat->defl.m_w, lat->defl.mu);
-    m = lat->defl.m;
+    OVL_REQUIRE(lat->src()->defl.m > 0, "apply_sign: use_deflation but no deflation set");
+    OVL_REQUIRE(lat->src()->defl.m_w == p->m_W && lat->src()->defl.mu == p->mu,
+                "apply_sign: deflation set was computed for (m_W, mu) = (%g, %g)", lat->src()->defl.m_w, lat->src()->defl.mu);
+    m = lat->src()->defl.m;
   }
   const int kmax = p->fixed_k > 0 ? p->fixed_k : p->k_max;
   OVL_TRY(ensure_ws(lat, nrhs, kmax, f64, m, p->priority));
@@ -376,14 +378,14 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   // start: deflation split and first vectors
   if (m > 0) {
     std::vector<double> ls(m);
-    for (int i = 0; i < m; ++i) ls[i] = lat->defl.lam[2 * i] >= 0 ? 1.0 : -1.0;
+    for (int i = 0; i < m; ++i) ls[i] = lat->src()->defl.lam[2 * i] >= 0 ? 1.0 : -1.0;
     OVL_CHECK_CUDA(cudaMemcpyAsync(w->lam_sign, ls.data(), m * 8, cudaMemcpyHostToDevice, st));
   }
   LzVecs vec = w->vec;
   if (m == 0) vec.xp = nullptr;
-  OVL_CHECK_CUDA(launch_lanczos_start(g, f64, w->lz, vec, bd, m, lat->defl.R, lat->defl.L, w->lam_sign, w->dots, st));
-  const Links U = lat->links();
-  // autotuner: on first use of (volume, precision) time both pair-stencil variants on this
+  OVL_CHECK_CUDA(launch_lanczos_start(g, f64, w->lz, vec, bd, m, lat->src()->defl.R, lat->src()->defl.L, w->lam_sign, w->dots, st));
+  const Links U = lat->src()->links();
+  // autotuner: on first use of (volume, precision) time every pair-stencil variant on this
   // solve's step-1 data (the real step-1 launch below recomputes everything they write)
   struct TuneArg {
     const Geom* g;
@@ -397,7 +399,8 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   } targ{&g, &U, lf, f64, p, &w->lz, &vec, st};
   auto measure = [](void* v) -> int {
     TuneArg& t = *(TuneArg*)v;
-    float best[2] = {1e30f, 1e30f};
+    float best[kPairVariants];
+    for (float& b : best) b = 1e30f;
     cudaEvent_t a, b2;
     if (cudaEventCreate(&a) != cudaSuccess) return -1;
     if (cudaEventCreate(&b2) != cudaSuccess) {
@@ -406,7 +409,7 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
     }
     bool ok = true;
     for (int rep = 0; rep < 4 && ok; ++rep)
-      for (int var = 0; var < 2 && ok; ++var) {
+      for (int var = 0; var < kPairVariants && ok; ++var) {
         ok = cudaEventRecord(a, t.st) == cudaSuccess &&
              launch_lanczos_pair(*t.g, *t.U, t.lf, t.f64, t.p->m_W, t.p->mu, *t.lz, *t.vec, t.st, var) ==
                  cudaSuccess &&
@@ -417,7 +420,10 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
     cudaEventDestroy(a);
     cudaEventDestroy(b2);
     cudaGetLastError();
-    return ok ? (best[1] < best[0] ? 1 : 0) : -1;
+    int pick = 0;
+    for (int var = 1; var < kPairVariants; ++var)
+      if (best[var] < best[pick]) pick = var;
+    return ok ? pick : -1;
   };
   tune_pair_variant(g.vol, f64 ? 0 : lf, measure, &targ);
   const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 20, kmax));
