@@ -6,13 +6,15 @@ iteration, sign of the projected matrix, combine), inputs resident in HBM. L2 is
 (a 256 MB write) between timed steps. `e2e` repeats the steps through the same call with
 host buffers (copies inside the timed region). `roofline` reports the dominant kernel (the
 fused pair stencil) from CUDA events recorded around its launches inside the library.
-`--impl reference` times the oracle (plain FP64 CPU restatement of Algorithm 4) on the
-host cores on a bounded sample of the same workload.
+The default workload is 12^4, mu = 0.3, plain FP64 two-sided Lanczos (Algorithm 4) to 1e-8.
 
-Beside the headline the line carries `mixed_precision` (the workload's mixed-precision companion,
-e.g. the FP32 multishift with FP64 reliable updates at the same 1e-8, and its speedup over the
-line's value), `dslash` (kernel-only stencil bandwidth on 32^4) and `serving` (a bounded sample of
-the serving stream: p50/p99 latency, solves/s, success rate); `--no-extras` skips them.
+Beside the headline the line carries its companions (COMPANIONS: the same problem by the
+multishift BiCG with FP32 or FP16 12-real links under FP64 reliable updates, with their speedup
+over the line's value, and the 16-source 16^4 batch), `lattice8_defl16` (8^4 with 16 deflated
+eigenpairs: error at k = 600 and the k reaching 1e-10), `dslash` (kernel-only stencil bandwidth on
+32^4) and `serving` (a bounded sample of the serving stream: p50/p99 latency, solves/s, success
+rate); `--no-extras` skips them. `cpu_baseline` and `--impl reference` time the oracle (the plain C
+FP64 two-sided Lanczos with numpy's eigendecomposition of H_k) on the host cores at the GPU's k.
 
 Multi-GPU: replicas only (each rank solves its own copies, no collective on the data path);
 value = solves of all ranks / max over ranks of the timed region.
@@ -44,8 +46,7 @@ WORKLOADS = {
     # k <= 600 does not reach 1e-8 at mu = 0.3 with 16 deflated vectors on this ensemble, so
     # k_max is 2000 and the k actually used is reported.
     "lattice8_mu0-0.1-0.3_defl16_direct_f64": dict(dims=(8, 8, 8, 8), mus=(0.0, 0.1, 0.3), m=16, method="direct",
-                                                     precision="f64", tol=1e-8, k_max=2000,
-                                                     mixed="lattice8_mu0-0.1-0.3_defl16_multishift_f32_f64rel"),
+                                                     precision="f64", tol=1e-8, k_max=2000),
     # same lattice and deflation, rational variant (Algorithm 3 + Neuberger, Eq. no_of_poles)
     "lattice8_mu0-0.1-0.3_defl16_multishift_f64": dict(dims=(8, 8, 8, 8), mus=(0.0, 0.1, 0.3), m=16,
                                                          method="multishift", precision="f64", tol=1e-8,
@@ -70,12 +71,11 @@ WORKLOADS = {
     # the plain FP64 two-sided Lanczos path on the same 12^4 problem at 1e-8, with the mixed-precision
     # multishift line above as its companion (speedup reported in the line)
     "lattice12_mu0.3_direct_f64": dict(dims=(12, 12, 12, 12), mus=(0.3,), m=0, method="direct", precision="f64",
-                                       tol=1e-8, k_max=3000, mixed="lattice12_mu0.3_multishift_zolo20_f32_f64rel"),
+                                       tol=1e-8, k_max=3000),
     # 16^4, mu = 0.2 at 1e-8: FP64 direct on batches of 4 sources (16 sources at this k do not fit in
     # HBM: the basis is nrhs x k x 12.6 MB) against the mixed-precision multishift on all 16 at once
     "lattice16_mu0.2_nrhs4_direct_f64": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0, method="direct",
-                                             precision="f64", tol=1e-8, k_max=2500, nrhs=4,
-                                             mixed="lattice16_mu0.2_nrhs16_multishift_f32_f64rel"),
+                                             precision="f64", tol=1e-8, k_max=2500, nrhs=4),
     "lattice16_mu0.2_nrhs16_multishift_f16links_f64rel": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0,
                                                                method="multishift", precision="f16", tol=1e-8,
                                                                k_max=8000, rational="zolotarev", s=20, nrhs=16),
@@ -95,6 +95,34 @@ WORKLOADS = {
                                       tol=1e-8, k_max=1200),
 }
 DEFAULT_WORKLOAD = "lattice12_mu0.3_direct_f64"
+
+# Lines carried beside a headline workload in the same JSON object (same GPU, same run): the
+# mixed-precision companions of the same problem at the same tolerance (their speedup over the
+# headline's plain FP64 two-sided Lanczos value is reported), and the 16-source batch.
+COMPANIONS = {
+    "lattice12_mu0.3_direct_f64": [
+        ("mixed_precision", "lattice12_mu0.3_multishift_zolo20_f32_f64rel"),
+        ("mixed_precision_f16links", "lattice12_mu0.3_multishift_zolo20_f16links_f64rel"),
+        ("lattice16_nrhs16_mixed", "lattice16_mu0.2_nrhs16_multishift_f32_f64rel"),
+        ("lattice16_nrhs16_direct_f32", "lattice16_mu0.2_nrhs16_direct_f32"),
+    ],
+    "lattice8_mu0-0.1-0.3_defl16_direct_f64": [
+        ("mixed_precision", "lattice8_mu0-0.1-0.3_defl16_multishift_f32_f64rel")],
+    "lattice16_mu0.2_nrhs4_direct_f64": [("mixed_precision", "lattice16_mu0.2_nrhs16_multishift_f32_f64rel")],
+}
+
+# Krylov dimension k the GPU's FP64 direct solve reaches on each workload and mu (seed-0 links,
+# seed-1000 source), measured on a GB300. The reference arm runs the oracle for exactly these k
+# (the same amount of Lanczos work); the GPU arm reports its own k beside them.
+K_TABLE = {
+    "lattice12_mu0.3_direct_f64": {0.3: 1250},
+    "lattice8_mu0-0.1-0.3_defl16_direct_f64": {0.0: 450, 0.1: 550, 0.3: 900},
+    "lattice4_mu0.3_direct_f64": {0.3: 1000},
+}
+
+# The 8^4 configuration with 16 deflated critical eigenpairs per mu: the error attained at a fixed
+# k = 600 and the k that reaches 1e-10 (FP64 direct method).
+C2 = dict(workload="lattice8_mu0-0.1-0.3_defl16_direct_f64", k_fixed=600, tol=1e-10, k_max=3000)
 
 # Algorithmic traffic / work of one launch of the fused pair stencil per site: per right-hand
 # side two spinors in (neighbours read once each: 2 x 24 reals) and two out; the 4 links of a site
@@ -301,10 +329,14 @@ def _sources(wl):
     return synth.gaussian_source(wl["dims"], 1000, nrhs=nrhs if nrhs > 1 else None)
 
 
-def _time_workload(ovl, ctx, args, wl, u, per_mu, b, flush, world, clocks=None):
-    """Warm-up, then `args.steps` timed steps of one workload. A step = one ovl_apply_sign per
-    mu (each with all of the workload's right-hand sides), run concurrently from host threads."""
+def _time_workload(ovl, ctx, args, wl, u, per_mu, b, flush, world, steps=None, warmup=None):
+    """Warm-up, then `steps` (default args.steps) timed steps of one workload. A step = one
+    ovl_apply_sign per mu (each with all of the workload's right-hand sides), run concurrently from
+    host threads."""
     import torch
+
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
 
     lats = []
     for d in per_mu:
@@ -333,9 +365,9 @@ def _time_workload(ovl, ctx, args, wl, u, per_mu, b, flush, world, clocks=None):
             return [one(i, host, bh) for i in range(len(per_mu))]
         return list(pool.map(lambda i: one(i, host, bh), range(len(per_mu))))
 
-    for w in range(args.warmup):
+    for w in range(warmup):
         res = step()
-        if w == 0 and pool is not None and args.warmup >= 2:
+        if w == 0 and pool is not None and warmup >= 2:
             # concurrent solves: the one needing the most iterations gets the most urgent streams,
             # so it runs near its alone speed while the others fill the idle SMs (ranked on the
             # first warm-up step; the remaining warm-up steps run with the final priorities)
@@ -347,7 +379,7 @@ def _time_workload(ovl, ctx, args, wl, u, per_mu, b, flush, world, clocks=None):
         torch.distributed.barrier()
     times, infos = [], []
     stream = torch.cuda.current_stream()
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -364,7 +396,7 @@ def _time_workload(ovl, ctx, args, wl, u, per_mu, b, flush, world, clocks=None):
     bh = torch.from_numpy(b).pin_memory().numpy()
     step(True, bh)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step(True, bh)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
     # accuracy actually reached: the paper's measure 0.5 |sign(A)^2 b - b| / |b| (Section 6),
@@ -417,7 +449,46 @@ def _dslash_gbs(ovl, ctx, u_fn, L=32, reps=20):
         out[name] = {"lattice": "%d^4" % L, "us_per_launch": t * 1e3, "algorithmic_bytes_per_site": per_site,
                      "achieved_gbs": per_site * vol / (t * 1e-3) / 1e9}
     ovl.ovl_destroy_lattice(lat)
+    out.update(_dslash_batch_gbs(ovl, ctx, u_fn, reps=max(3, reps // 4)))
     return out
+
+
+def _dslash_batch_gbs(ovl, ctx, u_fn, L=24, nrhs=16, reps=5):
+    """FP32 stencil on a batch of `nrhs` sources on an L^4 lattice (native layout): one launch over
+    the batch (links loaded once per site for each group of sources) against `nrhs` single-source
+    launches. Algorithmic bytes per launch: the links once (288 B per site) plus 192 B per site and
+    source (spinor in and out)."""
+    import torch
+
+    dims = (L, L, L, L)
+    vol = L ** 4
+    lat = ovl.ovl_create_lattice(ctx, dims, -1)
+    ovl.ovl_set_links(lat, u_fn(dims), ovl.OVL_F32)
+    x = torch.randn(nrhs * 12 * vol, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    flags = ovl.OVL_LINKS_F32 | ovl.OVL_NATIVE | ovl.OVL_GAMMA5
+    byts = vol * (288 + nrhs * 192)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, run in (("f32_batch%d" % nrhs, lambda: ovl.ovl_apply_DW(lat, -2.0, 0.3, flags, x, y)),
+                      ("f32_batch%d_one_by_one" % nrhs,
+                       lambda: [ovl.ovl_apply_DW(lat, -2.0, 0.3, flags, x[r * 12 * vol:(r + 1) * 12 * vol],
+                                                 y[r * 12 * vol:(r + 1) * 12 * vol]) for r in range(nrhs)])):
+        for _ in range(2):
+            run()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run()
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        res[name] = {"lattice": "%d^4" % L, "nrhs": nrhs, "us_per_batch": t * 1e3,
+                     "algorithmic_bytes_per_batch": byts, "achieved_gbs": byts / (t * 1e-3) / 1e9}
+    ovl.ovl_destroy_lattice(lat)
+    return res
 
 
 def _roofline(wl, infos, fp64_peak, fp64_src):
@@ -461,6 +532,57 @@ def _summary(wl, per_mu, infos, acc):
     statuses = sorted({st for step in infos for st, _ in step})
     launches = sum(inf[0]["kernel_launches"] for step in infos for _, inf in step)
     return its, per_mu_stats, statuses, launches
+
+
+def _companion(ovl, ctx, args, cname, flush, world, local, fp64_peak, fp64_src, ref_value):
+    """One companion workload, timed like the headline with at most 3 warm-up and 3 timed steps."""
+    wm = WORKLOADS[cname]
+    lat_m, u_m, _, pm = _setup(ovl, ctx, wm, cache=args.setup_cache)
+    ovl.ovl_destroy_lattice(lat_m)
+    bm = _sources(wm)
+    sps = len(pm) * wm.get("nrhs", 1)
+    steps, warm = min(args.steps, 3), min(args.warmup, 3)
+    with ClockSampler(local) as clk:
+        tm, em, im, am = _time_workload(ovl, ctx, args, wm, u_m, pm, bm, flush, world, steps=steps, warmup=warm)
+    vm = throughput(steps, sps, world, tm)
+    _, pms, stm, lm = _summary(wm, pm, im, am)
+    return {"workload": cname, "lattice": "x".join(map(str, wm["dims"])), "method": wm["method"],
+            "precision": wm["precision"], "rational": wm.get("rational", "neuberger"), "poles": wm.get("s"),
+            "tol": wm["tol"], "nrhs": wm.get("nrhs", 1), "value": vm, "unit": UNIT, "steps": steps, "warmup": warm,
+            "ms_per_step": tm / steps, "speedup_vs_line_value": vm / ref_value,
+            "e2e_value": steps * sps * world / em, "statuses": stm, "accuracy_half_sign2b_minus_b": am,
+            "per_mu": pms, "gpu_launches": int(lm), "roofline": _roofline(wm, im, fp64_peak, fp64_src),
+            "clocks": clk.summary()}
+
+
+def _c2_line(ovl, ctx, args):
+    """8^4, mu in {0, 0.1, 0.3}, 16 deflated critical eigenpairs per mu, FP64 direct: the error
+    reached at k = 600 (the paper's measure 0.5 |sign(A)^2 b - b| / |b|, both solves at k = 600) and
+    the k that reaches 1e-10 (with the same measure for that solve)."""
+    import torch
+
+    wl = WORKLOADS[C2["workload"]]
+    lat, u, b, per_mu = _setup(ovl, ctx, wl, cache=args.setup_cache)
+    bt = torch.from_numpy(b).cuda()
+    out = []
+    for d in per_mu:
+        ovl.ovl_set_deflation(lat, -2.0, d["mu"], d["R"], d["L"], d["lam"])
+        row = {"mu": d["mu"], "deflated": wl["m"], "gap": d["gap"]}
+        for tag, kw in (("fixed_k600", dict(fixed_k=C2["k_fixed"])),
+                        ("tol1e-10", dict(tol=C2["tol"], k_max=C2["k_max"]))):
+            p = ovl.ovl_sign_params_default(mu=d["mu"], use_deflation=1, check_every=25, **kw)
+            x1, x2 = torch.empty_like(bt), torch.empty_like(bt)
+            t0 = time.perf_counter()
+            st1, i1 = ovl.ovl_apply_sign(lat, p, bt, x1)
+            t1 = time.perf_counter()
+            ovl.ovl_apply_sign(lat, p, x1, x2)
+            err = float(0.5 * torch.linalg.vector_norm(x2 - bt) / torch.linalg.vector_norm(bt))
+            row[tag] = {"k": i1[0]["iterations"], "status": st1, "accuracy_half_sign2b_minus_b": err,
+                        "t_solve_ms": 1e3 * (t1 - t0)}
+        out.append(row)
+    ovl.ovl_destroy_lattice(lat)
+    return {"workload": C2["workload"], "method": "direct", "precision": "f64", "per_mu": out,
+            "note": "attained error at fixed k = 600 and the k reaching 1e-10 (16 deflated eigenpairs)"}
 
 
 def run_ours(args, wl):
@@ -511,25 +633,17 @@ def run_ours(args, wl):
         "roofline": _roofline(wl, infos, fp64_peak, fp64_src), "e2e": e2e, "clocks": clocks,
         "gpu_launches": int(launches),
     }
-    # the same step in mixed precision (FP32 vectors and links, FP64 reliable
-    # updates), at the same accuracy, and its speedup over this line's value
-    mixed = wl.get("mixed")
-    if mixed and not args.no_extras:
-        wm = WORKLOADS[mixed]
-        lat_m, _, _, pm = _setup(ovl, ctx, wm, cache=args.setup_cache)
-        ovl.ovl_destroy_lattice(lat_m)
-        bm = _sources(wm)  # the companion's own batch (it may hold more right-hand sides)
-        sps_m = len(pm) * wm.get("nrhs", 1)
-        with ClockSampler(local) as clk2:
-            tm, em, im, am = _time_workload(ovl, ctx, args, wm, u, pm, bm, flush, world)
-        vm = throughput(args.steps, sps_m, world, tm)
-        _, pms, stm, lm = _summary(wm, pm, im, am)
-        res["mixed_precision"] = {
-            "workload": mixed, "method": wm["method"], "precision": wm["precision"], "tol": wm["tol"],
-            "nrhs": wm.get("nrhs", 1), "value": vm, "unit": UNIT, "ms_per_step": tm / args.steps,
-            "speedup_vs_line_value": vm / value, "e2e_value": args.steps * sps_m * world / em, "statuses": stm,
-            "accuracy_half_sign2b_minus_b": am, "per_mu": pms, "gpu_launches": int(lm),
-            "roofline": _roofline(wm, im, fp64_peak, fp64_src), "clocks": clk2.summary()}
+    # companion lines: the same problem in mixed precision (speedup over this line's value), the
+    # 16-source batch; each timed with at most 3 warm-up and 3 timed steps
+    if not args.no_extras:
+        for key, cname in COMPANIONS.get(args.workload, []):
+            res[key] = _companion(ovl, ctx, args, cname, flush, world, local, fp64_peak, fp64_src, value)
+        if args.workload == DEFAULT_WORKLOAD:
+            res["lattice8_defl16"] = _c2_line(ovl, ctx, args)
+    k_table = K_TABLE.get(args.workload)
+    if k_table:
+        res["config"]["k_table"] = {"%g" % m: {"gpu": s_["k"], "table": k_table.get(m)} for m, s_ in
+                                    zip(wl["mus"], per_mu_stats)}
     if not args.no_extras:
         res["dslash"] = _dslash_gbs(ovl, ctx, lambda d: synth.gauge_links(d, 0))
         if args.serving_requests > 0:
@@ -538,7 +652,7 @@ def run_ours(args, wl):
         for v in res["dslash"].values():
             v["frac_of_measured_hbm"] = v["achieved_gbs"] / pk["hbm_gbs"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(wl, its, seconds=args.cpu_seconds)
+        res["cpu_baseline"] = cpu_baseline(wl, args.workload, its, seconds=args.cpu_seconds)
     ovl.ovl_destroy_lattice(lat)
     ovl.ovl_ctx_destroy(ctx)
     if rank == 0:
@@ -619,75 +733,156 @@ def serving_sample(ovl, ctx, n_requests, mem_budget=200 << 30, max_slots=8):
             "k_max_cap": {"%d^4" % k: v for k, v in cfg["k_max_cap"].items()}}
 
 
-def _oracle_sample(wl, iterations, seconds):
-    """Time the oracle's Algorithm 4 (scipy sparse FP64 matvecs, numpy eig for sign(H_k))
-    on the bench workload for a bounded number of Lanczos steps; extrapolate to the
-    iterations the GPU path needed. Returns (solves/s, sample description)."""
+def _oracle_inputs(wl, mu):
+    """Links, the first source and (with deflation) the critical eigenpairs for the oracle legs."""
     import synth
-    from oracle import deflation, lanczos
+    from oracle import deflation
 
     dims = wl["dims"]
     u = synth.gauge_links(dims, 0)
-    b = synth.gaussian_source(dims, 1000).ravel()
-    mu = wl["mus"][-1]
-    a = deflation.sparse_hw(u, dims, -2.0, mu)
-    ah = deflation.sparse_hw(u, dims, -2.0, -mu)
-    k_full = int(np.mean(iterations)) if len(iterations) else wl["k_max"]
-    # bounded sample: as many Lanczos steps as fit in the time budget
+    b = synth.gaussian_source(dims, 1000, nrhs=wl.get("nrhs", 1) if wl.get("nrhs", 1) > 1 else None)
+    b0 = b[0] if wl.get("nrhs", 1) > 1 else b
+    R = L = lam = None
+    if wl["m"] > 0:
+        lam, R, L, _ = deflation.critical_sparse(u, dims, -2.0, mu, wl["m"])
+    return u, b0, R, L, lam
+
+
+def _oracle_solve(wl, mu, k, seconds):
+    """Time one oracle solve (the C FP64 two-sided Lanczos of Algorithm 4, exactly k steps, then
+    numpy's eigendecomposition for sign(H_k) e_1 and the combine) at mu on the workload's first
+    source. The whole solve runs when its estimate (from the first 10 steps) fits `seconds`;
+    otherwise as many steps as fit are timed and the steps and the k^3 eigendecomposition are
+    extrapolated to k. Returns (seconds per solve, description)."""
+    from oracle import krylov, lanczos
+
+    u, b0, R, L, lam = _oracle_inputs(wl, mu)
+    dims = wl["dims"]
+    s = krylov.DirectSolve(u, dims, -2.0, mu, b0, k, R=R, L=L, lam=lam)
     t0 = time.perf_counter()
-    ksamp = 0
-    st = None
-    kk = 10
-    while True:
-        t1 = time.perf_counter()
-        st = lanczos.two_sided_lanczos(lambda v: a @ v, lambda w: ah @ w, b, b, kk)
-        ksamp = kk
-        if time.perf_counter() - t0 > 0.5 * seconds or kk >= k_full:
-            break
-        kk = min(k_full, kk * 2)
-    t_steps = time.perf_counter() - t1
-    per_step = t_steps / ksamp
-    # dense sign of the projected matrix at the full k (numpy eig), timed once
-    ks = min(k_full, ksamp)
-    t2 = time.perf_counter()
-    lanczos.sign_tridiag_e1(st["alpha"][:ks], st["beta"][:ks - 1], st["delta"][:ks - 1])
-    t_small = (time.perf_counter() - t2) * (k_full / ks) ** 3
-    solve_s = per_step * k_full + t_small
-    desc = ("oracle two-sided Lanczos (Algorithm 4, scipy CSR FP64 matvecs) at %s mu=%g: %d steps timed "
-            "(%.2f s), extrapolated to k=%d, plus numpy eig of H_k scaled as k^3"
-            % ("x".join(map(str, dims)), mu, ksamp, t_steps, k_full))
-    return 1.0 / solve_s, desc
+    s.start()
+    s.steps(10)
+    per_step = (time.perf_counter() - t0) / 10
+    lat = "x".join(map(str, dims))
+    if per_step * k * 1.2 <= seconds:
+        s.steps(k - s.k)
+        s.finish()
+        total = time.perf_counter() - t0
+        return total, ("one full oracle solve at %s mu=%g: C two-sided Lanczos, k=%d steps (%s), numpy eig "
+                       "sign(H_k) e_1, combine" % (lat, mu, s.k, "deflated %d" % wl["m"] if wl["m"] else "no deflation"))
+    budget = max(10, int(0.7 * seconds / per_step))
+    s.steps(budget - s.k)
+    t_steps = time.perf_counter() - t0
+    kk = s.k
+    t1 = time.perf_counter()
+    lanczos.sign_tridiag_e1(s.alpha[:kk], s.beta[:kk - 1], s.delta[:kk - 1])
+    t_eig = (time.perf_counter() - t1) * (k / kk) ** 3
+    total = t_steps / kk * k + t_eig
+    return total, ("oracle at %s mu=%g: %d of k=%d C two-sided Lanczos steps timed (%.1f s), extrapolated, "
+                   "plus numpy eig of H_k scaled as k^3" % (lat, mu, kk, k, t_steps))
 
 
-def cpu_baseline(wl, iterations, seconds=20.0):
-    env_threads = os.environ.get("OMP_NUM_THREADS")
-    v, desc = _oracle_sample(wl, iterations, seconds)
-    return {"value": v, "unit": UNIT, "cores": int(env_threads) if env_threads else os.cpu_count(),
-            "kind": "oracle", "sample": desc}
+def cpu_baseline(wl, workload, iterations, seconds=20.0):
+    """The oracle on this host's cores, one solve of the workload's hardest mu at the k the GPU
+    needed (bounded: see _oracle_solve)."""
+    from oracle import krylov
+
+    mu = wl["mus"][-1]
+    k = int(round(float(np.mean(iterations)))) if len(iterations) else K_TABLE.get(workload, {}).get(mu, wl["k_max"])
+    t, desc = _oracle_solve(wl, mu, k, seconds)
+    return {"value": 1.0 / t, "unit": UNIT, "cores": krylov.threads(), "kind": "oracle", "sample": desc}
 
 
 def run_reference(args, wl):
+    """The oracle (plain C FP64 two-sided Lanczos, Algorithm 4, with numpy's eigendecomposition of
+    H_k) on this host's cores, for the workload's mu set, deflation and the per-mu k of K_TABLE (the
+    GPU's). The K timed steps are pieces of one full solve per mu: each advances every solve by
+    k/K Lanczos steps, the last one also evaluates sign(H_k) e_1 and combines. A multi-source
+    workload times its first source and counts it as nrhs solves (the sources are independent)."""
     rank, world, _ = _dist()
     if rank != 0:
         return
-    vals = []
-    desc = ""
-    its = [wl["k_max"]]
-    for _ in range(args.warmup + args.steps):
-        v, desc = _oracle_sample(wl, its, seconds=max(2.0, args.cpu_seconds / max(1, args.steps)))
-        vals.append(v)
-    vals = vals[args.warmup:]
-    value = float(np.mean(vals))
-    threads = os.environ.get("OMP_NUM_THREADS")
+    from oracle import krylov
+
+    ktab = K_TABLE.get(args.workload, {})
+    nrhs = wl.get("nrhs", 1)
+    solves = []
+    for mu in wl["mus"]:
+        u, b0, R, L, lam = _oracle_inputs(wl, mu)
+        solves.append(krylov.DirectSolve(u, wl["dims"], -2.0, mu, b0, int(ktab.get(mu, wl["k_max"])), R=R, L=L,
+                                         lam=lam))
+    warm = krylov.DirectSolve(u, wl["dims"], -2.0, wl["mus"][0], b0, args.warmup + 1).start()
+    for _ in range(args.warmup):
+        warm.steps(1)
+    del warm
+    K = max(1, args.steps)
+    times = []
+    for i in range(K):
+        t0 = time.perf_counter()
+        for sv in solves:
+            if i == 0:
+                sv.start()
+            sv.steps(-(-sv.kcap // K))
+            if i == K - 1:
+                sv.steps(sv.kcap - sv.k)
+                sv.finish()
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = len(solves) * nrhs / total
+    ks = {"%g" % sv.mu: sv.k for sv in solves}
+    desc = ("one full oracle solve per mu at %s (k per mu %s from the GPU's runs%s), split over the %d timed "
+            "steps" % ("x".join(map(str, wl["dims"])), ks, ", 16 deflated" if wl["m"] else "", K))
+    if nrhs > 1:
+        desc += "; first of %d sources timed, counted %d times" % (nrhs, nrhs)
+    cores = krylov.threads()
     res = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": args.workload},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(threads) if threads else os.cpu_count(),
-                         "kind": "oracle", "sample": desc},
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic: SU(3) links exp(0.5 i H) seed 0, Gaussian b seed 1000",
+        "config": {"workload": args.workload, "lattice": "x".join(map(str, wl["dims"])), "mu": list(wl["mus"]),
+                   "deflated": wl["m"], "method": "direct", "precision": "f64", "tol": wl["tol"], "k_per_mu": ks},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(res))
+
+
+def run_profile_case(args):
+    """A small, fixed amount of work for an Nsight Compute capture (a few hundred MB on the device,
+    a bounded number of launches): one fixed-k direct solve (`direct`), one fixed-iteration
+    multishift solve (`multishift`) or three stencil launches per link format (`dslash`) on an L^4
+    lattice with the seed-0 links. Prints nothing to compare; the capture is the product."""
+    import torch
+
+    import paper_0910_1048_gb300 as ovl
+    import synth
+
+    L = args.lattice
+    dims = (L, L, L, L)
+    ctx = ovl.ovl_ctx_create(0)
+    lat = ovl.ovl_create_lattice(ctx, dims, -1)
+    ovl.ovl_set_links(lat, synth.gauge_links(dims, 0), ovl.OVL_F64 | ovl.OVL_F32 | ovl.OVL_F16R12)
+    prec = {"f64": ovl.OVL_PREC_F64, "f32": ovl.OVL_PREC_F32, "f16": ovl.OVL_PREC_F32_F16LINKS}[args.prec]
+    if args.profile_case == "dslash":
+        dt = torch.complex128 if args.prec == "f64" else torch.complex64
+        x = torch.randn(args.nrhs * 12 * L ** 4, dtype=dt, device="cuda")
+        y = torch.empty_like(x)
+        fl = {"f64": 0, "f32": ovl.OVL_LINKS_F32, "f16": ovl.OVL_LINKS_F16R12}[args.prec]
+        for _ in range(3):
+            ovl.ovl_apply_DW(lat, -2.0, 0.3, fl | ovl.OVL_NATIVE | ovl.OVL_GAMMA5, x, y)
+    else:
+        b = torch.from_numpy(synth.gaussian_source(dims, 1000, nrhs=args.nrhs if args.nrhs > 1 else None)).cuda()
+        x = torch.empty_like(b)
+        if args.profile_case == "direct":
+            p = ovl.ovl_sign_params_default(mu=0.3, precision=prec, fixed_k=args.fixed_k, check_every=20)
+        else:
+            p = ovl.ovl_sign_params_default(mu=0.3, precision=prec, method=ovl.OVL_MULTISHIFT_BICG,
+                                            rational_kind=ovl.OVL_RAT_ZOLOTAREV, s=20, spec_lo=0.05, spec_hi=2.7,
+                                            tol=1e-3, k_max=args.fixed_k)
+        ovl.ovl_apply_sign(lat, p, b, x)
+    torch.cuda.synchronize()
+    ovl.ovl_destroy_lattice(lat)
+    ovl.ovl_ctx_destroy(ctx)
 
 
 def main():
@@ -707,7 +902,16 @@ def main():
                     help="run the step's independent solves concurrently (1) or one after another (0)")
     ap.add_argument("--setup-cache", default=None,
                     help=".npz file holding the untimed spectral set-up (created if missing)")
+    ap.add_argument("--profile-case", choices=["direct", "multishift", "dslash"], default=None,
+                    help="run one small fixed case for a profiler capture instead of the benchmark")
+    ap.add_argument("--lattice", type=int, default=8, help="--profile-case: extent L of the L^4 lattice")
+    ap.add_argument("--prec", choices=["f64", "f32", "f16"], default="f64", help="--profile-case: precision")
+    ap.add_argument("--nrhs", type=int, default=1, help="--profile-case: right-hand sides")
+    ap.add_argument("--fixed-k", type=int, default=40, help="--profile-case: Lanczos steps / BiCG iterations")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)

@@ -98,14 +98,15 @@ int64_t ovl_lattice_n(const ovl_lattice* lat);
 /* Copy links U (canonical complex128 layout, host or device memory per U_on_device)
  * into library-owned device copies in each format of the `formats` bit set (OVL_F64 is
  * always kept). The caller's buffer may be freed on return (the call synchronises).
- * Errors: EINVAL, ENOMEM, ECUDA. */
+ * Errors: EINVAL, EBUSY (a solve is reading the links), ENOMEM, ECUDA. */
 ovl_status ovl_set_links(ovl_lattice* lat, const void* U, int32_t U_on_device, uint32_t formats);
 
 /* LR deflation set (Section 3): m critical eigenpairs of A = H_W(m_W, mu):
  * R = right eigenvectors, L = left eigenvectors, each [m][n] canonical complex128,
  * lambda[m] complex128 eigenvalues; A R = R Lambda, L^H A = Lambda L^H, L^H R = I.
  * Copied to the device; valid for solves with the same (m_W, mu). m = 0 clears.
- * Errors: EINVAL (m < 0, max |L^H R - I| > 1e-8, NULL), ENOMEM, ECUDA. */
+ * Errors: EINVAL (m < 0, max |L^H R - I| > 1e-8, NULL), EBUSY (a solve is reading the set),
+ * ENOMEM, ECUDA. */
 ovl_status ovl_set_deflation(ovl_lattice* lat, double m_W, double mu, int32_t m,
                              const void* R, const void* L, const void* lambda, int32_t on_device);
 
@@ -126,12 +127,13 @@ ovl_status ovl_apply_DW(ovl_lattice* lat, double m_W, double mu, uint32_t flags,
 
 /* ----------------------------------------------------------------- sign solves */
 
-enum { OVL_DIRECT_2SL = 0, OVL_MULTISHIFT_BICG = 1 };
+enum { OVL_DIRECT_2SL = 0, OVL_MULTISHIFT_BICG = 1, OVL_FOM_RESTARTED = 2 };
 enum { OVL_PREC_F64 = 0, OVL_PREC_F32 = 1, OVL_PREC_F32_F16LINKS = 2 };
 enum { OVL_RAT_NEUBERGER = 0, OVL_RAT_ZOLOTAREV = 1, OVL_RAT_CUSTOM = 2 };
 
 typedef struct {
-  int32_t method;         /* OVL_DIRECT_2SL (Algorithm 4) | OVL_MULTISHIFT_BICG (Algorithm 3) */
+  int32_t method;         /* OVL_DIRECT_2SL (Algorithm 4) | OVL_MULTISHIFT_BICG (Algorithm 3) |
+                             OVL_FOM_RESTARTED (Algorithm 1: restarted FOM-LR on A^2) */
   int32_t precision;      /* OVL_PREC_*: vector/stencil precision; scalars always FP64 */
   double m_W;             /* Wilson mass (kappa = 1/(2 m_W + 8)) */
   double mu;              /* chemical potential */
@@ -151,6 +153,7 @@ typedef struct {
   int32_t priority;       /* CUDA stream priority of the solve, 0 default, p > 0 p levels more
                              urgent (clamped to the device's range); lets concurrent solves favour
                              the longest one. No effect on results. */
+  int32_t restart_k;      /* restarted FOM: Arnoldi steps per cycle k (default 40, at most 64) */
 } ovl_sign_params;
 
 typedef struct {
@@ -173,7 +176,7 @@ typedef struct {
 } ovl_sign_info;
 
 /* Fill p with defaults: DIRECT_2SL, F64, m_W = -2, mu = 0, tol = 1e-10, k_max = 600,
- * check_every = 20, no deflation, Neuberger, s = 0, use_graphs = 1. */
+ * check_every = 20, no deflation, Neuberger, s = 0, use_graphs = 1, restart_k = 40. */
 void ovl_sign_params_default(ovl_sign_params* p);
 
 /* x = sign(H_W(m_W, mu)) b for nrhs right-hand sides b[nrhs][n] (canonical complex128),
@@ -181,8 +184,10 @@ void ovl_sign_params_default(ovl_sign_params* p);
  * results (may be NULL). The call returns when x is written (it synchronises `stream`).
  * Returns OVL_OK if every rhs reached tol, else the first non-OK per-rhs status
  * (ENOCONV / EBREAKDOWN still write the best iterate).
- * Algorithm 4 (direct) or Algorithm 3 (multishift); LR split x = x_P + f(A)(I-P)b
- * (Eq. action) when use_deflation. Errors: EINVAL, ENOMEM, ECUDA. */
+ * Algorithm 4 (direct), Algorithm 3 (multishift BiCG) or Algorithm 1 (restarted FOM: k_max
+ * bounds the Arnoldi steps over all cycles, tol the shifted residuals |rho_i| |r| / |r_0|, the
+ * rational function as for the multishift method); LR split x = x_P + f(A)(I-P)b (Eq. action)
+ * when use_deflation. Errors: EINVAL, ENOMEM, ECUDA. */
 ovl_status ovl_apply_sign(ovl_lattice* lat, const ovl_sign_params* p, int32_t nrhs,
                           const void* b, void* x, ovl_sign_info* info, void* stream);
 
@@ -248,12 +253,21 @@ typedef struct {
   int32_t k_max;
   int32_t precision;        /* OVL_PREC_* */
   const void* b;            /* host complex128 [nrhs][n]; copied during ovl_submit */
+  int32_t method;           /* OVL_DIRECT_2SL (0) | OVL_MULTISHIFT_BICG (FP32 / FP16-link precisions
+                               refine with FP64 reliable updates below tol 2e-6) */
+  int32_t use_deflation;    /* 1: the field's deflation set (ovl_set_deflation on the field, same m_W, mu) */
+  int32_t rational_kind;    /* multishift: OVL_RAT_NEUBERGER | OVL_RAT_ZOLOTAREV */
+  int32_t s;                /* multishift: poles (0: Eq. no_of_poles from the bounds, Neuberger) */
+  double spec_lo, spec_hi;  /* multishift: bounds of |lambda| of the (deflated) spectrum */
 } ovl_request;
 
 /* A request loop on worker threads: requests are admitted when their device footprint fits
  * the memory budget and a slot is free, the least estimated work first (sites x nrhs x k_max)
  * unless the oldest request has waited more than 2 s; admitted requests run concurrently
- * (continuous batching across streams). The admission order does not change any result. */
+ * (continuous batching across streams). The admission order does not change any result.
+ * A field's links and deflation set are read at every solve: ovl_set_links / ovl_set_deflation
+ * on a field take effect for requests admitted afterwards and return OVL_EBUSY while a solve is
+ * reading them; ovl_destroy_lattice on a field returns OVL_EBUSY until its server is destroyed. */
 ovl_status ovl_server_create(ovl_ctx* ctx, const ovl_server_cfg* cfg, ovl_server** out);
 ovl_status ovl_server_add_field(ovl_server* srv, ovl_lattice* lat, int32_t* field_id);
 /* Enqueue; *ticket identifies the request. EINVAL for a request that can never fit. */

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "OK", 1: "PENDING", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", 
 OVL_F64, OVL_F32, OVL_F16R12 = 1, 2, 4
 OVL_C128, OVL_C64 = 0, 1
 OVL_DAGGER, OVL_GAMMA5, OVL_NATIVE, OVL_LINKS_F32, OVL_LINKS_F16R12 = 1, 2, 4, 8, 16
-OVL_DIRECT_2SL, OVL_MULTISHIFT_BICG = 0, 1
+OVL_DIRECT_2SL, OVL_MULTISHIFT_BICG, OVL_FOM_RESTARTED = 0, 1, 2
 OVL_PREC_F64, OVL_PREC_F32, OVL_PREC_F32_F16LINKS = 0, 1, 2
 OVL_RAT_NEUBERGER, OVL_RAT_ZOLOTAREV, OVL_RAT_CUSTOM = 0, 1, 2
 
@@ -45,7 +45,7 @@ class ovl_sign_params(ctypes.Structure):
         ("spec_lo", ctypes.c_double), ("spec_hi", ctypes.c_double),
         ("omega", ctypes.POINTER(ctypes.c_double)), ("sigma", ctypes.POINTER(ctypes.c_double)),
         ("host_io", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("fixed_k", ctypes.c_int32),
-        ("priority", ctypes.c_int32),
+        ("priority", ctypes.c_int32), ("restart_k", ctypes.c_int32),
     ]
 
 
@@ -70,7 +70,9 @@ class ovl_request(ctypes.Structure):
     _fields_ = [
         ("field_id", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("mu", ctypes.c_double), ("m_W", ctypes.c_double),
         ("tol", ctypes.c_double), ("k_max", ctypes.c_int32), ("precision", ctypes.c_int32),
-        ("b", ctypes.c_void_p),
+        ("b", ctypes.c_void_p), ("method", ctypes.c_int32), ("use_deflation", ctypes.c_int32),
+        ("rational_kind", ctypes.c_int32), ("s", ctypes.c_int32), ("spec_lo", ctypes.c_double),
+        ("spec_hi", ctypes.c_double),
     ]
 
 
@@ -376,13 +378,17 @@ def _nrhs_of(b: np.ndarray, nrhs):
     raise ValueError("pass nrhs for a spinor array of shape %r" % (b.shape,))
 
 
-def ovl_submit(srv, field_id, b: np.ndarray, mu, tol, m_W=-2.0, k_max=600, precision=OVL_PREC_F64, nrhs=None):
-    """Queue x = sign(H_W(mu)) b on a registered field; b is copied before the call returns."""
+def ovl_submit(srv, field_id, b: np.ndarray, mu, tol, m_W=-2.0, k_max=600, precision=OVL_PREC_F64, nrhs=None,
+               method=OVL_DIRECT_2SL, use_deflation=0, rational_kind=OVL_RAT_NEUBERGER, s=0, spec_lo=0.0,
+               spec_hi=0.0):
+    """Queue x = sign(H_W(mu)) b on a registered field; b is copied before the call returns.
+    method OVL_MULTISHIFT_BICG needs spec_lo < spec_hi (and s > 0 for Zolotarev)."""
     b = np.ascontiguousarray(b, dtype=np.complex128)
     nr = _nrhs_of(b, nrhs)
     if b.size % (12 * nr) != 0:
         raise ValueError("b does not hold nrhs whole spinors")
-    req = ovl_request(field_id, nr, mu, m_W, tol, k_max, precision, b.ctypes.data)
+    req = ovl_request(field_id, nr, mu, m_W, tol, k_max, precision, b.ctypes.data, method, use_deflation,
+                      rational_kind, s, spec_lo, spec_hi)
     t = ctypes.c_uint64()
     _check(lib.ovl_submit(srv, ctypes.byref(req), ctypes.byref(t)))
     return t.value

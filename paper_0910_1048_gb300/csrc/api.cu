@@ -1,5 +1,6 @@
 // C ABI entry points (include/ovl.h): context, lattice, links, deflation, D_W, sign solves.
 #include <cstdarg>
+#include <mutex>
 #include <cstdlib>
 #include <vector>
 
@@ -21,16 +22,16 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
                         ovl_sign_info* info, cudaStream_t st);
 ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, const double2* b, double2* x,
                             ovl_sign_info* info, cudaStream_t st);
+ovl_status solve_fom(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, const double2* b, double2* x,
+                     ovl_sign_info* info, cudaStream_t st);
 
-// A lattice sharing `parent`'s links (not its deflation set) with its own workspaces.
+// A lattice with its own workspaces that reads `parent`'s links and deflation set at every solve
+// (so it sees later ovl_set_links / ovl_set_deflation on the parent).
 ovl_lattice* lattice_view(ovl_lattice* parent) {
   ovl_lattice* v = new ovl_lattice();
   v->ctx = parent->ctx;
   v->g = parent->g;
-  v->formats = parent->formats;
-  v->u64 = parent->u64;
-  v->u32 = parent->u32;
-  v->u16 = parent->u16;
+  v->parent = parent;
   v->owns_links = false;
   v->server_mode = true;
   return v;
@@ -104,6 +105,10 @@ ovl_status ovl_create_lattice(ovl_ctx* ctx, const int32_t dims[4], int32_t t_bc,
 ovl_status ovl_destroy_lattice(ovl_lattice* lat) {
   clear_error();
   if (!lat) return OVL_OK;
+  if (lat->servers.load() > 0) {
+    set_error("ovl_destroy_lattice: the lattice is a field of a request server; destroy the server first");
+    return OVL_EBUSY;
+  }
   DeviceGuard dg(lat->ctx->device);
   free_direct_ws(lat->dws);
   free_multi_ws(lat->mws);
@@ -124,6 +129,11 @@ ovl_status ovl_set_links(ovl_lattice* lat, const void* U, int32_t U_on_device, u
   clear_error();
   OVL_REQUIRE(lat && U, "ovl_set_links: NULL argument");
   OVL_REQUIRE((formats & ~(OVL_F64 | OVL_F32 | OVL_F16R12)) == 0, "ovl_set_links: unknown format bits 0x%x", formats);
+  std::unique_lock<std::shared_mutex> excl(lat->guard, std::try_to_lock);
+  if (!excl.owns_lock()) {
+    set_error("ovl_set_links: a solve is using this lattice's links (retry when it has finished)");
+    return OVL_EBUSY;
+  }
   OVL_DEVICE_SCOPE(lat->ctx->device);
   const size_t nl = (size_t)36 * lat->g.vol;  // complex entries
   formats |= OVL_F64;
@@ -152,6 +162,11 @@ ovl_status ovl_set_deflation(ovl_lattice* lat, double m_W, double mu, int32_t m,
   clear_error();
   OVL_REQUIRE(lat, "ovl_set_deflation: NULL lattice");
   OVL_REQUIRE(m >= 0 && m <= 1024, "ovl_set_deflation: m must be in [0, 1024]");
+  std::unique_lock<std::shared_mutex> excl(lat->guard, std::try_to_lock);
+  if (!excl.owns_lock()) {
+    set_error("ovl_set_deflation: a solve is using this lattice's deflation set (retry when it has finished)");
+    return OVL_EBUSY;
+  }
   OVL_DEVICE_SCOPE(lat->ctx->device);
   cudaFree(lat->defl.R);
   cudaFree(lat->defl.L);
@@ -229,20 +244,21 @@ ovl_status ovl_apply_DW(ovl_lattice* lat, double m_W, double mu, uint32_t flags,
   OVL_REQUIRE((flags & ~(OVL_DAGGER | OVL_GAMMA5 | OVL_NATIVE | OVL_LINKS_F32 | OVL_LINKS_F16R12)) == 0,
               "ovl_apply_DW: unknown flags 0x%x", flags);
   OVL_REQUIRE(2.0 * m_W + 8.0 != 0.0, "ovl_apply_DW: m_W = -4 has no kappa");
+  std::shared_lock<std::shared_mutex> shared(lat->src()->guard);
   OVL_DEVICE_SCOPE(lat->ctx->device);
   const bool f64 = dtype == OVL_C128;
   int lf = LINK_F64;
   if (f64) {
     OVL_REQUIRE(!(flags & (OVL_LINKS_F32 | OVL_LINKS_F16R12)), "ovl_apply_DW: FP64 uses FP64 links");
-    OVL_REQUIRE(lat->u64, "ovl_apply_DW: links not set");
+    OVL_REQUIRE(lat->src()->u64, "ovl_apply_DW: links not set");
   } else {
     lf = (flags & OVL_LINKS_F16R12) ? LINK_F16R12 : LINK_F32;
-    OVL_REQUIRE(lf == LINK_F32 ? lat->u32 != nullptr : lat->u16 != nullptr,
+    OVL_REQUIRE(lf == LINK_F32 ? lat->src()->u32 != nullptr : lat->src()->u16 != nullptr,
                 "ovl_apply_DW: links not set in the requested format");
   }
   const bool dag = flags & OVL_DAGGER, g5 = flags & OVL_GAMMA5, nat = flags & OVL_NATIVE;
   // D^H = g5 D(-mu) g5; output gamma5 count = dag xor g5
-  OVL_CHECK_CUDA(launch_dslash(lat->g, lat->links(), lf, f64, m_W, dag ? -mu : mu, dag, dag != g5, nat, nat, nrhs, in,
+  OVL_CHECK_CUDA(launch_dslash(lat->g, lat->src()->links(), lf, f64, m_W, dag ? -mu : mu, dag, dag != g5, nat, nat, nrhs, in,
                                out, (cudaStream_t)stream));
   return OVL_OK;
 }
@@ -259,6 +275,7 @@ void ovl_sign_params_default(ovl_sign_params* p) {
   p->check_every = 20;
   p->rational_kind = OVL_RAT_NEUBERGER;
   p->use_graphs = 1;
+  p->restart_k = 40;
 }
 
 ovl_status ovl_apply_sign(ovl_lattice* lat, const ovl_sign_params* p, int32_t nrhs, const void* b, void* x,
@@ -269,11 +286,14 @@ ovl_status ovl_apply_sign(ovl_lattice* lat, const ovl_sign_params* p, int32_t nr
   OVL_REQUIRE(p->precision >= OVL_PREC_F64 && p->precision <= OVL_PREC_F32_F16LINKS, "ovl_apply_sign: precision");
   OVL_REQUIRE(p->tol >= 0, "ovl_apply_sign: tol must be >= 0");
   OVL_REQUIRE(2.0 * p->m_W + 8.0 != 0.0, "ovl_apply_sign: m_W = -4 has no kappa");
+  std::shared_lock<std::shared_mutex> shared(lat->src()->guard);  // links / deflation set stay as they are
   OVL_DEVICE_SCOPE(lat->ctx->device);
   if (p->method == OVL_DIRECT_2SL)
     return solve_direct(lat, p, nrhs, (const double2*)b, (double2*)x, info, (cudaStream_t)stream);
   if (p->method == OVL_MULTISHIFT_BICG)
     return solve_multishift(lat, p, nrhs, (const double2*)b, (double2*)x, info, (cudaStream_t)stream);
+  if (p->method == OVL_FOM_RESTARTED)
+    return solve_fom(lat, p, nrhs, (const double2*)b, (double2*)x, info, (cudaStream_t)stream);
   set_error("ovl_apply_sign: unknown method %d", p->method);
   return OVL_EINVAL;
 }

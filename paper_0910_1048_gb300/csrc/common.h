@@ -4,9 +4,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <shared_mutex>
 #include <string>
 #include <vector>
 
@@ -142,6 +144,9 @@ void free_multi_ws(MultiWS*);
 
 struct ovl_lattice {
   ovl_ctx* ctx = nullptr;
+  ovl_lattice* parent = nullptr;  // a server view: links and deflation set are the parent's
+  std::shared_mutex guard;        // solves hold it shared, ovl_set_links / ovl_set_deflation exclusive
+  std::atomic<int> servers{0};    // request servers this lattice is registered with
   bool owns_links = true;    // false for a server view sharing another lattice's links
   bool server_mode = false;  // workspaces allocated stream-ordered and released after each solve
   ovl::DirectWS* dws = nullptr;
@@ -161,4 +166,8 @@ struct ovl_lattice {
     l.f16 = u16;
     return l;
   }
+  // the lattice whose links and deflation set a solve on this one uses (a view reads its parent's,
+  // so later ovl_set_links / ovl_set_deflation on the field are seen by every view)
+  const ovl_lattice* src() const { return parent ? parent : this; }
+  ovl_lattice* src() { return parent ? parent : this; }
 };

@@ -26,6 +26,9 @@
 namespace ovl {
 ovl_lattice* lattice_view(ovl_lattice* parent);
 size_t direct_footprint(int vol, int nrhs, int kmax, bool f64);
+size_t multishift_footprint(int vol, int nrhs, int s, bool f64, bool refine);
+void neuberger_for_spectrum(double lo, double hi, double eps, int* s_out, double* c_out, double* d_out);
+constexpr double kFp32FloorHost = 2e-6;  // below it the reduced-precision multishift refines (FP64)
 }  // namespace ovl
 
 struct ovl_server {
@@ -51,14 +54,30 @@ struct ovl_server {
   uint64_t next_ticket = 1;
   bool stop = false;
   std::vector<std::thread> workers;
-  std::vector<std::vector<ovl_lattice*>> views;  // [slot][field]
+  // (slot, field) -> the slot's view of the field (own workspaces, the field's links and
+  // deflation set); created and looked up under `mu`, used outside it (the pointer is stable)
+  std::map<std::pair<int, int>, ovl_lattice*> views;
 };
 
 namespace {
 
+// Poles a multishift request will use: given, or Eq. no_of_poles for Neuberger (as the solver
+// chooses them).
+int request_poles(const ovl_request& r) {
+  if (r.s > 0) return r.s;
+  int s = 0;
+  double c = 0, d = 0;
+  ovl::neuberger_for_spectrum(r.spec_lo, r.spec_hi, std::max(r.tol, 1e-15), &s, &c, &d);
+  return s;
+}
+
 size_t footprint(const ovl_server* s, const ovl_request& r) {
   const ovl_lattice* lat = s->fields[r.field_id];
-  return ovl::direct_footprint(lat->g.vol, r.nrhs, r.k_max, r.precision == OVL_PREC_F64);
+  const bool f64 = r.precision == OVL_PREC_F64;
+  if (r.method == OVL_MULTISHIFT_BICG)
+    return ovl::multishift_footprint(lat->g.vol, r.nrhs, request_poles(r), f64,
+                                     !f64 && r.tol < ovl::kFp32FloorHost);
+  return ovl::direct_footprint(lat->g.vol, r.nrhs, r.k_max, f64);
 }
 
 constexpr double kMaxWait = 2.0;  // seconds after which the oldest request goes first
@@ -82,6 +101,7 @@ void worker(ovl_server* s, int slot) {
   cudaSetDevice(s->ctx->device);
   for (;;) {
     ovl_server::Request* job = nullptr;
+    ovl_lattice* view = nullptr;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       long at = -1;
@@ -91,18 +111,24 @@ void worker(ovl_server* s, int slot) {
       job = s->reqs[s->queue[at]].get();
       s->queue.erase(s->queue.begin() + at);
       s->in_use += job->footprint;
+      ovl_lattice*& v = s->views[{slot, job->req.field_id}];
+      if (!v) v = ovl::lattice_view(s->fields[job->req.field_id]);
+      view = v;
     }
     const ovl_request& r = job->req;
-    ovl_lattice*& view = s->views[slot][r.field_id];
-    if (!view) view = ovl::lattice_view(s->fields[r.field_id]);
     ovl_sign_params p;
     ovl_sign_params_default(&p);
-    p.method = OVL_DIRECT_2SL;
+    p.method = r.method;
     p.precision = r.precision;
     p.m_W = r.m_W;
     p.mu = r.mu;
     p.tol = r.tol;
     p.k_max = r.k_max;
+    p.use_deflation = r.use_deflation;
+    p.rational_kind = r.rational_kind;
+    p.s = r.s;
+    p.spec_lo = r.spec_lo;
+    p.spec_hi = r.spec_hi;
     p.host_io = 1;
     std::vector<ovl_sign_info> info(r.nrhs);
     std::vector<double> x(job->b.size());
@@ -133,7 +159,6 @@ ovl_status ovl_server_create(ovl_ctx* ctx, const ovl_server_cfg* cfg, ovl_server
   ovl_server* s = new ovl_server();
   s->ctx = ctx;
   s->cfg = *cfg;
-  s->views.assign(cfg->max_slots, {});
   for (int i = 0; i < cfg->max_slots; ++i) s->workers.emplace_back(worker, s, i);
   *out = s;
   return OVL_OK;
@@ -143,9 +168,10 @@ ovl_status ovl_server_add_field(ovl_server* s, ovl_lattice* lat, int32_t* field_
   ovl::clear_error();
   OVL_REQUIRE(s && lat && field_id, "ovl_server_add_field: NULL argument");
   OVL_REQUIRE(lat->u64, "ovl_server_add_field: the lattice has no links");
+  OVL_REQUIRE(lat->parent == nullptr, "ovl_server_add_field: not a field lattice");
   std::lock_guard<std::mutex> lk(s->mu);
   s->fields.push_back(lat);
-  for (auto& v : s->views) v.resize(s->fields.size(), nullptr);
+  lat->servers.fetch_add(1);  // ovl_destroy_lattice refuses it until the server is destroyed
   *field_id = (int32_t)s->fields.size() - 1;
   return OVL_OK;
 }
@@ -155,6 +181,13 @@ ovl_status ovl_submit(ovl_server* s, const ovl_request* r, uint64_t* ticket) {
   OVL_REQUIRE(s && r && ticket && r->b, "ovl_submit: NULL argument");
   OVL_REQUIRE(r->nrhs >= 1 && r->nrhs <= 64 && r->k_max >= 1 && r->tol >= 0, "ovl_submit: invalid request");
   OVL_REQUIRE(r->precision >= OVL_PREC_F64 && r->precision <= OVL_PREC_F32_F16LINKS, "ovl_submit: precision");
+  OVL_REQUIRE(r->method == OVL_DIRECT_2SL || r->method == OVL_MULTISHIFT_BICG, "ovl_submit: method");
+  OVL_REQUIRE(r->method == OVL_DIRECT_2SL ||
+                  (r->spec_lo > 0 && r->spec_hi > r->spec_lo &&
+                   (r->rational_kind == OVL_RAT_NEUBERGER || r->rational_kind == OVL_RAT_ZOLOTAREV) &&
+                   (r->rational_kind == OVL_RAT_NEUBERGER || r->s > 0) && r->s >= 0 && r->s <= 127),
+              "ovl_submit: a multishift request needs 0 < spec_lo < spec_hi and a Neuberger or Zolotarev kind "
+              "(Zolotarev with s > 0)");
   std::unique_lock<std::mutex> lk(s->mu);
   OVL_REQUIRE(r->field_id >= 0 && r->field_id < (int)s->fields.size(), "ovl_submit: unknown field %d", r->field_id);
   const ovl_lattice* lat = s->fields[r->field_id];
@@ -162,6 +195,8 @@ ovl_status ovl_submit(ovl_server* s, const ovl_request* r, uint64_t* ticket) {
                        (r->precision == OVL_PREC_F32 ? lat->u32 != nullptr : lat->u16 != nullptr);
   OVL_REQUIRE(has_fmt,
               "ovl_submit: field lacks the link format of this precision");
+  OVL_REQUIRE(!r->use_deflation || (lat->defl.m > 0 && lat->defl.m_w == r->m_W && lat->defl.mu == r->mu),
+              "ovl_submit: use_deflation needs the field's deflation set for (m_W, mu) = (%g, %g)", r->m_W, r->mu);
   auto job = std::make_unique<ovl_server::Request>();
   job->req = *r;
   job->footprint = footprint(s, *r);
@@ -211,9 +246,9 @@ ovl_status ovl_server_destroy(ovl_server* s) {
   }
   s->cv.notify_all();
   for (auto& t : s->workers) t.join();
-  for (auto& v : s->views)
-    for (ovl_lattice* l : v)
-      if (l) ovl_destroy_lattice(l);
+  for (auto& kv : s->views)
+    if (kv.second) ovl_destroy_lattice(kv.second);
+  for (ovl_lattice* f : s->fields) f->servers.fetch_sub(1);
   delete s;
   return OVL_OK;
 }

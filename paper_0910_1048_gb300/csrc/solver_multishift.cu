@@ -246,8 +246,10 @@ static ovl_status ensure_mws(ovl_lattice* lat, int nrhs, int s, bool f64, int m,
   return OVL_OK;
 }
 
-// Rational coefficients for the call; returns the approximation's own error bound.
-static ovl_status coefficients(const ovl_sign_params* p, std::vector<double>& om, std::vector<double>& sg, double* bound) {
+// Rational coefficients for the call; returns the approximation's own error bound. Shared with the
+// restarted FOM driver.
+ovl_status rational_coefficients(const ovl_sign_params* p, std::vector<double>& om, std::vector<double>& sg,
+                                 double* bound) {
   if (p->rational_kind == OVL_RAT_CUSTOM) {
     OVL_REQUIRE(p->s >= 1 && p->s <= kMaxShifts && p->omega && p->sigma, "apply_sign: custom rational needs s, omega, sigma");
     om.assign(p->omega, p->omega + p->s);
@@ -286,20 +288,20 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
   auto t0 = std::chrono::steady_clock::now();
   const bool f64 = p->precision == OVL_PREC_F64;
   const int lf = p->precision == OVL_PREC_F32_F16LINKS ? LINK_F16R12 : (f64 ? LINK_F64 : LINK_F32);
-  OVL_REQUIRE(lat->u64, "apply_sign: links not set");
-  OVL_REQUIRE(f64 || (lf == LINK_F32 ? lat->u32 != nullptr : lat->u16 != nullptr),
+  OVL_REQUIRE(lat->src()->u64, "apply_sign: links not set");
+  OVL_REQUIRE(f64 || (lf == LINK_F32 ? lat->src()->u32 != nullptr : lat->src()->u16 != nullptr),
               "apply_sign: links not set in the format this precision needs (ovl_set_links formats)");
   OVL_REQUIRE(p->k_max >= 1 && p->k_max <= 1000000, "apply_sign: k_max must be in [1, 1e6]");
   std::vector<double> om, sg;
   double bound = 0;
-  OVL_TRY(coefficients(p, om, sg, &bound));
+  OVL_TRY(rational_coefficients(p, om, sg, &bound));
   const int s = (int)om.size();
   int m = 0;
   if (p->use_deflation) {
-    OVL_REQUIRE(lat->defl.m > 0, "apply_sign: use_deflation but no deflation set");
-    OVL_REQUIRE(lat->defl.m_w == p->m_W && lat->defl.mu == p->mu,
-                "apply_sign: deflation set was computed for (m_W, mu) = (%g, %g)", lat->defl.m_w, lat->defl.mu);
-    m = lat->defl.m;
+    OVL_REQUIRE(lat->src()->defl.m > 0, "apply_sign: use_deflation but no deflation set");
+    OVL_REQUIRE(lat->src()->defl.m_w == p->m_W && lat->src()->defl.mu == p->mu,
+                "apply_sign: deflation set was computed for (m_W, mu) = (%g, %g)", lat->src()->defl.m_w, lat->src()->defl.mu);
+    m = lat->src()->defl.m;
   }
   // FP32 iterations reach about 1e-6; below that each shifted system is refined with FP64
   // residuals (reliable updates): x^(i) kept in FP64, r^(i) = r - (A^2 - sigma_i) x^(i) from the
@@ -327,13 +329,13 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
     bd = w->bdev;
   }
   std::vector<double> ls(std::max(m, 1));
-  for (int i = 0; i < m; ++i) ls[i] = lat->defl.lam[2 * i] >= 0 ? 1.0 : -1.0;
+  for (int i = 0; i < m; ++i) ls[i] = lat->src()->defl.lam[2 * i] >= 0 ? 1.0 : -1.0;
   if (m > 0) OVL_CHECK_CUDA(cudaMemcpyAsync(w->lam_sign, ls.data(), m * 8, cudaMemcpyHostToDevice, st));
   MsVecs v = w->v;
   if (m == 0) v.xp = nullptr;
   if (!refine) v.xs = v.r64 = nullptr;
-  OVL_CHECK_CUDA(launch_ms_start(g, f64, ms, v, bd, m, lat->defl.R, lat->defl.L, w->lam_sign, w->dots, st));
-  const Links U = lat->links();
+  OVL_CHECK_CUDA(launch_ms_start(g, f64, ms, v, bd, m, lat->src()->defl.R, lat->src()->defl.L, w->lam_sign, w->dots, st));
+  const Links U = lat->src()->links();
   const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 20, p->k_max));
   const bool use_graph = p->use_graphs != 0 && chunk > 1;
   if (use_graph && !(w->graph[0] && w->gchunk == chunk && w->g_lf == lf && w->g_mw == p->m_W && w->g_mu == p->mu &&
@@ -441,7 +443,7 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
     const int total = nrhs * s, grp = w->grp;
     // the correction solves run with FP32 links when the field has them: with FP16 12-real links
     // the operator itself is off by ~1e-3, which would cap what one correction sweep can gain
-    const int lf_ref = lat->u32 ? LINK_F32 : lf;
+    const int lf_ref = lat->src()->u32 ? LINK_F32 : lf;
     OVL_CHECK_CUDA(launch_ff_to_f64((size_t)total * n, v.xs, st));
     launches += 1;
     MsDev gm = w->gms;
@@ -595,8 +597,24 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
       info[r].ritz_evaluations = 0;
     }
   }
+  if (lat->server_mode) {  // the server accounts device memory per request
+    free_multi_ws(lat->mws);
+    lat->mws = nullptr;
+  }
   if (result != OVL_OK) set_error("apply_sign: at least one right-hand side ended with status %d", result);
   return result;
+}
+
+// Device bytes of one multishift solve (the workspace of ensure_mws, the correction batch at its
+// largest), for the server's admission.
+size_t multishift_footprint(int vol, int nrhs, int s, bool f64, bool refine) {
+  const size_t n = (size_t)12 * vol, elt = f64 ? 16 : 8, nr = (size_t)nrhs;
+  size_t b = nr * n * (8 * elt + (size_t)s * elt + 5 * 16);
+  if (refine) {
+    const size_t gq = std::min<size_t>(nr * s, kRefineGroup);
+    b += nr * s * n * 16 + nr * n * 16 + gq * n * (4 * 16 + 9 * 8 + 16);
+  }
+  return b + ((size_t)1 << 20);
 }
 
 }  // namespace ovl

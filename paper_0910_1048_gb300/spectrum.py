@@ -70,6 +70,11 @@ def critical_eigenpairs(ovl, lat, m_W, mu, m, tol=1e-10, solve_tol=1e-12, k_max=
         L[i] = vl[:, j]
     g = np.einsum("in,in->i", np.conj(L), R)
     L = L / np.conj(g)[:, None]
+    # the off-diagonal overlaps of eigenvectors of distinct eigenvalues vanish only to the
+    # eigensolver's accuracy: replace L by the combination conj(G^-1) L (G = L^H R), which makes
+    # L^H R = I to rounding while leaving each l_i a left eigenvector to that same accuracy
+    G = np.conj(L) @ R.T
+    L = np.conj(np.linalg.inv(G)) @ L
     gap = float(np.abs(lam_r[m]))
     info = {"inverse_solves": calls_r[0] + calls_l[0], "max_LR_offdiag": float(np.abs(np.conj(L) @ R.T - np.eye(m)).max())}
     del keep_r, keep_l

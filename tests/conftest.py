@@ -15,6 +15,20 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: takes more than a few seconds on CPU")
 
 
+def fp16_quantised(u):
+    """Links as the FP16 12-real format stores them: the first two rows' real and imaginary parts
+    rounded to float32 and then to float16, the third row rebuilt as conj(row1 x row2) (SU(3)).
+    Oracles that run on these links see the same operator as the library's FP16-link stencil, so
+    a comparison measures the FP32 arithmetic alone."""
+    q = u.copy()
+    r01 = u[..., :2, :]
+    rr = r01.real.astype(np.float32).astype(np.float16).astype(np.float64)
+    ri = r01.imag.astype(np.float32).astype(np.float16).astype(np.float64)
+    q[..., :2, :] = rr + 1j * ri
+    q[..., 2, :] = np.conj(np.cross(q[..., 0, :], q[..., 1, :]))
+    return q
+
+
 @pytest.fixture(scope="session")
 def problem_4444():
     """4^4, seed-0 links, m_W=-2, mu=0.3, antiperiodic t, Gaussian b (seed 1000):

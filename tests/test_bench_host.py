@@ -9,12 +9,33 @@ def test_workloads_consistent():
         assert wl["method"] in ("direct", "multishift") and wl["precision"] in ("f64", "f32", "f16"), name
         if wl["precision"] == "f16":
             assert wl["method"] == "multishift", "FP16 links only under the multishift's FP64 reliable updates"
-        if "mixed" in wl:
-            m = bench.WORKLOADS[wl["mixed"]]
-            # the companion solves the same problem to at least the same accuracy
-            assert m["dims"] == wl["dims"] and m["mus"] == wl["mus"] and m["m"] == wl["m"], name
-            assert m["tol"] <= wl["tol"], name
+    for name, comps in bench.COMPANIONS.items():
+        wl = bench.WORKLOADS[name]
+        for key, cname in comps:
+            m = bench.WORKLOADS[cname]
+            if key.startswith("mixed_precision"):
+                # a mixed-precision companion solves the same problem to at least the same accuracy
+                assert m["dims"] == wl["dims"] and m["mus"] == wl["mus"] and m["m"] == wl["m"], (name, key)
+                assert m["tol"] <= wl["tol"], (name, key)
     assert bench.DEFAULT_WORKLOAD in bench.WORKLOADS
+    for name, tab in bench.K_TABLE.items():
+        assert set(tab) == set(bench.WORKLOADS[name]["mus"]), name
+        assert all(0 < k <= bench.WORKLOADS[name]["k_max"] for k in tab.values()), name
+
+
+def test_reference_arm_runs_full_oracle_solves(capsys, monkeypatch):
+    """--impl reference on the 4^4 workload: one full oracle solve at the tabled k, split over the
+    timed steps; the JSON line carries the contract's keys."""
+    import json
+    import sys
+
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "lattice4_mu0.3_direct_f64",
+                                      "--steps", "3", "--warmup", "1"])
+    bench.main()
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == bench.UNIT
+    assert line["config"]["k_per_mu"] == {"0.3": bench.K_TABLE["lattice4_mu0.3_direct_f64"][0.3]}
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
 
 
 def test_pair_bytes_count_links_once_per_batch():

@@ -115,3 +115,92 @@ def test_admission_rejects_oversized(ovl, env):
         ovl.ovl_submit(srv, fid, synth.gaussian_source(fields[0][0], 1), 0.3, 1e-8)
     assert e.value.status == ovl.OVL_EINVAL and "budget" in str(e.value)
     ovl.ovl_server_destroy(srv)
+
+
+def _drain(ovl, srv, reqs, timeout=300):
+    results = {}
+    deadline = time.time() + timeout
+    while len(results) < len(reqs) and time.time() < deadline:
+        for r in reqs:
+            t, b, nrhs = r["t"], r["b"], r["nrhs"]
+            if t in results:
+                continue
+            x = np.zeros_like(b)
+            st, info = ovl.ovl_poll(srv, t, nrhs, x)
+            if st != ovl.OVL_PENDING:
+                results[t] = (st, x, info)
+        time.sleep(0.01)
+    return results
+
+
+def test_mixed_methods_stream_matches_alone(ovl, env, problem_4444):
+    """Requests that choose the method and precision (FP64 direct, direct with the field's 16-pair
+    deflation set, FP32 multishift with FP64 reliable updates, Zolotarev) run concurrently; each
+    result equals the same request solved alone, bitwise."""
+    ctx, fields = env
+    p4 = problem_4444
+    lat0 = fields[0][2]  # 4^4, seed-0 links: the links of problem_4444
+    ovl.ovl_set_deflation(lat0, -2.0, 0.3, np.ascontiguousarray(p4["R16"].T), np.ascontiguousarray(p4["L16"].T),
+                          p4["lam16"])
+    lo, hi = 0.99 * float(np.abs(p4["eig"]).min()), 1.01 * float(np.abs(p4["eig"]).max())
+    kinds = [dict(), dict(use_deflation=1), dict(method=ovl.OVL_MULTISHIFT_BICG, precision=ovl.OVL_PREC_F32,
+                                                 spec_lo=lo, spec_hi=hi),
+             dict(method=ovl.OVL_MULTISHIFT_BICG, rational_kind=ovl.OVL_RAT_ZOLOTAREV, s=24, spec_lo=lo,
+                  spec_hi=hi, precision=ovl.OVL_PREC_F32)]
+    srv = ovl.ovl_server_create(ctx, 8 << 30, max_slots=4)
+    fid = ovl.ovl_server_add_field(srv, lat0)
+    reqs = []
+    try:
+        for i in range(8):
+            kw = dict(kinds[i % len(kinds)])
+            kw.setdefault("precision", ovl.OVL_PREC_F64)
+            nrhs = 1 + i % 2
+            b = synth.gaussian_source(p4["dims"], 2000 + i, nrhs=nrhs)
+            t = ovl.ovl_submit(srv, fid, b, 0.3, 1e-8, k_max=3000, nrhs=nrhs, **kw)
+            reqs.append(dict(t=t, b=b, nrhs=nrhs, kw=kw))
+            time.sleep(0.005)
+        results = _drain(ovl, srv, reqs)
+    finally:
+        ovl.ovl_server_destroy(srv)
+    assert len(results) == len(reqs)
+    for r in reqs:
+        st, x, info = results[r["t"]]
+        kw = dict(r["kw"])
+        p = ovl.ovl_sign_params_default(mu=0.3, tol=1e-8, k_max=3000, **kw)
+        x1 = np.zeros_like(r["b"])
+        st1, _ = ovl.ovl_apply_sign(lat0, p, np.ascontiguousarray(r["b"]), x1)
+        assert st == st1 == ovl.OVL_OK, (kw, st, st1)
+        assert np.array_equal(x, x1), kw
+    ovl.ovl_set_deflation(lat0, -2.0, 0.3, None, None, None)
+
+
+def test_field_updates_seen_and_destroy_refused(ovl, env):
+    """A field's links are read at every solve: after ovl_set_links on a served field, a new
+    request sees the new links (equal to a solve on a fresh lattice holding them); destroying a
+    field that a server holds is refused until the server is gone."""
+    ctx, fields = env
+    dims, u1, lat1 = fields[1]
+    srv = ovl.ovl_server_create(ctx, 4 << 30, max_slots=2)
+    fid = ovl.ovl_server_add_field(srv, lat1)
+    b = synth.gaussian_source(dims, 55)
+    try:
+        with pytest.raises(ovl.OvlError) as e:
+            ovl.ovl_destroy_lattice(lat1)
+        assert e.value.status == ovl.OVL_EBUSY
+        ra = dict(t=ovl.ovl_submit(srv, fid, b, 0.2, 1e-8, k_max=2000), b=b, nrhs=1)
+        xa = _drain(ovl, srv, [ra])[ra["t"]][1]
+        u2 = synth.gauge_links(dims, 6)
+        ovl.ovl_set_links(lat1, u2, ovl.OVL_F64 | ovl.OVL_F32)
+        rb = dict(t=ovl.ovl_submit(srv, fid, b, 0.2, 1e-8, k_max=2000), b=b, nrhs=1)
+        stb, xb, _ = _drain(ovl, srv, [rb])[rb["t"]]
+    finally:
+        ovl.ovl_server_destroy(srv)
+        ovl.ovl_set_links(lat1, u1, ovl.OVL_F64 | ovl.OVL_F32)
+    fresh = ovl.ovl_create_lattice(ctx, dims, -1)
+    ovl.ovl_set_links(fresh, u2, ovl.OVL_F64 | ovl.OVL_F32)
+    x2 = np.zeros_like(b)
+    st2, _ = ovl.ovl_apply_sign(fresh, ovl.ovl_sign_params_default(mu=0.2, tol=1e-8, k_max=2000), b, x2)
+    ovl.ovl_destroy_lattice(fresh)
+    assert stb == st2 == ovl.OVL_OK
+    assert np.array_equal(xb, x2)
+    assert not np.allclose(xa, xb)
