@@ -86,10 +86,17 @@ WORKLOADS = {
     "lattice16_mu0.2_nrhs16_multishift_f32_f64rel": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0,
                                                           method="multishift", precision="f32", tol=1e-8,
                                                           k_max=8000, rational="zolotarev", s=20, nrhs=16),
+    # the same FP64 solve on all 16 sources in one batch by the two-pass strategy (Section 2.3): three
+    # basis vectors per source instead of k, twice the stencil work
+    "lattice16_mu0.2_nrhs16_direct_f64_twopass": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0, method="direct",
+                                                      precision="f64", tol=1e-8, k_max=2500, nrhs=16, two_pass=1),
     # 16^4, mu = 0.2, 16 Gaussian sources in one batch sharing the links, FP32 vectors with FP64
     # recurrence scalars and sign(H_k); FP32 vectors bound the attainable accuracy near 1e-5
     "lattice16_mu0.2_nrhs16_direct_f32": dict(dims=(16, 16, 16, 16), mus=(0.2,), m=0, method="direct",
                                               precision="f32", tol=1e-5, k_max=1500, nrhs=16),
+    # 12^4, mu = 0.3: restarted FOM-LR (Algorithm 1) on A^2, k = 40 per cycle, 20 Zolotarev poles, FP64
+    "lattice12_mu0.3_fom_zolo20_f64": dict(dims=(12, 12, 12, 12), mus=(0.3,), m=0, method="fom", precision="f64",
+                                           tol=1e-8, k_max=40000, rational="zolotarev", s=20, restart_k=40),
     # 4^4 smoke-sized case (the oracle finishes it in seconds)
     "lattice4_mu0.3_direct_f64": dict(dims=(4, 4, 4, 4), mus=(0.3,), m=0, method="direct", precision="f64",
                                       tol=1e-8, k_max=1200),
@@ -103,12 +110,14 @@ COMPANIONS = {
     "lattice12_mu0.3_direct_f64": [
         ("mixed_precision", "lattice12_mu0.3_multishift_zolo20_f32_f64rel"),
         ("mixed_precision_f16links", "lattice12_mu0.3_multishift_zolo20_f16links_f64rel"),
+        ("fom_restarted", "lattice12_mu0.3_fom_zolo20_f64"),
         ("lattice16_nrhs16_mixed", "lattice16_mu0.2_nrhs16_multishift_f32_f64rel"),
         ("lattice16_nrhs16_direct_f32", "lattice16_mu0.2_nrhs16_direct_f32"),
     ],
     "lattice8_mu0-0.1-0.3_defl16_direct_f64": [
         ("mixed_precision", "lattice8_mu0-0.1-0.3_defl16_multishift_f32_f64rel")],
-    "lattice16_mu0.2_nrhs4_direct_f64": [("mixed_precision", "lattice16_mu0.2_nrhs16_multishift_f32_f64rel")],
+    "lattice16_mu0.2_nrhs4_direct_f64": [("mixed_precision", "lattice16_mu0.2_nrhs16_multishift_f32_f64rel"),
+                                         ("two_pass_16_sources", "lattice16_mu0.2_nrhs16_direct_f64_twopass")],
 }
 
 # Krylov dimension k the GPU's FP64 direct solve reaches on each workload and mu (seed-0 links,
@@ -116,7 +125,7 @@ COMPANIONS = {
 # (the same amount of Lanczos work); the GPU arm reports its own k beside them.
 K_TABLE = {
     "lattice12_mu0.3_direct_f64": {0.3: 1250},
-    "lattice8_mu0-0.1-0.3_defl16_direct_f64": {0.0: 450, 0.1: 550, 0.3: 900},
+    "lattice8_mu0-0.1-0.3_defl16_direct_f64": {0.0: 730, 0.1: 825, 0.3: 1125},
     "lattice4_mu0.3_direct_f64": {0.3: 1000},
 }
 
@@ -276,14 +285,14 @@ def _setup(ovl, ctx, wl, rng_seed=0, cache=None):
                          setup_inverse_solves=info["inverse_solves"])
                 stored.update({key + "_lam": lam, key + "_R": R, key + "_L": L, key + "_gap": np.array(gap)})
                 changed = True
-        if wl["method"] == "multishift" and wl["m"] == 0:
+        if wl["method"] in ("multishift", "fom") and wl["m"] == 0:
             if key + "_lo" in stored:
                 d["gap"] = float(stored[key + "_lo"])
             else:
                 d["gap"] = spectrum.smallest_modulus(ovl, lat, -2.0, mu, precision=ovl.OVL_PREC_F32)
                 stored[key + "_lo"] = np.array(d["gap"])
                 changed = True
-        if wl["method"] == "multishift":
+        if wl["method"] in ("multishift", "fom"):
             if key + "_hi" in stored:
                 d["spec_hi"] = float(stored[key + "_hi"])
             else:
@@ -299,9 +308,10 @@ def _setup(ovl, ctx, wl, rng_seed=0, cache=None):
 def _params(ovl, wl, d):
     prec = {"f64": ovl.OVL_PREC_F64, "f32": ovl.OVL_PREC_F32, "f16": ovl.OVL_PREC_F32_F16LINKS}[wl["precision"]]
     kw = dict(m_W=-2.0, mu=d["mu"], tol=wl["tol"], k_max=wl["k_max"], precision=prec,
-              use_deflation=1 if wl["m"] > 0 else 0, check_every=25)
-    if wl["method"] == "multishift":
-        kw.update(method=ovl.OVL_MULTISHIFT_BICG, spec_lo=0.98 * d["gap"], spec_hi=d["spec_hi"], check_every=20)
+              use_deflation=1 if wl["m"] > 0 else 0, check_every=25, two_pass=wl.get("two_pass", 0))
+    if wl["method"] in ("multishift", "fom"):
+        kw.update(method=ovl.OVL_MULTISHIFT_BICG if wl["method"] == "multishift" else ovl.OVL_FOM_RESTARTED,
+                  spec_lo=0.98 * d["gap"], spec_hi=d["spec_hi"], check_every=20, restart_k=wl.get("restart_k", 40))
         if wl.get("rational") == "zolotarev":
             kw.update(rational_kind=ovl.OVL_RAT_ZOLOTAREV, s=wl["s"])
     return ovl.ovl_sign_params_default(**kw)
@@ -497,7 +507,7 @@ def _roofline(wl, infos, fp64_peak, fp64_src):
     kt = [i["t_kernel_ms"] for step in infos for _, inf in step for i in inf[:1] if i["kernel_samples"] > 0]
     t_pair = float(np.mean(kt)) if kt else None
     prec = wl["precision"]
-    kernel = "k_lz_pair" if wl["method"] == "direct" else "k_ms_pair"
+    kernel = {"direct": "k_lz_pair", "multishift": "k_ms_pair", "fom": "k_dslash (two per Arnoldi step)"}[wl["method"]]
     nr = wl.get("nrhs", 1)
     traffic = TRAFFIC.get((kernel, prec, tuple(wl["dims"]), nr))
     if prec == "f64":

@@ -154,6 +154,10 @@ typedef struct {
                              urgent (clamped to the device's range); lets concurrent solves favour
                              the longest one. No effect on results. */
   int32_t restart_k;      /* restarted FOM: Arnoldi steps per cycle k (default 40, at most 64) */
+  int32_t two_pass;       /* direct: 1 = two-pass strategy (Section 2.3): the first pass keeps three
+                             basis vectors and builds H_k, the second regenerates the same vectors
+                             and accumulates x; memory O(n) instead of O(k n), twice the stencils.
+                             The stop test then measures the change of y with the column norms. */
 } ovl_sign_params;
 
 typedef struct {

@@ -45,7 +45,7 @@ class ovl_sign_params(ctypes.Structure):
         ("spec_lo", ctypes.c_double), ("spec_hi", ctypes.c_double),
         ("omega", ctypes.POINTER(ctypes.c_double)), ("sigma", ctypes.POINTER(ctypes.c_double)),
         ("host_io", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("fixed_k", ctypes.c_int32),
-        ("priority", ctypes.c_int32), ("restart_k", ctypes.c_int32),
+        ("priority", ctypes.c_int32), ("restart_k", ctypes.c_int32), ("two_pass", ctypes.c_int32),
     ]
 
 

@@ -260,6 +260,12 @@ cudaError_t launch_dslash(const Geom& g, const Links& U, int lf, bool f64, doubl
 }
 
 // ------------------------------------------------------------------ Lanczos: start
+// Offset of basis column j (1-based) of rhs: slot (j - 1) % vcols (every column with the full
+// basis, a rotating window of three in the two-pass mode).
+__device__ __forceinline__ size_t vcol(const LzDev& lz, int rhs, int j, size_t n) {
+  return ((size_t)rhs * lz.vcols + (size_t)((j - 1) % lz.vcols)) * n;
+}
+
 // part layout for this kernel: [nrhs][nblk][4] = (|r|^2, Re r^H r~, Im r^H r~, |r~|^2)
 template <class R>
 __global__ void __launch_bounds__(kBlock) k_lz_start(Geom g, LzDev lz, typename V2<R>::T* vh, typename V2<R>::T* wh,
@@ -271,7 +277,7 @@ __global__ void __launch_bounds__(kBlock) k_lz_start(Geom g, LzDev lz, typename 
   const size_t n = (size_t)12 * g.vol;
   double acc[4] = {0, 0, 0, 0};
   if (s < g.vol) {
-    T* v1 = vh + (size_t)rhs * (lz.kmax + 1) * n;  // column 1
+    T* v1 = vh + vcol(lz, rhs, 1, n);  // column 1
     T* w1 = wh + (size_t)(1 * lz.nrhs + rhs) * n;  // slot (1 & 1) = 1
     const double2* dr = dots + (size_t)rhs * 2 * m;
     for (int c = 0; c < 12; ++c) {
@@ -289,6 +295,11 @@ __global__ void __launch_bounds__(kBlock) k_lz_start(Geom g, LzDev lz, typename 
       if (xp) stc<double>(xp, (size_t)rhs * n + e, x);
       stc<R>(v1, e, mk<R>((R)r.re, (R)r.im));
       stc<R>(w1, e, mk<R>((R)rt.re, (R)rt.im));
+      if (lz.xacc) {  // second pass: x = coef_1 vhat_1 (the stored, rounded vector)
+        const cplx<R> s1 = ldc<R>(v1, e);
+        stc<double>(lz.xacc, (size_t)rhs * n + e,
+                    ldc<double>(lz.xcoef, (size_t)rhs * (lz.kmax + 2) + 1) * mk((double)s1.re, (double)s1.im));
+      }
       acc[0] += norm2(r);
       zd ip = cdot(r, rt);
       acc[1] += ip.re;
@@ -433,7 +444,7 @@ __global__ void __launch_bounds__(2 * PS) k_lz_pair(Geom g, Links U, HopCoef<R> 
   const size_t n = (size_t)12 * g.vol;
   const size_t o = (size_t)rhs * (lz.kmax + 2);
   const double2 swd = lz.sw[o + j];
-  const T* vj = vh + ((size_t)rhs * (lz.kmax + 1) + (j - 1)) * n;
+  const T* vj = vh + vcol(lz, rhs, j, n);
   const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
   const int s = blockIdx.x * PS + threadIdx.x;
   const bool is_w = threadIdx.y == 1;
@@ -495,7 +506,7 @@ __global__ void __launch_bounds__(8 * kSplitSites) k_lz_pair_split(Geom g, Links
   const size_t n = (size_t)12 * g.vol;
   const size_t o = (size_t)rhs * (lz.kmax + 2);
   const double2 swd = lz.sw[o + j];
-  const T* vj = vh + ((size_t)rhs * (lz.kmax + 1) + (j - 1)) * n;
+  const T* vj = vh + vcol(lz, rhs, j, n);
   const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
   const R sv = (R)lz.sv[o + j];
   const cplx<R> sw = mk<R>((R)swd.x, (R)swd.y);
@@ -551,9 +562,11 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typen
   const double2 u0 = uc[0], u1 = uc[1], u2 = uc[2], u3 = uc[3];
   const cplx<R> a1 = mk<R>((R)u0.x, (R)u0.y), a2 = mk<R>((R)u1.x, (R)u1.y);
   const cplx<R> b1 = mk<R>((R)u2.x, (R)u2.y), b2 = mk<R>((R)u3.x, (R)u3.y);
-  const T* vj = vh + ((size_t)rhs * (lz.kmax + 1) + (j - 1)) * n;
-  const T* vjm = vh + ((size_t)rhs * (lz.kmax + 1) + (j > 1 ? j - 2 : 0)) * n;
-  T* vnew = vh + ((size_t)rhs * (lz.kmax + 1) + j) * n;
+  const T* vj = vh + vcol(lz, rhs, j, n);
+  const T* vjm = vh + vcol(lz, rhs, j > 1 ? j - 1 : 1, n);
+  T* vnew = vh + vcol(lz, rhs, j + 1, n);
+  double2* xa = lz.xacc ? lz.xacc + (size_t)rhs * n : nullptr;  // second pass: x += coef_{j+1} vhat_{j+1}
+  const zd xc = lz.xacc ? ldc<double>(lz.xcoef, o + j + 1) : mk(0.0, 0.0);
   const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
   T* wnew = wh + ((size_t)((j + 1) & 1) * lz.nrhs + rhs) * n;  // holds what_{j-1} until overwritten
   const T* avr = av + (size_t)rhs * n;
@@ -587,6 +600,10 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typen
     }
     stc<R>(vnew, e0, x0);
     stc<R>(wnew, e0, y0);
+    if (xa) {  // the stored (rounded) vector, in the order of the one-pass combine
+      const cplx<R> s0 = ldc<R>(vnew, e0);
+      stc<double>(xa, e0, ldc<double>(xa, e0) + xc * mk((double)s0.re, (double)s0.im));
+    }
     acc[0].dot2(y0.re, x0.re, y0.im, x0.im);  // (y^H x).re
     acc[1].dot2(y0.re, x0.im, -y0.im, x0.re);  // (y^H x).im
     acc[2].dot2(x0.re, x0.re, x0.im, x0.im);
@@ -594,6 +611,10 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typen
     if (has1) {
       stc<R>(vnew, e1, x1);
       stc<R>(wnew, e1, y1);
+      if (xa) {
+        const cplx<R> s1 = ldc<R>(vnew, e1);
+        stc<double>(xa, e1, ldc<double>(xa, e1) + xc * mk((double)s1.re, (double)s1.im));
+      }
       acc[0].dot2(y1.re, x1.re, y1.im, x1.im);
       acc[1].dot2(y1.re, x1.im, -y1.im, x1.re);
       acc[2].dot2(x1.re, x1.re, x1.im, x1.im);

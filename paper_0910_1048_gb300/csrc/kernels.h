@@ -56,7 +56,8 @@ inline unsigned vec_blocks(const Geom& g, int elt) {
 inline int partial_slots(const Geom& g) { return (int)vec_blocks(g); }
 
 // Device state of the two-sided Lanczos recurrences for nrhs right-hand sides.
-// Index conventions: column j = 1..kmax+1 of the basis; scalars indexed by j.
+// Index conventions: column j = 1..kmax+1 of the basis, stored at slot (j - 1) % vcols; scalars
+// indexed by j.
 struct LzDev {
   int kmax = 0;
   int nrhs = 0;
@@ -72,6 +73,9 @@ struct LzDev {
   double* beta0 = nullptr;  // [nrhs] ||r||
   double* part = nullptr;   // [nrhs][nblk][4] block partials
   unsigned* count = nullptr;// [nrhs] last-block counters (kept at 0 between launches)
+  int vcols = 0;            // basis columns kept per rhs: kmax + 1, or 3 (two-pass: a rotating window)
+  double2* xacc = nullptr;  // two-pass, second pass: [nrhs][12][V] FP64 sum of coef_j vhat_j so far
+  const double2* xcoef = nullptr;  // two-pass: [nrhs][kmax + 2] coefficient of column j (0 beyond k)
   double2* ucoef = nullptr; // [nrhs][4] coefficients of the next update, written with alpha_j:
                             // sv_j alpha_j, sv_{j-1} beta_{j-1}, sw_j conj(alpha_j), delta_{j-1} sw_{j-1}
 };

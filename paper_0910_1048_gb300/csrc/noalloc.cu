@@ -91,6 +91,7 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   OVL_REQUIRE(lat && p && b && x, "apply_sign_noalloc: NULL argument");
   OVL_REQUIRE(p->method == OVL_DIRECT_2SL, "apply_sign_noalloc: only the direct two-sided Lanczos method");
   OVL_REQUIRE(!p->host_io, "apply_sign_noalloc: b and x must be device buffers");
+  OVL_REQUIRE(!p->two_pass, "apply_sign_noalloc: the two-pass mode is not available here");
   OVL_REQUIRE(nrhs >= 1 && nrhs <= 64, "apply_sign_noalloc: nrhs must be in [1, 64]");
   OVL_REQUIRE(p->precision >= OVL_PREC_F64 && p->precision <= OVL_PREC_F32_F16LINKS, "apply_sign_noalloc: precision");
   OVL_REQUIRE(2.0 * p->m_W + 8.0 != 0.0, "apply_sign_noalloc: m_W = -4 has no kappa");
@@ -150,6 +151,7 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   lz.kmax = kmax;
   lz.nrhs = nrhs;
   lz.nblk = nblk;
+  lz.vcols = kmax + 1;  // the whole basis
   lz.j = (int*)(base + o_j);
   lz.status = (int*)(base + o_st);
   lz.sv = (double*)(base + o_sv);

@@ -26,7 +26,7 @@ ovl_status small_sign(int k, const std::complex<double>* al, const std::complex<
 void set_sign_concurrency(int n);
 
 struct DirectWS {
-  int nrhs = 0, kmax = 0, f64 = -1, m = 0, vol = 0, prio = 0;
+  int nrhs = 0, kmax = 0, f64 = -1, m = 0, vol = 0, prio = 0, two_pass = 0;
   LzDev lz;
   LzVecs vec;
   void* dev_block = nullptr;  // one allocation for everything
@@ -37,6 +37,8 @@ struct DirectWS {
   int* kr = nullptr;          // [nrhs] Krylov dimension per rhs for the combine
   double2* bdev = nullptr;    // staging for host b / x
   double2* xdev = nullptr;
+  double2* xacc = nullptr;    // two-pass: [nrhs][12][V] FP64 accumulator of the second pass
+  double2* xcoef = nullptr;   // two-pass: [nrhs][kmax+2] coefficient of basis column j
   // pinned host mirrors of the device scalars, double-buffered: the copies behind one
   // chunk's event never overwrite the snapshot the host is reading
   struct Mirror {
@@ -51,8 +53,8 @@ struct DirectWS {
   } h[2];
   void* h_block = nullptr;
   bool pageable = false;  // server views: host mirrors in pageable memory (no pinned alloc/free)
-  // two graphs of `gchunk` steps (alternating chunks); each records timing events around
-  // its first step's pair stencil (tev[q][0..1]) and update (tev[q][2..3])
+  // two graphs of `gchunk - 1` steps (alternating chunks); graph q records timing events around
+  // its middle step's pair stencil (tev[q][0..1]) and update (tev[q][2..3])
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaEvent_t tev[2][4] = {};
   int gchunk = 0;
@@ -93,10 +95,11 @@ void free_direct_ws(DirectWS* w) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int m, int prio) {
+static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int m, int prio, bool two_pass) {
   DirectWS* w = lat->dws;
   const int vol = lat->g.vol;
-  if (w && w->nrhs == nrhs && w->kmax == kmax && w->f64 == (int)f64 && w->m >= m && w->vol == vol && w->prio == prio)
+  if (w && w->nrhs == nrhs && w->kmax == kmax && w->f64 == (int)f64 && w->m >= m && w->vol == vol && w->prio == prio &&
+      w->two_pass == (int)two_pass)
     return OVL_OK;
   free_direct_ws(w);
   lat->dws = nullptr;
@@ -107,7 +110,9 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   w->m = m;
   w->vol = vol;
   w->prio = prio;
+  w->two_pass = two_pass;
   const size_t n = (size_t)12 * vol;
+  const int vcols = two_pass ? 3 : kmax + 1;  // the two-pass mode keeps a window of three columns
   const size_t elt = f64 ? 16 : 8;
   const int nblk = partial_slots(lat->g);  // the most blocks of any reduction kernel
   const int ks = kmax + 2;
@@ -118,7 +123,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
     off += align256(bytes);
     return o;
   };
-  size_t o_vh = take((size_t)nrhs * (kmax + 1) * n * elt);
+  size_t o_vh = take((size_t)nrhs * vcols * n * elt);
   size_t o_wh = take((size_t)2 * nrhs * n * elt);
   size_t o_av = take((size_t)nrhs * n * elt);
   size_t o_aw = take((size_t)nrhs * n * elt);
@@ -144,6 +149,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   size_t o_n1 = take((size_t)nrhs * kmax * 16), o_n2 = take((size_t)nrhs * kmax * 16);
   size_t o_nk = take((size_t)nrhs * 4), o_np = take((size_t)nrhs * 2 * vec_blocks(lat->g) * 8);
   size_t o_nc = take((size_t)nrhs * 4), o_no = take((size_t)nrhs * 2 * 8);
+  size_t o_xa = take(two_pass ? (size_t)nrhs * n * 16 : 0), o_xc = take(two_pass ? (size_t)nrhs * ks * 16 : 0);
   // stream priority: 0 the default; p > 0 asks for p levels more urgent (numerically lower,
   // clamped to the device's range), so that concurrent solves can favour the longest one
   int least = 0, greatest = 0;
@@ -176,6 +182,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   lz.kmax = kmax;
   lz.nrhs = nrhs;
   lz.nblk = nblk;
+  lz.vcols = vcols;
   lz.j = (int*)(base + o_j);
   lz.status = (int*)(base + o_st);
   lz.sv = (double*)(base + o_sv);
@@ -200,6 +207,10 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   w->npart = (double*)(base + o_np);
   w->ncount = (unsigned*)(base + o_nc);
   w->nout = (double*)(base + o_no);
+  if (two_pass) {
+    w->xacc = (double2*)(base + o_xa);
+    w->xcoef = (double2*)(base + o_xc);
+  }
   if (cudaMemsetAsync(lz.count, 0, (size_t)nrhs * 4, w->stream) != cudaSuccess ||
       cudaMemsetAsync(w->ncount, 0, (size_t)nrhs * 4, w->stream) != cudaSuccess) {
     free_direct_ws(w);
@@ -315,6 +326,23 @@ static ovl_status estimate_changes(DirectWS* w, const Geom& g, bool f64, const L
   const int nrhs = w->nrhs, kmax = w->kmax;
   const size_t ks = (size_t)kmax + 2;
   const DirectWS::Mirror& h = w->h[q];
+  if (w->two_pass) {
+    // no stored basis: the change is measured with the column norms |v_i| as if the columns were
+    // orthogonal, sum |dy_i|^2 |v_i|^2 / sum |y_i|^2 |v_i|^2
+    for (int r : which) {
+      RhsState& s = rs[r];
+      if (s.k < 1 || s.yprev.empty()) continue;
+      double num = 0, den = 0;
+      for (int i = 0; i < s.k; ++i) {
+        const std::complex<double> pv = i < (int)s.yprev.size() ? s.yprev[i] : 0.0;
+        const double vn2 = h.vnorm[r * ks + i + 1] * h.vnorm[r * ks + i + 1];
+        num += std::norm(s.y[i] - pv) * vn2;
+        den += std::norm(s.y[i]) * vn2;
+      }
+      s.est = den > 0 ? std::sqrt(num / den) : 1e300;
+    }
+    return OVL_OK;
+  }
   std::vector<double2> d1((size_t)nrhs * kmax, make_double2(0, 0)), d2 = d1;
   std::vector<int> kr(nrhs, 0);
   bool any = false;
@@ -362,7 +390,8 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
     m = lat->src()->defl.m;
   }
   const int kmax = p->fixed_k > 0 ? p->fixed_k : p->k_max;
-  OVL_TRY(ensure_ws(lat, nrhs, kmax, f64, m, p->priority));
+  const bool two_pass = p->two_pass != 0;
+  OVL_TRY(ensure_ws(lat, nrhs, kmax, f64, m, p->priority, two_pass));
   DirectWS* w = lat->dws;
   cudaStream_t st = w->stream;
   const Geom& g = lat->g;
@@ -438,25 +467,32 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
     if (tev && (e = cudaEventRecord(tev[3], st))) return e;
     return cudaSuccess;
   };
-  // a chunk = one step launched directly on the stream with timing events around its two
-  // kernels, then a CUDA graph of the chunk's other steps (re-captured when they change)
+  // a chunk = one step launched directly on the stream, then a CUDA graph of the chunk's other
+  // steps (re-captured when they change). The chunks alternate between two graphs, each recording
+  // timing events (tev[q]) around the two kernels of its middle step, so the sampled launches are
+  // steady-state ones inside a busy stream; a chunk without a graph records them around its first
+  // step instead.
   bool use_graph = p->use_graphs != 0 && chunk > 1;
-  if (use_graph && !(w->graph[0] && w->gchunk == chunk && w->g_mw == p->m_W && w->g_mu == p->mu && w->g_lf == lf)) {
-    if (w->graph[0]) cudaGraphExecDestroy(w->graph[0]);
-    w->graph[0] = nullptr;
-    cudaGraph_t gr;
-    OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    for (int i = 1; i < chunk && e == cudaSuccess; ++i) e = step(nullptr);
-    cudaError_t e2 = cudaStreamEndCapture(st, &gr);
-    if (e != cudaSuccess) {
-      set_error("apply_sign: capture failed: %s", cudaGetErrorString(e));
-      return OVL_ECUDA;
+  if (use_graph && !(w->graph[0] && w->graph[1] && w->gchunk == chunk && w->g_mw == p->m_W && w->g_mu == p->mu &&
+                     w->g_lf == lf)) {
+    const int mid = std::max(1, chunk / 2);
+    for (int q = 0; q < 2; ++q) {
+      if (w->graph[q]) cudaGraphExecDestroy(w->graph[q]);
+      w->graph[q] = nullptr;
+      cudaGraph_t gr;
+      OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      for (int i = 1; i < chunk && e == cudaSuccess; ++i) e = step(i == mid ? w->tev[q] : nullptr);
+      cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+      if (e != cudaSuccess) {
+        set_error("apply_sign: capture failed: %s", cudaGetErrorString(e));
+        return OVL_ECUDA;
+      }
+      OVL_CHECK_CUDA(e2);
+      e = cudaGraphInstantiate(&w->graph[q], gr, 0);
+      cudaGraphDestroy(gr);
+      OVL_CHECK_CUDA(e);
     }
-    OVL_CHECK_CUDA(e2);
-    e = cudaGraphInstantiate(&w->graph[0], gr, 0);
-    cudaGraphDestroy(gr);
-    OVL_CHECK_CUDA(e);
     w->gchunk = chunk;
     w->g_mw = p->m_W;
     w->g_mu = p->mu;
@@ -465,16 +501,17 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   int launches = 1 + (m > 0 ? 1 : 0) + 1;  // start (+ deflation dots) and the combine
   auto run_steps = [&](int nsteps, int q) -> cudaError_t {
     launches += 2 * nsteps;
-    cudaError_t e = step(w->tev[q]);
+    const bool graph = use_graph && nsteps == chunk;
+    cudaError_t e = step(graph ? nullptr : w->tev[q]);
     if (e != cudaSuccess || nsteps == 1) return e;
-    if (use_graph && nsteps == chunk) return cudaGraphLaunch(w->graph[0], st);
+    if (graph) return cudaGraphLaunch(w->graph[q], st);
     for (int i = 1; i < nsteps; ++i)
       if ((e = step(nullptr)) != cudaSuccess) return e;
     return cudaSuccess;
   };
   double t_pair = 0, t_upd = 0;
   int nsamp = 0;
-  auto sample = [&](int q) {  // durations of the first step of the chunk behind slot q
+  auto sample = [&](int q) {  // durations of the sampled step of the chunk behind slot q
     float a = 0, b = 0;
     if (cudaEventElapsedTime(&a, w->tev[q][0], w->tev[q][1]) == cudaSuccess &&
         cudaEventElapsedTime(&b, w->tev[q][2], w->tev[q][3]) == cudaSuccess) {
@@ -661,7 +698,43 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   OVL_CHECK_CUDA(cudaMemcpyAsync(w->coef, coef.data(), coef.size() * 16, cudaMemcpyHostToDevice, st));
   OVL_CHECK_CUDA(cudaMemcpyAsync(w->kr, kr.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
   double2* xd = p->host_io ? w->xdev : x;
-  OVL_CHECK_CUDA(launch_lanczos_combine(g, f64, w->lz, vec, w->kr, w->coef, kmax, xd, st));
+  if (!two_pass) {
+    OVL_CHECK_CUDA(launch_lanczos_combine(g, f64, w->lz, vec, w->kr, w->coef, kmax, xd, st));
+  } else {
+    // second pass (the two-pass strategy of Section 2.3): the same start and steps regenerate
+    // vhat_1..vhat_k bit for bit (fixed-order reductions), and each column is added to x with its
+    // coefficient as it appears; a right-hand side retires once its k columns are in
+    std::vector<double2> xc((size_t)nrhs * ks, make_double2(0, 0));
+    int kmax2 = 0;
+    for (int r = 0; r < nrhs; ++r) {
+      for (int i = 0; i < rs[r].k; ++i) xc[(size_t)r * ks + i + 1] = coef[(size_t)r * kmax + i];
+      kmax2 = std::max(kmax2, rs[r].k);
+    }
+    OVL_CHECK_CUDA(cudaMemcpyAsync(w->xcoef, xc.data(), xc.size() * 16, cudaMemcpyHostToDevice, st));
+    OVL_CHECK_CUDA(cudaMemsetAsync(w->xacc, 0, (size_t)nrhs * n * 16, st));
+    LzDev lz2 = w->lz;
+    lz2.xacc = w->xacc;
+    lz2.xcoef = w->xcoef;
+    OVL_CHECK_CUDA(launch_lanczos_start(g, f64, lz2, vec, bd, m, lat->src()->defl.R, lat->src()->defl.L, w->lam_sign,
+                                        w->dots, st));
+    launches += 1 + (m > 0 ? 1 : 0);
+    auto retire = [&](int jdone) -> cudaError_t {  // rhs whose last column is jdone
+      for (int r = 0; r < nrhs; ++r)
+        if (rs[r].k == jdone) {
+          cudaError_t e = cudaMemsetAsync(w->lz.status + r, 2, sizeof(int), st);
+          if (e != cudaSuccess) return e;
+        }
+      return cudaSuccess;
+    };
+    OVL_CHECK_CUDA(retire(1));
+    for (int j = 1; j < kmax2; ++j) {  // step j adds column j + 1
+      OVL_CHECK_CUDA(launch_lanczos_pair(g, U, lf, f64, p->m_W, p->mu, lz2, vec, st));
+      OVL_CHECK_CUDA(launch_lanczos_update(g, f64, lz2, vec, st));
+      launches += 2;
+      OVL_CHECK_CUDA(retire(j + 1));
+    }
+    OVL_CHECK_CUDA(launch_ms_finish(g, nrhs, w->xacc, vec.xp, xd, st));
+  }
   if (p->host_io) OVL_CHECK_CUDA(cudaMemcpyAsync(x, w->xdev, (size_t)nrhs * n * 16, cudaMemcpyDeviceToHost, st));
   OVL_CHECK_CUDA(cudaStreamSynchronize(st));
   double t_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();

@@ -338,20 +338,26 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
   const Links U = lat->src()->links();
   const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 20, p->k_max));
   const bool use_graph = p->use_graphs != 0 && chunk > 1;
-  if (use_graph && !(w->graph[0] && w->gchunk == chunk && w->g_lf == lf && w->g_mw == p->m_W && w->g_mu == p->mu &&
-                     w->g_s1 == s1 && w->g_tol == ms.tol)) {
-    if (w->graph[0]) cudaGraphExecDestroy(w->graph[0]);
-    w->graph[0] = nullptr;
-    cudaGraph_t gr;
-    OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    for (int i = 1; i < chunk && e == cudaSuccess; ++i) e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st);
-    cudaError_t e2 = cudaStreamEndCapture(st, &gr);
-    OVL_CHECK_CUDA(e);
-    OVL_CHECK_CUDA(e2);
-    e = cudaGraphInstantiate(&w->graph[0], gr, 0);
-    cudaGraphDestroy(gr);
-    OVL_CHECK_CUDA(e);
+  // the chunks alternate between two graphs; graph q records timing events (tev[q]) around its
+  // middle iteration, so the sampled launches are steady-state ones inside a busy stream
+  if (use_graph && !(w->graph[0] && w->graph[1] && w->gchunk == chunk && w->g_lf == lf && w->g_mw == p->m_W &&
+                     w->g_mu == p->mu && w->g_s1 == s1 && w->g_tol == ms.tol)) {
+    const int mid = std::max(1, chunk / 2);
+    for (int q = 0; q < 2; ++q) {
+      if (w->graph[q]) cudaGraphExecDestroy(w->graph[q]);
+      w->graph[q] = nullptr;
+      cudaGraph_t gr;
+      OVL_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      for (int i = 1; i < chunk && e == cudaSuccess; ++i)
+        e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st, i == mid ? w->tev[q] : nullptr);
+      cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+      OVL_CHECK_CUDA(e);
+      OVL_CHECK_CUDA(e2);
+      e = cudaGraphInstantiate(&w->graph[q], gr, 0);
+      cudaGraphDestroy(gr);
+      OVL_CHECK_CUDA(e);
+    }
     w->gchunk = chunk;
     w->g_lf = lf;
     w->g_mw = p->m_W;
@@ -360,12 +366,13 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
     w->g_tol = ms.tol;
   }
   int launches = 1 + (m > 0 ? 1 : 0) + 2;  // start (+ deflation dots), final stencil and finish
-  // a chunk = one iteration launched directly with timing events, then a graph of the rest
+  // a chunk = one iteration launched directly, then a graph of the rest (events: see above)
   auto run_chunk = [&](int ns, int q) -> cudaError_t {
     launches += 4 * ns;
-    cudaError_t e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st, w->tev[q]);
+    const bool graph = use_graph && ns == chunk;
+    cudaError_t e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st, graph ? nullptr : w->tev[q]);
     if (e != cudaSuccess || ns == 1) return e;
-    if (use_graph && ns == chunk) return cudaGraphLaunch(w->graph[0], st);
+    if (graph) return cudaGraphLaunch(w->graph[q], st);
     for (int i = 1; i < ns; ++i)
       if ((e = launch_ms_step(g, U, lf, f64, p->m_W, p->mu, ms, v, st)) != cudaSuccess) return e;
     return cudaSuccess;

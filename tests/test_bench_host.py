@@ -6,7 +6,7 @@ import bench
 def test_workloads_consistent():
     for name, wl in bench.WORKLOADS.items():
         assert len(wl["dims"]) == 4 and all(d % 2 == 0 for d in wl["dims"]), name
-        assert wl["method"] in ("direct", "multishift") and wl["precision"] in ("f64", "f32", "f16"), name
+        assert wl["method"] in ("direct", "multishift", "fom") and wl["precision"] in ("f64", "f32", "f16"), name
         if wl["precision"] == "f16":
             assert wl["method"] == "multishift", "FP16 links only under the multishift's FP64 reliable updates"
     for name, comps in bench.COMPANIONS.items():

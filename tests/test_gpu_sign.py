@@ -286,3 +286,32 @@ def test_sampled_stopping_estimate_1212(ovl, ctx):
     acc = 0.5 * np.linalg.norm(x2 - b) / np.linalg.norm(b)
     assert acc < 3e-5, (acc, info[0]["iterations"], info2[0]["iterations"])
     ovl.ovl_destroy_lattice(lat)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_two_pass_equals_one_pass(ovl, ctx, p4, prec):
+    """The two-pass strategy (Section 2.3): the second pass regenerates the first pass's vectors bit
+    for bit, so at the same k (two sources, 16 deflated eigenpairs) x equals the one-pass result to
+    rounding of the accumulation (1e-12)."""
+    lat = _lat(ovl, ctx, p4["dims"], p4["links"])
+    ovl.ovl_set_deflation(lat, -2.0, 0.3, p4["R16"].T.copy(), p4["L16"].T.copy(), p4["lam16"])
+    b = synth.gaussian_source(p4["dims"], 91, nrhs=2)
+    pr = ovl.OVL_PREC_F64 if prec == "f64" else ovl.OVL_PREC_F32
+    kw = dict(mu=0.3, fixed_k=150, precision=pr, use_deflation=1, check_every=10)
+    st1, i1, x1 = _solve(ovl, lat, b, **kw)
+    st2, i2, x2 = _solve(ovl, lat, b, two_pass=1, **kw)
+    ovl.ovl_destroy_lattice(lat)
+    assert st1 == st2 == ovl.OVL_OK
+    assert [i["iterations"] for i in i1] == [i["iterations"] for i in i2] == [150, 150]
+    for r in range(2):
+        assert _rel(x2[r], x1[r]) < 1e-12
+
+
+def test_two_pass_converged_vs_dense(ovl, ctx, p4):
+    """Two-pass with its own stop test (the change of y weighted by the column norms) reaches the
+    dense x* at 4^4 like the one-pass solve."""
+    lat = _lat(ovl, ctx, p4["dims"], p4["links"], ovl.OVL_F64)
+    st, info, x = _solve(ovl, lat, p4["b"], mu=0.3, tol=3e-11, k_max=1500, check_every=25, two_pass=1)
+    ovl.ovl_destroy_lattice(lat)
+    assert st == ovl.OVL_OK, info
+    assert _rel(x, p4["xstar"]) < 1e-9
