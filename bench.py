@@ -676,32 +676,32 @@ SERVING = dict(sizes=(4, 8, 12, 16), fields_per_size=5, tols=(1e-6, 1e-8, 1e-10)
                mean_interarrival_s=0.25)
 
 
-def serving_sample(ovl, ctx, n_requests, mem_budget=200 << 30, max_slots=8):
-    """A bounded sample of the serving stream: Poisson arrivals of sign(H_W(mu)) b requests on 20
-    resident gauge fields (5 per lattice size 4^4, 8^4, 12^4, 16^4, seeds 0-19), mu ~ U[0, 1],
-    tol in {1e-6, 1e-8, 1e-10}, 1-8 Gaussian sources each (seed 42), FP64 direct method, admitted
-    by device-memory footprint (ovl_submit / ovl_poll). Latency = completion - arrival."""
+def _serving_stream(n_requests):
+    """The first n requests of the serving stream (seed 42): field index uniform over 20 resident
+    fields (5 per lattice size 4^4, 8^4, 12^4, 16^4), mu ~ U[0, 1], tol in {1e-6, 1e-8, 1e-10}, 1-8
+    Gaussian sources (seed 2000 + request), exponential inter-arrival gaps of unit mean (scaled by
+    the run's rate)."""
+    cfg = SERVING
+    rng = np.random.default_rng(cfg["seed"])
+    nf = len(cfg["sizes"]) * cfg["fields_per_size"]
+    reqs = []
+    for i in range(n_requests):
+        fi = int(rng.integers(0, nf))
+        L = cfg["sizes"][fi // cfg["fields_per_size"]]
+        nrhs = int(rng.integers(1, cfg["nrhs_max"] + 1))
+        reqs.append(dict(i=i, fi=fi, L=L, nrhs=nrhs, mu=float(rng.uniform(0.0, 1.0)),
+                         tol=float(rng.choice(cfg["tols"])), gap=float(rng.exponential(1.0))))
+    return reqs
+
+
+def _serving_run(ovl, srv, ids, reqs, mean_gap_s):
+    """Submit `reqs` with gaps gap * mean_gap_s (0: all at once) and poll until every one is done.
+    Returns (done list of (request, latency_s, status, info), wall seconds)."""
     import synth
 
     cfg = SERVING
-    rng = np.random.default_rng(cfg["seed"])
-    lats, ids = [], []
-    srv = ovl.ovl_server_create(ctx, mem_budget, max_slots=max_slots)
-    for si, L in enumerate(cfg["sizes"]):
-        for f in range(cfg["fields_per_size"]):
-            dims = (L, L, L, L)
-            lat = ovl.ovl_create_lattice(ctx, dims, -1)
-            ovl.ovl_set_links(lat, synth.gauge_links(dims, si * cfg["fields_per_size"] + f), ovl.OVL_F64)
-            lats.append((L, lat))
-            ids.append(ovl.ovl_server_add_field(srv, lat))
-    reqs = []
-    for i in range(n_requests):
-        fi = int(rng.integers(0, len(lats)))
-        L = lats[fi][0]
-        nrhs = int(rng.integers(1, cfg["nrhs_max"] + 1))
-        reqs.append(dict(fi=fi, L=L, nrhs=nrhs, mu=float(rng.uniform(0.0, 1.0)), tol=float(rng.choice(cfg["tols"])),
-                         gap=float(rng.exponential(cfg["mean_interarrival_s"])),
-                         b=synth.gaussian_source((L,) * 4, 2000 + i, nrhs=nrhs)))
+    for r in reqs:  # sources made before the clock starts
+        r["b"] = synth.gaussian_source((r["L"],) * 4, 2000 + r["i"], nrhs=r["nrhs"])
     pending, done = {}, []
     t_start = time.perf_counter()
     t_next = t_start
@@ -715,7 +715,7 @@ def serving_sample(ovl, ctx, n_requests, mem_budget=200 << 30, max_slots=8):
             pending[tk] = (r, now)
             i += 1
             if i < len(reqs):
-                t_next += reqs[i]["gap"]
+                t_next += reqs[i]["gap"] * mean_gap_s
         for tk in list(pending):
             r, t0 = pending[tk]
             st, info = ovl.ovl_poll(srv, tk, r["nrhs"], None)
@@ -724,9 +724,12 @@ def serving_sample(ovl, ctx, n_requests, mem_budget=200 << 30, max_slots=8):
                 del pending[tk]
         time.sleep(0.001)
     wall = time.perf_counter() - t_start
-    ovl.ovl_server_destroy(srv)
-    for _, lat in lats:
-        ovl.ovl_destroy_lattice(lat)
+    for r in reqs:
+        r.pop("b", None)
+    return done, wall
+
+
+def _serving_stats(ovl, done, wall):
     lat_ms = sorted(1e3 * d for _, d, _, _ in done)
     ok = sum(1 for r, _, _, info in done for inf in info[:r["nrhs"]] if inf["status"] == ovl.OVL_OK)
     sources = sum(r["nrhs"] for r, _, _, _ in done)
@@ -735,12 +738,90 @@ def serving_sample(ovl, ctx, n_requests, mem_budget=200 << 30, max_slots=8):
         per_size.setdefault("%d^4" % r["L"], []).append(1e3 * d)
     return {"requests": len(done), "sources": sources, "wall_s": wall, "solves_per_s": sources / wall,
             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-            "success_rate": ok / max(1, sources), "precision": "f64", "method": "direct",
-            "p50_ms_by_size": {k: float(np.percentile(v, 50)) for k, v in sorted(per_size.items())},
-            "sample": "%d requests of the 2000-request stream's distribution (Poisson, mean gap %g s)"
-                      % (n_requests, cfg["mean_interarrival_s"]), "mem_budget_bytes": mem_budget,
-            "max_slots": max_slots, "k_max_by_tol": {"%g" % k: v for k, v in cfg["k_max_by_tol"].items()},
-            "k_max_cap": {"%d^4" % k: v for k, v in cfg["k_max_cap"].items()}}
+            "success_rate": ok / max(1, sources),
+            "p50_ms_by_size": {k: float(np.percentile(v, 50)) for k, v in sorted(per_size.items())}}
+
+
+def _serving_server(ovl, ctx, mem_budget, max_slots):
+    import synth
+
+    cfg = SERVING
+    lats, ids = [], []
+    srv = ovl.ovl_server_create(ctx, mem_budget, max_slots=max_slots)
+    for si, L in enumerate(cfg["sizes"]):
+        for f in range(cfg["fields_per_size"]):
+            dims = (L, L, L, L)
+            lat = ovl.ovl_create_lattice(ctx, dims, -1)
+            ovl.ovl_set_links(lat, synth.gauge_links(dims, si * cfg["fields_per_size"] + f), ovl.OVL_F64)
+            lats.append(lat)
+            ids.append(ovl.ovl_server_add_field(srv, lat))
+    return srv, lats, ids
+
+
+def serving_sample(ovl, ctx, n_requests, mem_budget=200 << 30, max_slots=8):
+    """A bounded sample of the serving stream: the first n requests, Poisson arrivals with a mean gap
+    of SERVING['mean_interarrival_s'], FP64 direct method, admitted by device-memory footprint
+    (ovl_submit / ovl_poll). Latency = completion - arrival."""
+    cfg = SERVING
+    srv, lats, ids = _serving_server(ovl, ctx, mem_budget, max_slots)
+    done, wall = _serving_run(ovl, srv, ids, _serving_stream(n_requests), cfg["mean_interarrival_s"])
+    ovl.ovl_server_destroy(srv)
+    for lat in lats:
+        ovl.ovl_destroy_lattice(lat)
+    res = _serving_stats(ovl, done, wall)
+    res.update({"precision": "f64", "method": "direct",
+                "sample": "%d requests of the 2000-request stream (Poisson, mean gap %g s)"
+                          % (n_requests, cfg["mean_interarrival_s"]), "mem_budget_bytes": mem_budget,
+                "max_slots": max_slots, "k_max_by_tol": {"%g" % k: v for k, v in cfg["k_max_by_tol"].items()},
+                "k_max_cap": {"%d^4" % k: v for k, v in cfg["k_max_cap"].items()}})
+    return res
+
+
+def run_serving(args):
+    """The serving configuration as its own line: the first `--serving-requests` requests of the
+    2000-request stream (seed 42) all submitted at once (the saturation throughput S, sources/s),
+    then the same requests with Poisson arrivals at 0.5 S and 0.9 S (mean gap = mean sources per
+    request / rate). value = solves/s of the 0.9 S run; p50 / p99 latency of each run."""
+    import torch
+
+    import paper_0910_1048_gb300 as ovl
+
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    ctx = ovl.ovl_ctx_create(local)
+    n = args.serving_requests if args.serving_requests > 0 else 200
+    reqs = _serving_stream(n)
+    mean_src = float(np.mean([r["nrhs"] for r in reqs]))
+    srv, lats, ids = _serving_server(ovl, ctx, 200 << 30, 8)
+    with ClockSampler(local) as clk:
+        done, wall = _serving_run(ovl, srv, ids, reqs, 0.0)
+        sat = _serving_stats(ovl, done, wall)
+        runs = {}
+        for frac in (0.5, 0.9):
+            rate = frac * sat["solves_per_s"]  # sources per second
+            d2, w2 = _serving_run(ovl, srv, ids, reqs, mean_src / rate)
+            runs["%.1fx" % frac] = dict(_serving_stats(ovl, d2, w2), offered_sources_per_s=rate)
+    ovl.ovl_server_destroy(srv)
+    for lat in lats:
+        ovl.ovl_destroy_lattice(lat)
+    ovl.ovl_ctx_destroy(ctx)
+    main_run = runs["0.9x"]
+    res = {
+        "metric": "sgn(H_W)b serving solves/s; p50/p99 latency", "value": main_run["solves_per_s"],
+        "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * main_run["wall_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: 20 fields (seeds 0-19), Gaussian sources seed 2000+request",
+        "config": {"workload": "serving", "requests": n, "of_stream": 2000, "seed": SERVING["seed"],
+                   "sizes": ["%d^4" % L for L in SERVING["sizes"]], "mu": "U[0,1]", "tols": list(SERVING["tols"]),
+                   "nrhs": "1-%d" % SERVING["nrhs_max"], "mem_budget_bytes": 200 << 30, "max_slots": 8,
+                   "method": "direct", "precision": "f64", "parallelism": "single"},
+        "saturation": sat, "runs": runs, "p50_ms": main_run["p50_ms"], "p99_ms": main_run["p99_ms"],
+        "clocks": clk.summary(),
+        "e2e": {"value": main_run["solves_per_s"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(res))
 
 
 def _oracle_inputs(wl, mu):
@@ -901,7 +982,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving"], default=DEFAULT_WORKLOAD)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=16,
@@ -921,6 +1002,13 @@ def main():
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.workload == "serving":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the serving stream has no oracle counterpart "
+                              "(the oracle is timed per solve by the other workloads)"}))
+        else:
+            run_serving(args)
         return
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

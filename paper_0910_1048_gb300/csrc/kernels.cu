@@ -493,8 +493,8 @@ __global__ void __launch_bounds__(2 * PS) k_lz_pair(Geom g, Links U, HopCoef<R> 
 // The same step with 8 threads per site (small lattices): see pair_split. Each thread finishes
 // one spin (three colours) of its site: scale, gamma5, store, and for the v half the partial of
 // alpha_j.
-template <class R, int LF>
-__global__ void __launch_bounds__(8 * kSplitSites) k_lz_pair_split(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm,
+template <class R, int LF, int MINB = 1>
+__global__ void __launch_bounds__(8 * kSplitSites, MINB) k_lz_pair_split(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm,
                                                                    LzDev lz, const typename V2<R>::T* vh,
                                                                    const typename V2<R>::T* wh,
                                                                    typename V2<R>::T* av, typename V2<R>::T* aw) {
@@ -682,6 +682,17 @@ cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64,
     else
       e = launch_plain(k_lz_pair_split<float, LINK_F32>, grid, block, st, g, U, fp, fm, lz, fv, fw, (float2*)vec.av,
                      (float2*)vec.aw);
+  } else if (variant == 4) {  // the split kernel held to 128 registers: two blocks per SM
+    dim3 grid((g.vol + kSplitSites - 1) / kSplitSites, lz.nrhs), block(kSplitSites, 8);
+    if (f64)
+      e = launch_plain(k_lz_pair_split<double, LINK_F64, 2>, grid, block, st, g, U, dp, dm, lz, dv, dw,
+                       (double2*)vec.av, (double2*)vec.aw);
+    else if (lf == LINK_F16R12)
+      e = launch_plain(k_lz_pair_split<float, LINK_F16R12, 2>, grid, block, st, g, U, fp, fm, lz, fv, fw,
+                       (float2*)vec.av, (float2*)vec.aw);
+    else
+      e = launch_plain(k_lz_pair_split<float, LINK_F32, 2>, grid, block, st, g, U, fp, fm, lz, fv, fw,
+                       (float2*)vec.av, (float2*)vec.aw);
   } else if (variant == 2) {
     e = pair_unsplit<48>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
   } else if (variant == 3) {

@@ -30,11 +30,11 @@ inline cudaError_t launch_plain(void (*kern)(KArgs...), dim3 grid, dim3 block, c
 
 // Pair-stencil variant chosen by the autotuner for (volume, precision): -1 none yet,
 // 0 one thread per site (64 sites per block), 1 split over 8 threads, 2 / 3 one thread per site
-// with 48 / 32 sites per block (the multishift kernels run variants 0, 2, 3 as 0). Thread-safe,
-// process-wide. (A 16-thread split,
+// with 48 / 32 sites per block, 4 split held to 128 registers (two blocks per SM); the multishift
+// kernels run variants 0, 2, 3 as 0 and 4 as 1. Thread-safe, process-wide. (A 16-thread split,
 // one hop per thread, measured 54 us against 32 us for FP64 at 8^4: more index and reduction
 // work than the extra warps hide.)
-constexpr int kPairVariants = 4;
+constexpr int kPairVariants = 5;
 int tuned_pair_variant(int vol, int prec);
 // Returns the variant for the key, running `measure` (which returns 0 or 1) under the table's
 // lock the first time, so that every solve in the process uses one decision per key.

@@ -432,21 +432,21 @@ static cudaError_t ms_step_t(const Geom& g, const Links& U, double m_w, double m
   HopCoef<R> cp = hop_coef<R>(m_w, mu), cm = hop_coef<R>(m_w, -mu);
   dim3 sgrid((g.vol + kSplitSites - 1) / kSplitSites, ms.nrhs), sblock(kSplitSites, 8);
   const int tv = tuned_pair_variant(g.vol, sizeof(R) == 8 ? 0 : LF);
-  const bool split = tv < 0 ? use_split(g) : tv == 1;
+  const bool split = tv < 0 ? use_split(g) : (tv == 1 || tv == 4);
   const int elt = vec_elts(g, ms.nrhs, sizeof(R) == 8);
   cudaError_t e;
-  if (ev) cudaEventRecord(ev[0], st);
+  if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
   e = split ? launch_plain(k_ms_pair_split<R, LF, 0>, sgrid, sblock, st, g, U, cp, cm, ms, v)
             : launch_plain(k_ms_pair<R, LF, 0>, pgrid, pblock, st, g, U, cp, cm, ms, v);
   if (e) return e;
-  if (ev) cudaEventRecord(ev[1], st);
+  if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
   e = split ? launch_plain(k_ms_pair_split<R, LF, 1>, sgrid, sblock, st, g, U, cp, cm, ms, v)
             : launch_plain(k_ms_pair<R, LF, 1>, pgrid, pblock, st, g, U, cp, cm, ms, v);
   if (e) return e;
   if ((e = launch_plain(k_ms_update<R>, dim3(vec_blocks(g, elt), ms.nrhs), dim3(kVecBlock), st, g, ms, v, elt))) return e;
-  if (ev) cudaEventRecord(ev[2], st);
+  if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
   if ((e = launch_plain(k_ms_dirs<R>, grid, dim3(kVecBlock), st, g, ms, v))) return e;
-  if (ev) cudaEventRecord(ev[3], st);
+  if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
   return cudaGetLastError();
 }
 

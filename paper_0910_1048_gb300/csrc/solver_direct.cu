@@ -459,12 +459,12 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   // one step, with timing events around its two launches when `tev` is given
   auto step = [&](cudaEvent_t* tev) -> cudaError_t {
     cudaError_t e;
-    if (tev && (e = cudaEventRecord(tev[0], st))) return e;
+    if (tev && (e = cudaEventRecordWithFlags(tev[0], st, cudaEventRecordExternal))) return e;
     if ((e = launch_lanczos_pair(g, U, lf, f64, p->m_W, p->mu, w->lz, vec, st))) return e;
-    if (tev && (e = cudaEventRecord(tev[1], st))) return e;
-    if (tev && (e = cudaEventRecord(tev[2], st))) return e;
+    if (tev && (e = cudaEventRecordWithFlags(tev[1], st, cudaEventRecordExternal))) return e;
+    if (tev && (e = cudaEventRecordWithFlags(tev[2], st, cudaEventRecordExternal))) return e;
     if ((e = launch_lanczos_update(g, f64, w->lz, vec, st))) return e;
-    if (tev && (e = cudaEventRecord(tev[3], st))) return e;
+    if (tev && (e = cudaEventRecordWithFlags(tev[3], st, cudaEventRecordExternal))) return e;
     return cudaSuccess;
   };
   // a chunk = one step launched directly on the stream, then a CUDA graph of the chunk's other

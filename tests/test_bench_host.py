@@ -51,3 +51,20 @@ def test_pair_bytes_count_links_once_per_batch():
 
 def test_throughput_counts_every_rank():
     assert bench.throughput(steps=5, solves_per_step=3, world=2, max_ms=1000.0) == 30.0
+
+
+def test_serving_stream_is_the_configured_distribution():
+    """The serving stream is deterministic (seed 42) and draws what the configuration states:
+    20 fields over four lattice sizes, mu in [0, 1], three tolerances, 1-8 sources, unit-mean gaps."""
+    import numpy as np
+
+    a = bench._serving_stream(2000)
+    b = bench._serving_stream(2000)
+    assert a == b and len(a) == 2000
+    assert {r["L"] for r in a} == set(bench.SERVING["sizes"])
+    assert {r["fi"] for r in a} == set(range(20))
+    assert all(r["L"] == bench.SERVING["sizes"][r["fi"] // 5] for r in a)
+    assert all(0.0 <= r["mu"] <= 1.0 for r in a) and {r["tol"] for r in a} == set(bench.SERVING["tols"])
+    assert {r["nrhs"] for r in a} == set(range(1, 9))
+    assert abs(np.mean([r["gap"] for r in a]) - 1.0) < 0.1
+    assert bench._serving_stream(200) == a[:200]  # a prefix is the first requests of the full stream
