@@ -510,19 +510,24 @@ def _roofline(wl, infos, fp64_peak, fp64_src):
     kernel = {"direct": "k_lz_pair", "multishift": "k_ms_pair", "fom": "k_dslash (two per Arnoldi step)"}[wl["method"]]
     nr = wl.get("nrhs", 1)
     traffic = TRAFFIC.get((kernel, prec, tuple(wl["dims"]), nr))
+    import paper_0910_1048_gb300 as ovl
+    code = {"f64": ovl.OVL_PREC_F64, "f32": ovl.OVL_PREC_F32, "f16": ovl.OVL_PREC_F32_F16LINKS}[prec]
+    shape = ovl.ovl_get_pair_variant(vol, code)  # the autotuner's pick (see ovl_set_pair_variant)
     if prec == "f64":
         flops = PAIR_FLOPS_PER_SITE * vol * nr
         ach = flops / (t_pair * 1e-3) / 1e12 if t_pair else None
         return {"kernel": kernel, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
                 "frac": (ach / fp64_peak) if ach else None, "traffic": traffic, "peak_source": fp64_src,
                 "algorithmic_flops_per_launch": flops,
-                "algorithmic_bytes_per_launch": pair_bytes("f64", vol, nr),
-                "note": "FP64 kernels are bound by GB300's FP64 pipe (ncu: FP64 pipe 65-74% active)"}
+                "algorithmic_bytes_per_launch": pair_bytes("f64", vol, nr), "pair_variant": shape,
+                "note": "FP64 kernels are bound by GB300's FP64 pipe (ncu at 12^4: FP64 pipe 84% of active "
+                        "cycles in the pair stencil, 66-72% in the update)"}
     byts = pair_bytes(prec, vol, nr)
     ach = byts / (t_pair * 1e-3) / 1e9 if t_pair else None
     return {"kernel": kernel, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": ach / peaks["hbm_gbs"] if ach else None, "traffic": traffic,
-            "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)", "algorithmic_bytes_per_launch": byts}
+            "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)", "algorithmic_bytes_per_launch": byts,
+            "pair_variant": shape}
 
 
 def _summary(wl, per_mu, infos, acc):
@@ -954,6 +959,8 @@ def run_profile_case(args):
     lat = ovl.ovl_create_lattice(ctx, dims, -1)
     ovl.ovl_set_links(lat, synth.gauge_links(dims, 0), ovl.OVL_F64 | ovl.OVL_F32 | ovl.OVL_F16R12)
     prec = {"f64": ovl.OVL_PREC_F64, "f32": ovl.OVL_PREC_F32, "f16": ovl.OVL_PREC_F32_F16LINKS}[args.prec]
+    if args.pair_variant >= 0:  # a pinned pair-stencil shape: no autotuner launches before the capture
+        ovl.ovl_set_pair_variant(L ** 4, prec, args.pair_variant)
     if args.profile_case == "dslash":
         dt = torch.complex128 if args.prec == "f64" else torch.complex64
         x = torch.randn(args.nrhs * 12 * L ** 4, dtype=dt, device="cuda")
@@ -999,6 +1006,8 @@ def main():
     ap.add_argument("--prec", choices=["f64", "f32", "f16"], default="f64", help="--profile-case: precision")
     ap.add_argument("--nrhs", type=int, default=1, help="--profile-case: right-hand sides")
     ap.add_argument("--fixed-k", type=int, default=40, help="--profile-case: Lanczos steps / BiCG iterations")
+    ap.add_argument("--pair-variant", type=int, default=-1,
+                    help="--profile-case: pin the pair-stencil shape (ovl_set_pair_variant); -1 autotunes")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)

@@ -195,6 +195,23 @@ void ovl_sign_params_default(ovl_sign_params* p);
 ovl_status ovl_apply_sign(ovl_lattice* lat, const ovl_sign_params* p, int32_t nrhs,
                           const void* b, void* x, ovl_sign_info* info, void* stream);
 
+/* Kernel shape of the two-sided Lanczos pair stencil (H(mu) v and H(-mu) w of one step of
+ * Algorithm 4, the dominant kernel of the direct method) for lattices of `volume` sites at
+ * `precision` (OVL_PREC_*): 0 one thread per site, 64 sites per block; 1 eight threads per site,
+ * 32 sites per block; 2 / 3 as 0 with 48 / 32 sites per block; 4 as 1 held to two blocks per SM;
+ * 5 eight threads per site, 16 sites per block, three blocks per SM; 6 one thread per site, 32
+ * sites per one-warp block computing one of the two stencils; 7 one thread per site, the warps of
+ * a grid that fills the GPU claiming 32-site tasks (one of the two stencils each) from a counter. The multishift method runs 1, 4, 5 as its eight-thread stencil and the others as its
+ * one-thread stencil. variant = -1
+ * clears the entry: the next direct solve for that key times every shape on its own vectors and
+ * keeps the fastest. Process-wide. All shapes compute the same step; results differ in the
+ * rounding of the partial sums of alpha_j only.
+ * Errors: EINVAL (variant outside -1..7, volume < 1, unknown precision). */
+ovl_status ovl_set_pair_variant(int64_t volume, int32_t precision, int32_t variant);
+
+/* The shape in use for (volume, precision); -1 if no solve has tuned it yet. */
+int32_t ovl_get_pair_variant(int64_t volume, int32_t precision);
+
 /* Allocation-free variant of ovl_apply_sign's direct method, for callers that cannot
  * allocate device memory: processes whose device memory belongs to another allocator (a
  * framework's pool, a server that reserves its budget at start-up) and latency-critical

@@ -96,6 +96,8 @@ _PROTOS = {
     "ovl_apply_sign": (_I, [_P, ctypes.POINTER(ovl_sign_params), _I, _P, _P, ctypes.POINTER(ovl_sign_info), _P]),
     "ovl_apply_sign_noalloc": (_I, [_P, ctypes.POINTER(ovl_sign_params), _I, _P, _P,
                                     ctypes.POINTER(ovl_sign_info), _P]),
+    "ovl_set_pair_variant": (_I, [ctypes.c_int64, _I, _I]),
+    "ovl_get_pair_variant": (_I, [ctypes.c_int64, _I]),
     "ovl_get_tridiag": (_I, [_P, _I, _I, ctypes.POINTER(_I), _P, _P, _P]),
     "ovl_small_sign": (_I, [_I, _P, _P, _P, _P, _I]),
     "ovl_rational_coeffs": (_I, [_I, _I, _D, _D, _D, _I, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
@@ -312,6 +314,17 @@ def ovl_apply_sign_noalloc(lat, params: ovl_sign_params, b, x, stream=None):
     if st in (OVL_EINVAL, OVL_ENOMEM, OVL_ECUDA):
         raise _err(st)
     return st, [i.as_dict() for i in infos]
+
+
+def ovl_set_pair_variant(volume: int, precision: int, variant: int):
+    """Pin (variant >= 0) or clear (-1) the pair-stencil shape for (volume, precision)."""
+    st = lib.ovl_set_pair_variant(volume, precision, variant)
+    if st != OVL_OK:
+        raise _err(st)
+
+
+def ovl_get_pair_variant(volume: int, precision: int) -> int:
+    return int(lib.ovl_get_pair_variant(volume, precision))
 
 
 def ovl_get_tridiag(lat, rhs: int = 0, k_cap: int = 100000):

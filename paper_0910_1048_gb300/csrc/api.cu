@@ -47,6 +47,26 @@ const char* ovl_last_error(void) { return g_err; }
 
 const char* ovl_version(void) { return "ovl 1.0 sm_103a"; }
 
+ovl_status ovl_set_pair_variant(int64_t volume, int32_t precision, int32_t variant) {
+  clear_error();
+  OVL_REQUIRE(volume >= 1 && volume <= (int64_t(1) << 26), "ovl_set_pair_variant: volume out of range");
+  OVL_REQUIRE(precision >= OVL_PREC_F64 && precision <= OVL_PREC_F32_F16LINKS,
+              "ovl_set_pair_variant: unknown precision %d", precision);
+  OVL_REQUIRE(variant >= -1 && variant < ovl::kPairVariants, "ovl_set_pair_variant: variant %d outside -1..%d",
+              variant, ovl::kPairVariants - 1);
+  static_assert(OVL_PREC_F64 == ovl::LINK_F64 && OVL_PREC_F32 == ovl::LINK_F32 &&
+                    OVL_PREC_F32_F16LINKS == ovl::LINK_F16R12,
+                "the tuner's key is the link format of the precision");
+  ovl::set_pair_variant((int)volume, precision, variant);
+  return OVL_OK;
+}
+
+int32_t ovl_get_pair_variant(int64_t volume, int32_t precision) {
+  if (volume < 1 || volume > (int64_t(1) << 26) || precision < OVL_PREC_F64 || precision > OVL_PREC_F32_F16LINKS)
+    return -1;
+  return ovl::tuned_pair_variant((int)volume, precision);
+}
+
 ovl_status ovl_ctx_create(int32_t device, ovl_ctx** out) {
   clear_error();
   OVL_REQUIRE(out != nullptr, "ovl_ctx_create: out is NULL");

@@ -74,6 +74,26 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
   return FF{hi, e - (hi - s)};
 }
 
+// N FP64 scalars in the kernel's precision R, converted once per block: on this GPU a
+// double -> float conversion issues on the FP64 pipe (1/64 of the FP32 rate), so FP32 threads
+// that each convert their own coefficients spend a large share of an element-wise kernel on it
+// (ncu, 16 sources at 16^4: the FP32 Lanczos update had its FP64 pipe 87% active). Every thread of
+// the block must call this (it synchronises the block); src is read by threads 0..N-1 only.
+template <class R, int N>
+__device__ __forceinline__ void scalars_in(const double* src, R (&out)[N]) {
+  if constexpr (sizeof(R) == 8) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = src[i];
+  } else {
+    __shared__ R sh[N];
+    const int t = lin_tid();
+    if (t < N) sh[t] = (R)src[t];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = sh[i];
+  }
+}
+
 template <class R> struct Red;
 template <> struct Red<double> {
   double v = 0.0;
@@ -252,19 +272,20 @@ __device__ __forceinline__ void store_spin(typename V2<R>::T* p, int vol, int s,
 // adds them to its own and to the diagonal term, then hands D_W(+-mu) psi at (spin, colours
 // 0..2) to `emit(which, site, spin, x[3])`. The epilogue (scaling, stores, reductions) is thus
 // spread over all eight warps of the block instead of the two that held the first direction.
+// SITES sites per block (blockDim = (SITES, 8)).
 constexpr int kSplitSites = 32;
 
-template <class R>
+template <class R, int SITES = kSplitSites>
 struct SplitSmem {
-  cplx<R> part[2][3][12][kSplitSites];  // [which][slot of the contributing direction][component][site]
+  cplx<R> part[2][3][12][SITES];  // [which][slot of the contributing direction][component][site]
 };
 
-template <class R, int LF, class Emit>
+template <class R, int LF, int SITES = kSplitSites, class Emit>
 __device__ __forceinline__ void pair_split(const Geom& g, const Links& U, const HopCoef<R>& c0, const HopCoef<R>& c1,
                                            const typename V2<R>::T* in0, const typename V2<R>::T* in1,
-                                           SplitSmem<R>& sm, Emit emit) {
+                                           SplitSmem<R, SITES>& sm, Emit emit) {
   const int tx = threadIdx.x, which = threadIdx.y >> 2, dir = threadIdx.y & 3;
-  const int s = blockIdx.x * kSplitSites + tx;
+  const int s = blockIdx.x * SITES + tx;
   const typename V2<R>::T* in = which ? in1 : in0;
   const HopCoef<R>& c = which ? c1 : c0;
   Loader<R, true> ld{in, g.vol, false};

@@ -34,6 +34,13 @@ int tune_pair_variant(int vol, int prec, int (*measure)(void*), void* arg) {
   if (v >= 0) g_tune[{vol, prec}] = v;
   return v;
 }
+void set_pair_variant(int vol, int prec, int variant) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (variant < 0)
+    g_tune.erase({vol, prec});
+  else
+    g_tune[{vol, prec}] = variant;
+}
 
 // ------------------------------------------------------------------ layout conversion
 template <class Tin, class Tout>
@@ -433,8 +440,11 @@ __device__ __forceinline__ void lz_alpha_finish(const LzDev& lz, int rhs, size_t
 // the link lines in L1. PS (64, 48 or 32 sites) sets how evenly the blocks spread over the SMs:
 // 12^4 FP64 with 64 sites is 324 blocks, three on 20 SMs and two on the other 132 (the SMs sat
 // idle a third of the time under ncu); with 48 sites it is 432 blocks, 2.84 per SM.
-template <class R, int LF, int PS>
-__global__ void __launch_bounds__(2 * PS) k_lz_pair(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm, LzDev lz,
+// ONE_ROLE: one warp-uniform half per block instead (block (PS, 1), even blocks H(mu) vhat, odd
+// blocks H(-mu) what), twice the blocks at half the size: 12^4 with 32 sites is 1296 one-warp
+// blocks, at most 9 on an SM against a mean of 8.53 (with both halves per block: 5 against 4.26).
+template <class R, int LF, int PS, bool ONE_ROLE = false>
+__global__ void __launch_bounds__(ONE_ROLE ? PS : 2 * PS) k_lz_pair(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm, LzDev lz,
                                                             const typename V2<R>::T* vh, const typename V2<R>::T* wh,
                                                             typename V2<R>::T* av, typename V2<R>::T* aw) {
   using T = typename V2<R>::T;
@@ -446,14 +456,17 @@ __global__ void __launch_bounds__(2 * PS) k_lz_pair(Geom g, Links U, HopCoef<R> 
   const double2 swd = lz.sw[o + j];
   const T* vj = vh + vcol(lz, rhs, j, n);
   const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
-  const int s = blockIdx.x * PS + threadIdx.x;
-  const bool is_w = threadIdx.y == 1;
+  const int s = (ONE_ROLE ? (int)(blockIdx.x >> 1) : (int)blockIdx.x) * PS + threadIdx.x;
+  const bool is_w = ONE_ROLE ? (blockIdx.x & 1) != 0 : threadIdx.y == 1;
+  const double sd[3] = {lz.sv[o + j], swd.x, swd.y};
+  R sc[3];
+  scalars_in<R, 3>(sd, sc);
   Red<R> acc[2];
   if (s < g.vol) {
     Spin<R> ov;
     if (!is_w) {
       dslash_site<LF, R>(g, U, s, cp, Loader<R, true>{vj, g.vol, false}, ov);
-      const R sv = (R)lz.sv[o + j];
+      const R sv = sc[0];
       // all loads of w_j before the stores of Av (the compiler cannot reorder them across stores
       // that might alias, which would serialise twelve memory round trips)
       cplx<R> wv[12];
@@ -471,7 +484,7 @@ __global__ void __launch_bounds__(2 * PS) k_lz_pair(Geom g, Links U, HopCoef<R> 
       acc[1].add(a.im);
     } else {
       dslash_site<LF, R>(g, U, s, cm, Loader<R, true>{wj, g.vol, false}, ov);
-      const cplx<R> sw = mk<R>((R)swd.x, (R)swd.y);
+      const cplx<R> sw = mk<R>(sc[1], sc[2]);
 #pragma unroll
       for (int c = 0; c < 12; ++c) {
         cplx<R> y = sw * ov.c[c / 3][c % 3];
@@ -492,14 +505,14 @@ __global__ void __launch_bounds__(2 * PS) k_lz_pair(Geom g, Links U, HopCoef<R> 
 
 // The same step with 8 threads per site (small lattices): see pair_split. Each thread finishes
 // one spin (three colours) of its site: scale, gamma5, store, and for the v half the partial of
-// alpha_j.
-template <class R, int LF, int MINB = 1>
-__global__ void __launch_bounds__(8 * kSplitSites, MINB) k_lz_pair_split(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm,
+// alpha_j. SITES sites per block, at least MINB blocks per SM.
+template <class R, int LF, int MINB = 1, int SITES = kSplitSites>
+__global__ void __launch_bounds__(8 * SITES, MINB) k_lz_pair_split(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm,
                                                                    LzDev lz, const typename V2<R>::T* vh,
                                                                    const typename V2<R>::T* wh,
                                                                    typename V2<R>::T* av, typename V2<R>::T* aw) {
   using T = typename V2<R>::T;
-  __shared__ SplitSmem<R> sm;
+  __shared__ SplitSmem<R, SITES> sm;
   const int rhs = blockIdx.y;
   if (lz.status[rhs]) return;
   const int j = lz.j[rhs];
@@ -508,10 +521,13 @@ __global__ void __launch_bounds__(8 * kSplitSites, MINB) k_lz_pair_split(Geom g,
   const double2 swd = lz.sw[o + j];
   const T* vj = vh + vcol(lz, rhs, j, n);
   const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
-  const R sv = (R)lz.sv[o + j];
-  const cplx<R> sw = mk<R>((R)swd.x, (R)swd.y);
+  const double sd[3] = {lz.sv[o + j], swd.x, swd.y};
+  R sc[3];
+  scalars_in<R, 3>(sd, sc);
+  const R sv = sc[0];
+  const cplx<R> sw = mk<R>(sc[1], sc[2]);
   Red<R> acc[2];
-  pair_split<R, LF>(g, U, cp, cm, vj, wj, sm, [&](int which, int s, int sp, cplx<R> (&x)[3]) {
+  pair_split<R, LF, SITES>(g, U, cp, cm, vj, wj, sm, [&](int which, int s, int sp, cplx<R> (&x)[3]) {
     const R g5 = sp >= 2 ? (R)-1 : (R)1;
     if (which == 0) {
       cplx<R> wv[3];  // loads first (see k_lz_pair)
@@ -539,6 +555,105 @@ __global__ void __launch_bounds__(8 * kSplitSites, MINB) k_lz_pair_split(Geom g,
   }
 }
 
+// The pair step, dynamically scheduled: a grid of as many blocks as the GPU holds at once whose
+// warps claim tasks from a counter; task t applies H(mu) to vhat_j (t even) or H(-mu) to what_j
+// (t odd) on the 32 sites of chunk t / 2. The FP64 stencil is bound by the FP64 pipe and a
+// statically scheduled grid finishes with its most loaded SM: at 12^4 ncu counted 140K / 164K /
+// 214K active cycles (min / mean / max over the SMs) for 1296 one-warp blocks, so a third of the
+// SM time idled at the end. Here every warp keeps claiming until the tasks run out. The alpha
+// partial of a chunk goes to the chunk's own slot and the last block sums the slots in chunk order:
+// the result does not depend on which warp ran which task.
+constexpr int kDynWarps = 4;  // warps per block
+
+template <class R, int LF>
+__global__ void __launch_bounds__(32 * kDynWarps) k_lz_pair_dyn(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm,
+                                                                 LzDev lz, const typename V2<R>::T* vh,
+                                                                 const typename V2<R>::T* wh,
+                                                                 typename V2<R>::T* av, typename V2<R>::T* aw) {
+  using T = typename V2<R>::T;
+  const int rhs = blockIdx.y;
+  if (lz.status[rhs]) return;
+  const int j = lz.j[rhs];
+  const size_t n = (size_t)12 * g.vol;
+  const size_t o = (size_t)rhs * (lz.kmax + 2);
+  const double2 swd = lz.sw[o + j];
+  const T* vj = vh + vcol(lz, rhs, j, n);
+  const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
+  const double sd[3] = {lz.sv[o + j], swd.x, swd.y};
+  R sc[3];
+  scalars_in<R, 3>(sd, sc);
+  const int lane = threadIdx.x & 31;
+  const int nchunk = (g.vol + 31) >> 5;
+  double* part = lz.part + (size_t)rhs * lz.nblk * 4;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = (int)atomicAdd(lz.claim + rhs, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= 2 * nchunk) break;
+    const int c = t >> 1, s = c * 32 + lane;
+    const bool is_w = t & 1;
+    Red<R> acc[2];
+    if (s < g.vol) {
+      Spin<R> ov;
+      if (!is_w) {
+        dslash_site<LF, R>(g, U, s, cp, Loader<R, true>{vj, g.vol, false}, ov);
+        cplx<R> wv[12];  // all loads of w_j before the stores of Av (see k_lz_pair)
+#pragma unroll
+        for (int q = 0; q < 12; ++q) wv[q] = ldc<R>(wj, (size_t)q * g.vol + s);
+        cplx<R> a = mk<R>(0, 0);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          cplx<R> x = sc[0] * ov.c[q / 3][q % 3];
+          if (q >= 6) x = -x;  // gamma5
+          stc<R>(av + (size_t)rhs * n, (size_t)q * g.vol + s, x);
+          a = a + cdot(wv[q], x);
+        }
+        acc[0].add(a.re);
+        acc[1].add(a.im);
+      } else {
+        dslash_site<LF, R>(g, U, s, cm, Loader<R, true>{wj, g.vol, false}, ov);
+        const cplx<R> sw = mk<R>(sc[1], sc[2]);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          cplx<R> y = sw * ov.c[q / 3][q % 3];
+          if (q >= 6) y = -y;  // gamma5
+          stc<R>(aw + (size_t)rhs * n, (size_t)q * g.vol + s, y);
+        }
+      }
+    }
+    if (!is_w) {  // the chunk's partial of alpha_j, at the chunk's slot
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        acc[0].add(acc[0].shfl_xor(off));
+        acc[1].add(acc[1].shfl_xor(off));
+      }
+      if (lane == 0) {
+        double* pc = part + (size_t)c * 4;
+        pc[0] = acc[0].get();
+        pc[1] = acc[1].get();
+        pc[2] = 0.0;
+        pc[3] = 0.0;
+        __threadfence();
+      }
+    }
+  }
+  __syncthreads();  // every warp of the block has stopped claiming
+  __shared__ bool last;
+  if (lin_tid() == 0) {
+    __threadfence();
+    last = atomicAdd(lz.count + rhs, 1u) == gridDim.x - 1;
+    if (last) {  // no block claims any more: both counters back to zero for the next launch
+      lz.count[rhs] = 0u;
+      lz.claim[rhs] = 0u;
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  double pv[4];
+  reduce_partials<4>(part, nchunk, pv);
+  if (lin_tid() == 0) lz_alpha_finish(lz, rhs, o, j, swd, pv);
+}
+
 // vhat_{j+1} = Av_j - alpha_j v_j - beta_{j-1} v_{j-1}
 // what_{j+1} = Aw_j - conj(alpha_j) w_j - conj(delta_{j-1}) w_{j-1}    (Eqs. 2sided1/2)
 // then delta_j = sqrt|what^H vhat|, beta_j = what^H vhat / delta_j (scaling reading).
@@ -558,10 +673,10 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typen
   const int j = lz.j[rhs];
   const size_t n = (size_t)12 * g.vol;
   const size_t o = (size_t)rhs * (lz.kmax + 2);
-  const double2* uc = lz.ucoef + (size_t)rhs * 4;
-  const double2 u0 = uc[0], u1 = uc[1], u2 = uc[2], u3 = uc[3];
-  const cplx<R> a1 = mk<R>((R)u0.x, (R)u0.y), a2 = mk<R>((R)u1.x, (R)u1.y);
-  const cplx<R> b1 = mk<R>((R)u2.x, (R)u2.y), b2 = mk<R>((R)u3.x, (R)u3.y);
+  R u[8];  // the four complex coefficients of LzDev::ucoef
+  scalars_in<R, 8>((const double*)(lz.ucoef + (size_t)rhs * 4), u);
+  const cplx<R> a1 = mk<R>(u[0], u[1]), a2 = mk<R>(u[2], u[3]);
+  const cplx<R> b1 = mk<R>(u[4], u[5]), b2 = mk<R>(u[6], u[7]);
   const T* vj = vh + vcol(lz, rhs, j, n);
   const T* vjm = vh + vcol(lz, rhs, j > 1 ? j - 1 : 1, n);
   T* vnew = vh + vcol(lz, rhs, j + 1, n);
@@ -647,19 +762,59 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typen
   }
 }
 
-template <int PS>
+// As many blocks of k_lz_pair_dyn as the device holds at once (queried once per instance), at most
+// one warp per task.
+template <class R, int LF>
+static cudaError_t pair_dyn_launch(const Geom& g, const Links& U, const HopCoef<R>& cp, const HopCoef<R>& cm,
+                                   const LzDev& lz, const LzVecs& vec, cudaStream_t st) {
+  static const int resident = [] {
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lz_pair_dyn<R, LF>, 32 * kDynWarps, 0) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return nsm * per_sm;
+  }();
+  if (resident <= 0) return cudaErrorLaunchFailure;
+  const int ntask = 2 * ((g.vol + 31) >> 5);
+  const int nb = std::max(1, std::min(resident, (ntask + kDynWarps - 1) / kDynWarps));
+  using T = typename V2<R>::T;
+  return launch_plain(k_lz_pair_dyn<R, LF>, dim3(nb, lz.nrhs), dim3(32 * kDynWarps), st, g, U, cp, cm, lz,
+                      (const T*)vec.vh, (const T*)vec.wh, (T*)vec.av, (T*)vec.aw);
+}
+
+template <int PS, bool ONE_ROLE = false>
 static cudaError_t pair_unsplit(const Geom& g, const Links& U, int lf, bool f64, HopCoef<double> dp, HopCoef<double> dm,
                                 HopCoef<float> fp, HopCoef<float> fm, const LzDev& lz, const LzVecs& vec,
                                 cudaStream_t st) {
-  dim3 grid((g.vol + PS - 1) / PS, lz.nrhs), block(PS, 2);
+  const unsigned nb = (unsigned)((g.vol + PS - 1) / PS);
+  dim3 grid(ONE_ROLE ? 2 * nb : nb, lz.nrhs), block(PS, ONE_ROLE ? 1 : 2);
   if (f64)
-    return launch_plain(k_lz_pair<double, LINK_F64, PS>, grid, block, st, g, U, dp, dm, lz, (const double2*)vec.vh,
-                        (const double2*)vec.wh, (double2*)vec.av, (double2*)vec.aw);
+    return launch_plain(k_lz_pair<double, LINK_F64, PS, ONE_ROLE>, grid, block, st, g, U, dp, dm, lz,
+                        (const double2*)vec.vh, (const double2*)vec.wh, (double2*)vec.av, (double2*)vec.aw);
   if (lf == LINK_F16R12)
-    return launch_plain(k_lz_pair<float, LINK_F16R12, PS>, grid, block, st, g, U, fp, fm, lz, (const float2*)vec.vh,
-                        (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
-  return launch_plain(k_lz_pair<float, LINK_F32, PS>, grid, block, st, g, U, fp, fm, lz, (const float2*)vec.vh,
-                      (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
+    return launch_plain(k_lz_pair<float, LINK_F16R12, PS, ONE_ROLE>, grid, block, st, g, U, fp, fm, lz,
+                        (const float2*)vec.vh, (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
+  return launch_plain(k_lz_pair<float, LINK_F32, PS, ONE_ROLE>, grid, block, st, g, U, fp, fm, lz,
+                      (const float2*)vec.vh, (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
+}
+
+template <int MINB, int SITES>
+static cudaError_t pair_split_launch(const Geom& g, const Links& U, int lf, bool f64, const HopCoef<double>& dp,
+                                     const HopCoef<double>& dm, const HopCoef<float>& fp, const HopCoef<float>& fm,
+                                     const LzDev& lz, const LzVecs& vec, cudaStream_t st) {
+  dim3 grid((g.vol + SITES - 1) / SITES, lz.nrhs), block(SITES, 8);
+  if (f64)
+    return launch_plain(k_lz_pair_split<double, LINK_F64, MINB, SITES>, grid, block, st, g, U, dp, dm, lz,
+                        (const double2*)vec.vh, (const double2*)vec.wh, (double2*)vec.av, (double2*)vec.aw);
+  if (lf == LINK_F16R12)
+    return launch_plain(k_lz_pair_split<float, LINK_F16R12, MINB, SITES>, grid, block, st, g, U, fp, fm, lz,
+                        (const float2*)vec.vh, (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
+  return launch_plain(k_lz_pair_split<float, LINK_F32, MINB, SITES>, grid, block, st, g, U, fp, fm, lz,
+                      (const float2*)vec.vh, (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
 }
 
 cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
@@ -672,31 +827,21 @@ cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64,
   const float2 *fv = (const float2*)vec.vh, *fw = (const float2*)vec.wh;
   cudaError_t e;
   if (variant == 1) {
-    dim3 grid((g.vol + kSplitSites - 1) / kSplitSites, lz.nrhs), block(kSplitSites, 8);
-    if (f64)
-      e = launch_plain(k_lz_pair_split<double, LINK_F64>, grid, block, st, g, U, dp, dm, lz, dv, dw, (double2*)vec.av,
-                     (double2*)vec.aw);
-    else if (lf == LINK_F16R12)
-      e = launch_plain(k_lz_pair_split<float, LINK_F16R12>, grid, block, st, g, U, fp, fm, lz, fv, fw, (float2*)vec.av,
-                     (float2*)vec.aw);
-    else
-      e = launch_plain(k_lz_pair_split<float, LINK_F32>, grid, block, st, g, U, fp, fm, lz, fv, fw, (float2*)vec.av,
-                     (float2*)vec.aw);
-  } else if (variant == 4) {  // the split kernel held to 128 registers: two blocks per SM
-    dim3 grid((g.vol + kSplitSites - 1) / kSplitSites, lz.nrhs), block(kSplitSites, 8);
-    if (f64)
-      e = launch_plain(k_lz_pair_split<double, LINK_F64, 2>, grid, block, st, g, U, dp, dm, lz, dv, dw,
-                       (double2*)vec.av, (double2*)vec.aw);
-    else if (lf == LINK_F16R12)
-      e = launch_plain(k_lz_pair_split<float, LINK_F16R12, 2>, grid, block, st, g, U, fp, fm, lz, fv, fw,
-                       (float2*)vec.av, (float2*)vec.aw);
-    else
-      e = launch_plain(k_lz_pair_split<float, LINK_F32, 2>, grid, block, st, g, U, fp, fm, lz, fv, fw,
-                       (float2*)vec.av, (float2*)vec.aw);
+    e = pair_split_launch<1, kSplitSites>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
+  } else if (variant == 4) {  // held to 128 registers: two blocks per SM
+    e = pair_split_launch<2, kSplitSites>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
+  } else if (variant == 5) {  // 16 sites per block held to 168 registers: three blocks per SM
+    e = pair_split_launch<3, 16>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
   } else if (variant == 2) {
     e = pair_unsplit<48>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
   } else if (variant == 3) {
     e = pair_unsplit<32>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
+  } else if (variant == 6) {
+    e = pair_unsplit<32, true>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
+  } else if (variant == 7) {
+    e = f64 ? pair_dyn_launch<double, LINK_F64>(g, U, dp, dm, lz, vec, st)
+            : lf == LINK_F16R12 ? pair_dyn_launch<float, LINK_F16R12>(g, U, fp, fm, lz, vec, st)
+                                : pair_dyn_launch<float, LINK_F32>(g, U, fp, fm, lz, vec, st);
   } else {
     e = pair_unsplit<kPairSites>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
   }

@@ -28,17 +28,34 @@ inline cudaError_t launch_plain(void (*kern)(KArgs...), dim3 grid, dim3 block, c
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// Records a timing event around a launch: as an external event node while `st` is being captured
+// into a graph (a plain record inside a capture only orders the graph's nodes and times nothing),
+// as a plain record otherwise (the runtime refuses the external flag outside a capture).
+inline cudaError_t record_timing(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                                             : cudaEventRecord(ev, st);
+}
+
 // Pair-stencil variant chosen by the autotuner for (volume, precision): -1 none yet,
 // 0 one thread per site (64 sites per block), 1 split over 8 threads, 2 / 3 one thread per site
-// with 48 / 32 sites per block, 4 split held to 128 registers (two blocks per SM); the multishift
-// kernels run variants 0, 2, 3 as 0 and 4 as 1. Thread-safe, process-wide. (A 16-thread split,
-// one hop per thread, measured 54 us against 32 us for FP64 at 8^4: more index and reduction
-// work than the extra warps hide.)
-constexpr int kPairVariants = 5;
+// with 48 / 32 sites per block, 4 split held to 128 registers (two blocks per SM), 5 split with
+// 16 sites per block held to 168 registers (three blocks per SM), 6 one thread per site, 32 sites,
+// one stencil (H(mu) or H(-mu)) per one-warp block, 7 dynamically scheduled (warps of a resident
+// grid claim 32-site tasks from a counter). The FP64 stencil is bound by the FP64 pipe, so its time
+// follows the most loaded SM: at 12^4 ncu counted SM active cycles of max 206K against a mean of
+// 156K for variant 3 and 214K against 164K for variant 6. The multishift kernels run variants 0,
+// 2, 3, 6, 7 as 0 and 4, 5 as 1. Thread-safe, process-wide. (A 16-thread split, one hop per thread, measured
+// 54 us against 32 us for FP64 at 8^4: more index and reduction work than the extra warps hide.)
+constexpr int kPairVariants = 8;
 int tuned_pair_variant(int vol, int prec);
 // Returns the variant for the key, running `measure` (which returns 0 or 1) under the table's
 // lock the first time, so that every solve in the process uses one decision per key.
 int tune_pair_variant(int vol, int prec, int (*measure)(void*), void* arg);
+// Sets the entry (variant >= 0) or removes it (-1).
+void set_pair_variant(int vol, int prec, int variant);
 constexpr int kVecBlock = 128;  // threads per block of the element-parallel vector kernels
 inline unsigned vec_blocks(const Geom& g) { return (unsigned)((12 * (size_t)g.vol + kVecBlock - 1) / kVecBlock); }
 // Elements per thread of the element-parallel kernels: enough to amortise the per-thread set-up and
@@ -73,6 +90,7 @@ struct LzDev {
   double* beta0 = nullptr;  // [nrhs] ||r||
   double* part = nullptr;   // [nrhs][nblk][4] block partials
   unsigned* count = nullptr;// [nrhs] last-block counters (kept at 0 between launches)
+  unsigned* claim = nullptr;// [nrhs] task counters of the dynamically scheduled pair stencil (kept at 0)
   int vcols = 0;            // basis columns kept per rhs: kmax + 1, or 3 (two-pass: a rotating window)
   double2* xacc = nullptr;  // two-pass, second pass: [nrhs][12][V] FP64 sum of coef_j vhat_j so far
   const double2* xcoef = nullptr;  // two-pass: [nrhs][kmax + 2] coefficient of column j (0 beyond k)

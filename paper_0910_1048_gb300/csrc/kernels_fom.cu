@@ -133,10 +133,11 @@ __global__ void __launch_bounds__(256) k_fom_scale(FomDev f, int j) {
   const int rhs = blockIdx.y;
   if (f.status[rhs]) return;
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  R s[1];
+  scalars_in<R, 1>(f.scale + rhs, s);
   if (e >= f.n) return;
   T* w = (T*)f.V + ((size_t)(j + 1) * f.nrhs + rhs) * f.n;
-  const R s = (R)f.scale[rhs];
-  stc<R>(w, e, s * ldc<R>(w, e));
+  stc<R>(w, e, s[0] * ldc<R>(w, e));
 }
 
 static int fom_elts(size_t n) {

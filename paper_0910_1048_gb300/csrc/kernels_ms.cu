@@ -142,11 +142,14 @@ __global__ void __launch_bounds__(2 * kPairSites) k_ms_pair(Geom g, Links U, Hop
   const bool is_t = threadIdx.y == 1;
   const T* in = (const T*)(MODE == 0 ? (is_t ? v.pt : v.p) : (is_t ? v.tt : v.t)) + voff<R>(rhs, n);
   T* out = (T*)(MODE == 0 ? (is_t ? v.tt : v.t) : (is_t ? v.qt : v.q)) + voff<R>(rhs, n);
+  const double s1d = ms.sig1v ? ms.sig1v[rhs] : ms.sigma1;
+  R s1v[1];
+  scalars_in<R, 1>(&s1d, s1v);
   Red<R> acc[2];
   if (s < g.vol) {
     Spin<R> o;
     dslash_site<LF, R>(g, U, s, is_t ? cm : cp, Loader<R, true>{in, g.vol, false}, o);
-    const R s1 = (R)(ms.sig1v ? ms.sig1v[rhs] : ms.sigma1);
+    const R s1 = s1v[0];
     const T* pp = (const T*)(is_t ? v.pt : v.p) + voff<R>(rhs, n);
     const T* ptl = (const T*)v.pt + voff<R>(rhs, n);
     // MODE 1: every load before the first store (stores that might alias would otherwise
@@ -196,7 +199,10 @@ __global__ void __launch_bounds__(8 * kSplitSites) k_ms_pair_split(Geom g, Links
   const size_t n = (size_t)12 * g.vol;
   const T* in0 = (const T*)(MODE == 0 ? v.p : v.t) + voff<R>(rhs, n);
   const T* in1 = (const T*)(MODE == 0 ? v.pt : v.tt) + voff<R>(rhs, n);
-  const R s1 = (R)(ms.sig1v ? ms.sig1v[rhs] : ms.sigma1);
+  const double s1d = ms.sig1v ? ms.sig1v[rhs] : ms.sigma1;
+  R s1v[1];
+  scalars_in<R, 1>(&s1d, s1v);
+  const R s1 = s1v[0];
   Red<R> acc[2];
   // each thread finishes one spin (three colours) of its site: see pair_split
   pair_split<R, LF>(g, U, cp, cm, in0, in1, sm, [&](int which, int s, int sp, cplx<R> (&o)[3]) {
@@ -244,8 +250,9 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_update(Geom g, MsDev ms, MsVec
   if (ms.status[rhs] != 0) return;
   const size_t n = (size_t)12 * g.vol;
   double2* sd = ms.seed + (size_t)rhs * 8;
-  const zd ak = ldc<double>(sd, 1);
-  const cplx<R> a = mk<R>((R)ak.re, (R)ak.im), ac = mk<R>((R)ak.re, (R)-ak.im);
+  R akr[2];
+  scalars_in<R, 2>((const double*)(sd + 1), akr);
+  const cplx<R> a = mk<R>(akr[0], akr[1]), ac = mk<R>(akr[0], -akr[1]);
   T* r = (T*)v.r + voff<R>(rhs, n);
   T* rt = (T*)v.rt + voff<R>(rhs, n);
   const T* q = (const T*)v.q + voff<R>(rhs, n);
@@ -351,9 +358,10 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs 
     coefb[i].y = (R)b.y;
   }
   __syncthreads();
+  R bkr[2];
+  scalars_in<R, 2>((const double*)(ms.seed + (size_t)rhs * 8 + 5), bkr);
   if (e >= n) return;
-  const zd bk = ldc<double>(ms.seed + (size_t)rhs * 8, 5);
-  const cplx<R> b = mk<R>((R)bk.re, (R)bk.im), bc = mk<R>((R)bk.re, (R)-bk.im);
+  const cplx<R> b = mk<R>(bkr[0], bkr[1]), bc = mk<R>(bkr[0], -bkr[1]);
   const T* r = (const T*)v.r + voff<R>(rhs, n);
   const T* rt = (const T*)v.rt + voff<R>(rhs, n);
   T* p = (T*)v.p + voff<R>(rhs, n);
@@ -432,21 +440,21 @@ static cudaError_t ms_step_t(const Geom& g, const Links& U, double m_w, double m
   HopCoef<R> cp = hop_coef<R>(m_w, mu), cm = hop_coef<R>(m_w, -mu);
   dim3 sgrid((g.vol + kSplitSites - 1) / kSplitSites, ms.nrhs), sblock(kSplitSites, 8);
   const int tv = tuned_pair_variant(g.vol, sizeof(R) == 8 ? 0 : LF);
-  const bool split = tv < 0 ? use_split(g) : (tv == 1 || tv == 4);
+  const bool split = tv < 0 ? use_split(g) : (tv == 1 || tv == 4 || tv == 5);
   const int elt = vec_elts(g, ms.nrhs, sizeof(R) == 8);
   cudaError_t e;
-  if (ev) cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal);
+  if (ev && (e = record_timing(ev[0], st))) return e;
   e = split ? launch_plain(k_ms_pair_split<R, LF, 0>, sgrid, sblock, st, g, U, cp, cm, ms, v)
             : launch_plain(k_ms_pair<R, LF, 0>, pgrid, pblock, st, g, U, cp, cm, ms, v);
   if (e) return e;
-  if (ev) cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal);
+  if (ev && (e = record_timing(ev[1], st))) return e;
   e = split ? launch_plain(k_ms_pair_split<R, LF, 1>, sgrid, sblock, st, g, U, cp, cm, ms, v)
             : launch_plain(k_ms_pair<R, LF, 1>, pgrid, pblock, st, g, U, cp, cm, ms, v);
   if (e) return e;
   if ((e = launch_plain(k_ms_update<R>, dim3(vec_blocks(g, elt), ms.nrhs), dim3(kVecBlock), st, g, ms, v, elt))) return e;
-  if (ev) cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal);
+  if (ev && (e = record_timing(ev[2], st))) return e;
   if ((e = launch_plain(k_ms_dirs<R>, grid, dim3(kVecBlock), st, g, ms, v))) return e;
-  if (ev) cudaEventRecordWithFlags(ev[3], st, cudaEventRecordExternal);
+  if (ev && (e = record_timing(ev[3], st))) return e;
   return cudaGetLastError();
 }
 

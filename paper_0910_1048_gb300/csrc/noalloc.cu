@@ -134,7 +134,7 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   size_t o_sv = take((size_t)nrhs * ks * 8), o_sw = take((size_t)nrhs * ks * 16);
   size_t o_al = take((size_t)nrhs * ks * 16), o_be = take((size_t)nrhs * ks * 16);
   size_t o_de = take((size_t)nrhs * ks * 8), o_vn = take((size_t)nrhs * ks * 8), o_b0 = take((size_t)nrhs * 8);
-  size_t o_pa = take((size_t)nrhs * std::max(m, 1) * nblk * 4 * 8), o_cn = take((size_t)nrhs * 4);
+  size_t o_pa = take((size_t)nrhs * std::max(m, 1) * nblk * 4 * 8), o_cn = take((size_t)nrhs * 8);
   size_t o_uc = take((size_t)nrhs * 4 * 16);
   size_t o_do = take((size_t)nrhs * 2 * std::max(m, 1) * 16), o_ls = take((size_t)std::max(m, 1) * 8);
   size_t o_co = take((size_t)nrhs * kmax * 16), o_kr = take((size_t)nrhs * 4);
@@ -163,6 +163,7 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   lz.beta0 = (double*)(base + o_b0);
   lz.part = (double*)(base + o_pa);
   lz.count = (unsigned*)(base + o_cn);
+  lz.claim = lz.count + nrhs;
   lz.ucoef = (double2*)(base + o_uc);
   LzVecs vec;
   vec.vh = base + o_vh;
@@ -180,7 +181,7 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   unsigned* ncount = (unsigned*)(base + o_nc);
   double* nout = (double*)(base + o_no);
   // the array keeps the previous call's contents: the block counters must start at zero
-  OVL_CHECK_CUDA(cudaMemsetAsync(lz.count, 0, (size_t)nrhs * 4, st));
+  OVL_CHECK_CUDA(cudaMemsetAsync(lz.count, 0, (size_t)nrhs * 8, st));
   OVL_CHECK_CUDA(cudaMemsetAsync(ncount, 0, (size_t)nrhs * 4, st));
   std::vector<double> ls(std::max(m, 1));
   for (int i = 0; i < m; ++i) ls[i] = lat->src()->defl.lam[2 * i] >= 0 ? 1.0 : -1.0;

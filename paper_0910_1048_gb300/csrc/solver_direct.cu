@@ -138,7 +138,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   size_t o_vn = take((size_t)nrhs * ks * 8);
   size_t o_b0 = take((size_t)nrhs * 8);
   size_t o_pa = take((size_t)nrhs * std::max(m, 1) * nblk * 4 * 8);
-  size_t o_cn = take((size_t)nrhs * 4);
+  size_t o_cn = take((size_t)nrhs * 8);  // last-block counters, then task counters
   size_t o_uc = take((size_t)nrhs * 4 * 16);
   size_t o_do = take((size_t)nrhs * 2 * std::max(m, 1) * 16);
   size_t o_ls = take((size_t)std::max(m, 1) * 8);
@@ -194,6 +194,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   lz.beta0 = (double*)(base + o_b0);
   lz.part = (double*)(base + o_pa);
   lz.count = (unsigned*)(base + o_cn);
+  lz.claim = lz.count + nrhs;
   lz.ucoef = (double2*)(base + o_uc);
   w->dots = (double2*)(base + o_do);
   w->lam_sign = (double*)(base + o_ls);
@@ -211,7 +212,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
     w->xacc = (double2*)(base + o_xa);
     w->xcoef = (double2*)(base + o_xc);
   }
-  if (cudaMemsetAsync(lz.count, 0, (size_t)nrhs * 4, w->stream) != cudaSuccess ||
+  if (cudaMemsetAsync(lz.count, 0, (size_t)nrhs * 8, w->stream) != cudaSuccess ||
       cudaMemsetAsync(w->ncount, 0, (size_t)nrhs * 4, w->stream) != cudaSuccess) {
     free_direct_ws(w);
     set_error("apply_sign: cudaMemset failed");
@@ -459,12 +460,12 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   // one step, with timing events around its two launches when `tev` is given
   auto step = [&](cudaEvent_t* tev) -> cudaError_t {
     cudaError_t e;
-    if (tev && (e = cudaEventRecordWithFlags(tev[0], st, cudaEventRecordExternal))) return e;
+    if (tev && (e = record_timing(tev[0], st))) return e;
     if ((e = launch_lanczos_pair(g, U, lf, f64, p->m_W, p->mu, w->lz, vec, st))) return e;
-    if (tev && (e = cudaEventRecordWithFlags(tev[1], st, cudaEventRecordExternal))) return e;
-    if (tev && (e = cudaEventRecordWithFlags(tev[2], st, cudaEventRecordExternal))) return e;
+    if (tev && (e = record_timing(tev[1], st))) return e;
+    if (tev && (e = record_timing(tev[2], st))) return e;
     if ((e = launch_lanczos_update(g, f64, w->lz, vec, st))) return e;
-    if (tev && (e = cudaEventRecordWithFlags(tev[3], st, cudaEventRecordExternal))) return e;
+    if (tev && (e = record_timing(tev[3], st))) return e;
     return cudaSuccess;
   };
   // a chunk = one step launched directly on the stream, then a CUDA graph of the chunk's other

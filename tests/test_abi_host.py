@@ -3,7 +3,9 @@ include/ovl.h, and its host-side pieces agree with the oracle:
   - ovl_small_sign (sign(H_k) e_1, Section 2 / Algorithm 4's last line) vs eigendecomposition,
     for each route (rational g_s(cH) e_1, complex-symmetric eigenvectors, dense Newton);
   - ovl_rational_coeffs (Eq. pfe_s with Eq. no_of_poles; Zolotarev) vs the oracle's coefficients;
-  - argument errors come back as EINVAL with a message, not a crash.
+  - argument errors come back as EINVAL with a message, not a crash;
+  - the pair-stencil shape table (ovl_set_pair_variant / ovl_get_pair_variant): set, read back,
+    cleared, refused outside its range.
 """
 import os
 import re
@@ -138,3 +140,19 @@ def test_sign_buffers_refused_before_the_library(ovl, monkeypatch):
             ovl.ovl_apply_sign(lat, p, b, x)
         with pytest.raises((TypeError, ValueError)):
             ovl.ovl_apply_sign_noalloc(lat, p, b, x)
+
+
+def test_pair_variant_table(ovl):
+    vol = 6 * 6 * 6 * 10  # a volume no other test solves
+    assert ovl.ovl_get_pair_variant(vol, ovl.OVL_PREC_F32) == -1
+    ovl.ovl_set_pair_variant(vol, ovl.OVL_PREC_F32, 5)
+    assert ovl.ovl_get_pair_variant(vol, ovl.OVL_PREC_F32) == 5
+    assert ovl.ovl_get_pair_variant(vol, ovl.OVL_PREC_F64) == -1
+    ovl.ovl_set_pair_variant(vol, ovl.OVL_PREC_F32, -1)
+    assert ovl.ovl_get_pair_variant(vol, ovl.OVL_PREC_F32) == -1
+    for args in [(vol, ovl.OVL_PREC_F64, 8), (vol, ovl.OVL_PREC_F64, -2), (0, ovl.OVL_PREC_F64, 1),
+                 (vol, 3, 1), (1 << 27, ovl.OVL_PREC_F64, 0)]:
+        with pytest.raises(ovl.OvlError) as e:
+            ovl.ovl_set_pair_variant(*args)
+        assert e.value.status == ovl.OVL_EINVAL and "ovl_set_pair_variant" in str(e.value)
+    assert ovl.ovl_get_pair_variant(vol, 7) == -1

@@ -9,6 +9,8 @@ sizes where they run, and of the solver's edge cases.
   the FP64 links, so both bounds measure FP32 arithmetic only: 1e-5.
 - 16^4 FP32 direct with 16 right-hand sides in one batch, equal k, each against the oracle's
   Algorithm 4 (the C FP64 two-sided Lanczos), 1e-4 (the bound of the 4^4 FP32 equal-k test).
+- every pair-stencil shape the autotuner may pick (pinned through ovl_set_pair_variant) at 12^4,
+  the headline size, FP64 and FP32, equal k against the oracle's Algorithm 4: 1e-10 / 1e-4.
 - FP64 reliable updates with more than 64 correction systems in one batch (4 sources x s poles).
 - the spectral set-up (ARPACK through the library) against the oracle's critical eigenpairs.
 - breakdown at the start (shadow residual orthogonal to the residual), the ill-posed free field
@@ -104,6 +106,42 @@ def test_direct_batch16_1616_f32_equal_k(ovl, ctx):
     for r in range(16):
         xo, _, _ = krylov.direct_lanczos(u, dims, -2.0, 0.2, b[r], k)
         assert _rel(x[r], xo) < 1e-4, r
+
+
+@pytest.fixture(scope="module")
+def lat12(ovl, ctx):
+    dims = (12, 12, 12, 12)
+    u = synth.gauge_links(dims, 0)
+    b = synth.gaussian_source(dims, 1000)
+    lat = ovl.ovl_create_lattice(ctx, dims, -1)
+    ovl.ovl_set_links(lat, u, ovl.OVL_F64 | ovl.OVL_F32)
+    k = 24
+    xo, _, _ = krylov.direct_lanczos(u, dims, -2.0, 0.3, b, k)
+    yield lat, b, k, xo
+    ovl.ovl_destroy_lattice(lat)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_every_pair_shape_equal_k_1212(ovl, lat12, prec):
+    lat, b, k, xo = lat12
+    vol = 12 ** 4
+    pr = ovl.OVL_PREC_F64 if prec == "f64" else ovl.OVL_PREC_F32
+    bound = 1e-10 if prec == "f64" else 1e-4
+    xs = []
+    try:
+        for var in range(8):
+            ovl.ovl_set_pair_variant(vol, pr, var)
+            assert ovl.ovl_get_pair_variant(vol, pr) == var
+            st, info, x = _solve(ovl, lat, b, mu=0.3, fixed_k=k, precision=pr, check_every=8)
+            assert st == ovl.OVL_OK and info[0]["iterations"] == k
+            assert _rel(x, xo) < bound, var
+            xs.append(x)
+    finally:
+        ovl.ovl_set_pair_variant(vol, pr, -1)
+    assert ovl.ovl_get_pair_variant(vol, pr) == -1
+    # the shapes differ only in the order of alpha's partial sums
+    for x in xs[1:]:
+        assert _rel(x, xs[0]) < (1e-12 if prec == "f64" else 1e-5)
 
 
 def test_reliable_update_batch_over_64_systems(ovl, ctx, problem_4444):
