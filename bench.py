@@ -152,10 +152,10 @@ def pair_bytes(prec, vol, nrhs):
 FP64_PEAK_TFLOPS = 1.256
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture (cold L2, every
-# pass flushed), keyed (kernel, precision, lattice, nrhs); the captures and their commands are in
-# profiles/. An entry is removed when its kernel changes.
+# pass flushed), keyed (kernel, precision, lattice, nrhs, pair-stencil shape); the captures and their
+# commands are in profiles/. An entry is removed when its kernel changes.
 TRAFFIC = {
-    ("k_lz_pair", "f64", (8, 8, 8, 8), 1): 4045184,  # k_lz_pair_split<double>, the autotuned variant at 8^4
+    ("k_lz_pair", "f64", (12, 12, 12, 12), 1, 7): 20003840,  # k_lz_pair_dyn<double>: 20.003 MB read + 0.5 KB written
 }
 
 
@@ -501,6 +501,10 @@ def _dslash_batch_gbs(ovl, ctx, u_fn, L=24, nrhs=16, reps=5):
     return res
 
 
+def _prec_code(ovl, prec):
+    return {"f64": ovl.OVL_PREC_F64, "f32": ovl.OVL_PREC_F32, "f16": ovl.OVL_PREC_F32_F16LINKS}[prec]
+
+
 def _roofline(wl, infos, fp64_peak, fp64_src):
     peaks, src = _peaks()
     vol = int(np.prod(wl["dims"]))
@@ -509,10 +513,9 @@ def _roofline(wl, infos, fp64_peak, fp64_src):
     prec = wl["precision"]
     kernel = {"direct": "k_lz_pair", "multishift": "k_ms_pair", "fom": "k_dslash (two per Arnoldi step)"}[wl["method"]]
     nr = wl.get("nrhs", 1)
-    traffic = TRAFFIC.get((kernel, prec, tuple(wl["dims"]), nr))
     import paper_0910_1048_gb300 as ovl
-    code = {"f64": ovl.OVL_PREC_F64, "f32": ovl.OVL_PREC_F32, "f16": ovl.OVL_PREC_F32_F16LINKS}[prec]
-    shape = ovl.ovl_get_pair_variant(vol, code)  # the autotuner's pick (see ovl_set_pair_variant)
+    shape = ovl.ovl_get_pair_variant(vol, _prec_code(ovl, prec))  # the autotuner's pick (ovl_set_pair_variant)
+    traffic = TRAFFIC.get((kernel, prec, tuple(wl["dims"]), nr, shape))
     if prec == "f64":
         flops = PAIR_FLOPS_PER_SITE * vol * nr
         ach = flops / (t_pair * 1e-3) / 1e12 if t_pair else None
@@ -541,6 +544,7 @@ def _summary(wl, per_mu, infos, acc):
                              "t_small_ms": float(np.mean([i["t_small_ms"] for i in sel])),
                              "t_pair_ms": float(np.mean([i["t_kernel_ms"] for i in sel])),
                              "t_update_ms": float(np.mean([i["t_update_ms"] for i in sel])),
+                             "t_finish_ms": float(np.mean([i["t_finish_ms"] for i in sel])),
                              "evaluations": float(np.mean([i["evaluations"] for i in sel])),
                              "ritz_evaluations": float(np.mean([i["ritz_evaluations"] for i in sel])),
                              "gap": d.get("gap"), "accuracy_half_sign2b_minus_b": acc[j]})
@@ -613,6 +617,8 @@ def run_ours(args, wl):
         dist.init_process_group("nccl")
     ctx = ovl.ovl_ctx_create(local)
     lat, u, _, per_mu = _setup(ovl, ctx, wl, cache=args.setup_cache)
+    if args.pair_variant >= 0:  # a pinned pair-stencil shape instead of the autotuner's pick
+        ovl.ovl_set_pair_variant(int(np.prod(wl["dims"])), _prec_code(ovl, wl["precision"]), args.pair_variant)
     b = _sources(wl)
     nrhs = wl.get("nrhs", 1)
     n = b.size // nrhs
@@ -644,7 +650,8 @@ def run_ours(args, wl):
                    "accuracy_half_sign2b_minus_b": acc, "per_mu": per_mu_stats,
                    "untimed_setup_s": [round(d.get("setup_s", 0.0), 2) for d in per_mu],
                    "setup_inverse_solves": [d.get("setup_inverse_solves", 0) for d in per_mu],
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "pair_variant_pinned": args.pair_variant if args.pair_variant >= 0 else None},
         "roofline": _roofline(wl, infos, fp64_peak, fp64_src), "e2e": e2e, "clocks": clocks,
         "gpu_launches": int(launches),
     }
@@ -983,6 +990,37 @@ def run_profile_case(args):
     ovl.ovl_ctx_destroy(ctx)
 
 
+def summarize_launches(path, skip_before=None):
+    """Per-kernel totals of an Nsight Compute launch list (`ncu --metrics gpu__time_duration.sum --csv
+    --log-file PATH ...`): launches, total time, share and mean per kernel, largest share first.
+    With `skip_before`, launches before the first one whose kernel name contains it are left out
+    (the set-up and autotuner launches ahead of the solves)."""
+    import csv
+    rows = []
+    with open(path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    rd = csv.reader(lines)
+    hdr = next(rd)
+    ik, iu, iv = hdr.index("Kernel Name"), hdr.index("Metric Unit"), hdr.index("Metric Value")
+    scale = {"ns": 1e-3, "nsecond": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3}
+    for r in rd:
+        name = r[ik].split("(")[0].replace("void ", "")
+        rows.append((name, float(r[iv].replace(",", "")) * scale[r[iu]]))
+    if skip_before:
+        first = next((i for i, (nm, _) in enumerate(rows) if skip_before in nm), 0)
+        rows = rows[first:]
+    tot = sum(t for _, t in rows)
+    agg = {}
+    for nm, t in rows:
+        a = agg.setdefault(nm, [0, 0.0])
+        a[0] += 1
+        a[1] += t
+    print("launches=%d total_us=%.1f" % (len(rows), tot))
+    print("%-48s %8s %12s %7s %9s" % ("kernel", "launches", "total_us", "share", "mean_us"))
+    for nm, (c, t) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+        print("%-48s %8d %12.1f %6.1f%% %9.2f" % (nm[:48], c, t, 100.0 * t / tot, t / c))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1007,8 +1045,16 @@ def main():
     ap.add_argument("--nrhs", type=int, default=1, help="--profile-case: right-hand sides")
     ap.add_argument("--fixed-k", type=int, default=40, help="--profile-case: Lanczos steps / BiCG iterations")
     ap.add_argument("--pair-variant", type=int, default=-1,
-                    help="--profile-case: pin the pair-stencil shape (ovl_set_pair_variant); -1 autotunes")
+                    help="pin the pair-stencil shape of the workload (or of --profile-case) with ovl_set_pair_variant; "
+                         "-1 autotunes")
+    ap.add_argument("--summarize-launches", metavar="CSV", default=None,
+                    help="print per-kernel totals of an ncu launch list (gpu__time_duration.sum) and exit")
+    ap.add_argument("--from-kernel", default=None,
+                    help="--summarize-launches: start at the first launch of this kernel")
     args = ap.parse_args()
+    if args.summarize_launches:
+        summarize_launches(args.summarize_launches, args.from_kernel)
+        return
     if args.profile_case:
         run_profile_case(args)
         return

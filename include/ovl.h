@@ -177,6 +177,9 @@ typedef struct {
   int32_t evaluations;    /* direct method: evaluations of sign(H_j) e_1 for this rhs */
   int32_t ritz_evaluations;/* direct method: of those, the ones that computed Ritz values to choose
                               the rational scale and pole count (the others reused them) */
+  double t_finish_ms;     /* direct method: the same for the one-block kernels that finish a step's
+                             cross-block sums and scalars, where the step's shapes have them
+                             (t_kernel_ms and t_update_ms exclude them) */
 } ovl_sign_info;
 
 /* Fill p with defaults: DIRECT_2SL, F64, m_W = -2, mu = 0, tol = 1e-10, k_max = 600,

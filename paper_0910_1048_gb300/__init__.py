@@ -55,7 +55,7 @@ class ovl_sign_info(ctypes.Structure):
         ("poles", ctypes.c_int32), ("est_error", ctypes.c_double), ("t_total_ms", ctypes.c_double),
         ("t_small_ms", ctypes.c_double), ("residual", ctypes.c_double), ("t_kernel_ms", ctypes.c_double),
         ("t_update_ms", ctypes.c_double), ("kernel_samples", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
-        ("evaluations", ctypes.c_int32), ("ritz_evaluations", ctypes.c_int32),
+        ("evaluations", ctypes.c_int32), ("ritz_evaluations", ctypes.c_int32), ("t_finish_ms", ctypes.c_double),
     ]
 
     def as_dict(self):

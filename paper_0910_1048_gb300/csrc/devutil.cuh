@@ -212,16 +212,67 @@ __device__ __forceinline__ bool publish_partials(double (&v)[NV], double* part, 
   return last;
 }
 
-// Fixed-order sum of nblk partials (NV each) by the last block; result in thread 0.
+// Sum over b < count of part[b * stride + v] for the NV values v, result in thread 0: each warp
+// sums one value over a share of the partials (lane-strided, then a butterfly) and thread 0 adds
+// the shares in a fixed order. blockDim.x = 32 * NV * SPLIT. Few FP64 instructions in a short
+// dependent chain, which is what costs time on GB300's narrow FP64 pipe.
+template <int NV, int SPLIT>
+__device__ __forceinline__ void sum_partials_by_warp(const double* part, int count, int stride, double (&out)[NV]) {
+  static_assert(NV * SPLIT <= 32, "at most 32 warps");
+  __shared__ double sh[NV * SPLIT];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, v = w % NV, q = w / NV;
+  double s = 0.0;
+#pragma unroll 4
+  for (int b = q * 32 + lane; b < count; b += 32 * SPLIT) s += __ldcg(part + (size_t)b * stride + v);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) sh[w] = s;
+  __syncthreads();
+  if (t == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double a = sh[i];
+#pragma unroll
+      for (int k = 1; k < SPLIT; ++k) a += sh[k * NV + i];
+      out[i] = a;
+    }
+}
+
+// Fixed-order sum of nblk partials (NV each) by the last block; result in thread 0. With at least
+// NV warps, each warp sums one value over a share of the partials (lane-strided, then a butterfly)
+// and thread 0 adds the shares in order: on GB300 every FP64 warp instruction holds the FP64 pipe
+// for many cycles, and a tree over all warps and values costs several times more instructions.
 template <int NV>
 __device__ __forceinline__ void reduce_partials(const double* part, int nblk, double (&v)[NV]) {
   __threadfence();
+  const int nt = lin_nthreads(), t = lin_tid(), nw = nt >> 5;
+  if (nw >= NV) {
+    __shared__ double sh[32];
+    const int split = nw / NV, lane = t & 31, w = t >> 5, val = w % NV, q = w / NV;
+    double s = 0.0;
+    if (q < split) {
+#pragma unroll 4
+      for (int b = q * 32 + lane; b < nblk; b += 32 * split) s += __ldcg(part + (size_t)b * NV + val);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0 && q < split) sh[w] = s;
+    __syncthreads();
+    if (t == 0)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        double a = sh[i];
+        for (int k = 1; k < split; ++k) a += sh[k * NV + i];
+        v[i] = a;
+      }
+    __syncthreads();
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < NV; ++i) v[i] = 0.0;
   // four partials per thread per pass, loaded before they are added (one memory round trip per
   // pass instead of one per partial)
-  const int nt = lin_nthreads();
-  for (int b0 = lin_tid(); b0 < nblk; b0 += 4 * nt) {
+  for (int b0 = t; b0 < nblk; b0 += 4 * nt) {
     double x[4][NV];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {

@@ -10,6 +10,7 @@
 
 #include <map>
 #include <mutex>
+#include <set>
 #include <tuple>
 
 #include "devutil.cuh"
@@ -40,6 +41,77 @@ void set_pair_variant(int vol, int prec, int variant) {
     g_tune.erase({vol, prec});
   else
     g_tune[{vol, prec}] = variant;
+}
+
+// ------------------------------------------------------------------ one block per SM
+// Launch geometry that puts exactly one block of a kernel on every SM: a request for more than half
+// of an SM's shared memory (the kernels do not use it) keeps a second block of the same kernel off
+// the SM, so a grid of one block per SM is spread evenly whatever order the hardware hands the
+// blocks out in. (Left to the hardware, 648 equal blocks of the FP64 pair stencil at 12^4 gave the
+// busiest SM 1.3 times the mean SM time.)
+struct SmFill {
+  int nsm = 0;   // SMs of the current device (0: query failed)
+  int smem = 0;  // dynamic shared memory per block that admits one block per SM
+};
+static std::mutex g_fill_mu;
+static SmFill sm_fill(int dev) {
+  static std::map<int, SmFill> cache;
+  std::lock_guard<std::mutex> lk(g_fill_mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  SmFill r;
+  int per_sm = 0;
+  if (cudaDeviceGetAttribute(&r.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SmFill{};
+  }
+  r.smem = per_sm / 2 + 1024;
+  cache[dev] = r;
+  return r;
+}
+// Launch `kern` with one block per SM of the current device (grid (SM count, gy)), after allowing
+// it the shared-memory request once per kernel and device.
+// early = true: programmatic dependent launch (the blocks may start while the previous kernel of
+// the stream runs; the kernel waits for it with griddepcontrol.wait before reading its results).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_sm_fill(void (*kern)(KArgs...), int gy, dim3 block, cudaStream_t st, bool early,
+                                  Args... args) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const SmFill f = sm_fill(dev);
+  if (f.nsm <= 0) return cudaErrorLaunchFailure;
+  {
+    static std::set<std::pair<const void*, int>> allowed;
+    std::lock_guard<std::mutex> lk(g_fill_mu);
+    if (!allowed.count({(const void*)kern, dev})) {
+      if ((e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, f.smem)))
+        return e;
+      allowed.insert({(const void*)kern, dev});
+    }
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(f.nsm, gy);
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = f.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (early) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+static int sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sm_fill(dev).nsm;
 }
 
 // ------------------------------------------------------------------ layout conversion
@@ -334,6 +406,7 @@ __global__ void __launch_bounds__(kBlock) k_lz_start(Geom g, LzDev lz, typename 
       const int st = nr2 == 0.0 ? 3 : (sqrt(den) > 1e-14 * sqrt(nr2 * acc[3]) && den < 1e300 ? 0 : 1);
       lz.status[rhs] = st;
       lz.j[rhs] = st == 1 ? 0 : 1;
+      lz.pending[rhs] = 0;
     }
   }
 }
@@ -415,22 +488,96 @@ cudaError_t launch_lanczos_start(const Geom& g, bool f64, const LzDev& lz, const
 // follows, so that its threads only load them:
 //   vhat_{j+1} = A v_j - (sv_j alpha_j) vhat_j - (sv_{j-1} beta_{j-1}) vhat_{j-1},
 //   what_{j+1} = A^H w_j - (sw_j conj(alpha_j)) what_j - (delta_{j-1} sw_{j-1}) what_{j-1}.
-__device__ __forceinline__ void lz_alpha_finish(const LzDev& lz, int rhs, size_t o, int j, double2 swd,
-                                                const double (&pv)[4]) {
+// alpha_j = conj(sw_j) (sum of the partials), and the update coefficients in LzDev::ucoef order.
+__device__ __forceinline__ zd lz_alpha_coeffs(const LzDev& lz, size_t o, int j, double2 swd, const double (&pv)[4],
+                                              double2 (&c)[4]) {
   const zd sw = mk(swd.x, swd.y);
   const zd alpha = conj(sw) * mk(pv[0], pv[1]);
-  lz.alpha[o + j] = make_double2(alpha.re, alpha.im);
   const zd a1 = lz.sv[o + j] * alpha, b1 = sw * conj(alpha);
   zd a2 = mk(0.0, 0.0), b2 = mk(0.0, 0.0);
   if (j > 1) {
     a2 = lz.sv[o + j - 1] * ldc<double>(lz.beta, o + j - 1);
     b2 = lz.delta[o + j - 1] * ldc<double>(lz.sw, o + j - 1);
   }
+  c[0] = make_double2(a1.re, a1.im);
+  c[1] = make_double2(a2.re, a2.im);
+  c[2] = make_double2(b1.re, b1.im);
+  c[3] = make_double2(b2.re, b2.im);
+  return alpha;
+}
+
+__device__ __forceinline__ void lz_alpha_store(const LzDev& lz, int rhs, size_t o, int j, zd alpha,
+                                               const double2 (&c)[4]) {
+  lz.alpha[o + j] = make_double2(alpha.re, alpha.im);
   double2* u = lz.ucoef + (size_t)rhs * 4;
-  u[0] = make_double2(a1.re, a1.im);
-  u[1] = make_double2(a2.re, a2.im);
-  u[2] = make_double2(b1.re, b1.im);
-  u[3] = make_double2(b2.re, b2.im);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) u[i] = c[i];
+}
+
+__device__ __forceinline__ void lz_alpha_finish(const LzDev& lz, int rhs, size_t o, int j, double2 swd,
+                                                const double (&pv)[4]) {
+  double2 c[4];
+  const zd alpha = lz_alpha_coeffs(lz, o, j, swd, pv, c);
+  lz_alpha_store(lz, rhs, o, j, alpha, c);
+}
+
+struct BetaVals {
+  bool ok;    // false: breakdown (or a non-finite value)
+  double d;   // delta_j
+  double id;  // 1/delta_j = sv_{j+1}
+  zd bt;      // beta_j
+  zd swv;     // 1/conj(beta_j) = sw_{j+1}
+  double vn;  // |v_{j+1}|
+};
+
+__device__ __forceinline__ BetaVals lz_beta_vals(const double (&sums)[4]) {
+  // few FP64 operations in one dependent chain (each is slow on this GPU's FP64 pipe): with
+  // r = |ip|^-1 and id = r^(1/2) = 1/delta_j, delta_j = |ip| id, beta_j = id ip, and
+  // 1/conj(beta_j) = beta_j / |beta_j|^2 = id r ip (|beta_j|^2 = |ip|); the breakdown test on squares
+  BetaVals b{};
+  const zd ip = mk(sums[0], sums[1]);
+  const double n2 = norm2(ip);
+  b.ok = (n2 > 1e-28 * (sums[2] * sums[3])) && (n2 <= 1.7976931348623157e308);
+  if (!b.ok) return b;
+  const double r = rsqrt(n2), id = sqrt(r), idp = id * r;
+  b.id = id;
+  b.d = n2 * r * id;  // |ip| / delta_j = delta_j
+  b.bt = id * ip;
+  b.swv = mk(idp * ip.re, idp * ip.im);
+  b.vn = sqrt(sums[2]) * id;
+  return b;
+}
+
+// Stores the values of step j (b.ok) or marks the breakdown.
+__device__ __forceinline__ void lz_beta_store(const LzDev& lz, int rhs, size_t o, int j, const BetaVals& b) {
+  if (!b.ok) {
+    lz.status[rhs] = 1;
+    return;
+  }
+  lz.delta[o + j] = b.d;
+  lz.beta[o + j] = make_double2(b.bt.re, b.bt.im);
+  lz.sv[o + j + 1] = b.id;
+  lz.sw[o + j + 1] = make_double2(b.swv.re, b.swv.im);
+  lz.vnorm[o + j + 1] = b.vn;
+}
+
+// From sums = (what^H vhat re, im, |vhat|^2, |what|^2) of step j: delta_j = sqrt|what^H vhat|,
+// beta_j = what^H vhat / delta_j, the next column scales and |v_{j+1}|; j advances. A relative
+// breakdown (or a non-finite value) sets status 1 instead.
+__device__ __forceinline__ void lz_beta_finish(const LzDev& lz, int rhs, size_t o, int j, const double (&sums)[4]) {
+  const BetaVals b = lz_beta_vals(sums);
+  lz_beta_store(lz, rhs, o, j, b);
+  if (b.ok) lz.j[rhs] = j + 1;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Pair stencil: Av_j = sv_j H(mu) vhat_j, Aw_j = sw_j H(-mu) what_j (H(mu)^H = H(-mu)),
@@ -555,36 +702,61 @@ __global__ void __launch_bounds__(8 * SITES, MINB) k_lz_pair_split(Geom g, Links
   }
 }
 
-// The pair step, dynamically scheduled: a grid of as many blocks as the GPU holds at once whose
-// warps claim tasks from a counter; task t applies H(mu) to vhat_j (t even) or H(-mu) to what_j
-// (t odd) on the 32 sites of chunk t / 2. The FP64 stencil is bound by the FP64 pipe and a
-// statically scheduled grid finishes with its most loaded SM: at 12^4 ncu counted 140K / 164K /
-// 214K active cycles (min / mean / max over the SMs) for 1296 one-warp blocks, so a third of the
-// SM time idled at the end. Here every warp keeps claiming until the tasks run out. The alpha
-// partial of a chunk goes to the chunk's own slot and the last block sums the slots in chunk order:
-// the result does not depend on which warp ran which task.
-constexpr int kDynWarps = 4;  // warps per block
+// The pair step on one block per SM, all SMs with the same number of warps, whose warps claim
+// tasks from a counter; task t applies H(mu) to vhat_j (t even) or H(-mu) to what_j (t odd) on the
+// 32 sites of chunk t / 2. The FP64 stencil is bound by the FP64 pipe, so a grid finishes with its
+// most loaded SM: at 12^4 ncu counted 140K / 164K / 214K active cycles (min / mean / max over the
+// SMs) for 1296 one-warp blocks placed by the hardware. Here the 1296 tasks go to 152 x 9 warps
+// (at most 9 per SM against a mean of 8.53), and on larger lattices, with several tasks per warp,
+// a warp that finishes early claims the next. The alpha partial of a chunk goes to the chunk's own
+// slot and k_lz_alpha_finish sums the slots in chunk order: the result does not depend on which
+// warp ran which task.
+constexpr int kDynMaxWarps = 12;  // warps per block at most
 
 template <class R, int LF>
-__global__ void __launch_bounds__(32 * kDynWarps) k_lz_pair_dyn(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm,
+__global__ void __launch_bounds__(32 * kDynMaxWarps, 1) k_lz_pair_dyn(Geom g, Links U, HopCoef<R> cp, HopCoef<R> cm,
                                                                  LzDev lz, const typename V2<R>::T* vh,
                                                                  const typename V2<R>::T* wh,
                                                                  typename V2<R>::T* av, typename V2<R>::T* aw) {
   using T = typename V2<R>::T;
+  // launched early (programmatic dependent launch): the blocks are resident while the previous
+  // kernel finishes, and wait for it here (a no-op when launched the ordinary way)
+  // Launched early (programmatic dependent launch) behind k_lz_settle, which finishes the previous
+  // update: status and j are final before k_lz_settle starts (the update advanced j), so they are
+  // read now; the column scales sv_j, sw_j are read after griddepcontrol.wait, which each warp runs
+  // before its first epilogue, so the settle kernel's serial FP64 chain overlaps the stencil work.
   const int rhs = blockIdx.y;
-  if (lz.status[rhs]) return;
-  const int j = lz.j[rhs];
+  __shared__ int stat, jsh;
+  if (threadIdx.x == 0) {
+    stat = lz.status[rhs];
+    jsh = lz.j[rhs];
+  }
+  __syncthreads();
+  if (stat) return;
+  const int j = jsh;
   const size_t n = (size_t)12 * g.vol;
   const size_t o = (size_t)rhs * (lz.kmax + 2);
-  const double2 swd = lz.sw[o + j];
   const T* vj = vh + vcol(lz, rhs, j, n);
   const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
-  const double sd[3] = {lz.sv[o + j], swd.x, swd.y};
-  R sc[3];
-  scalars_in<R, 3>(sd, sc);
+  R sc[3] = {0, 0, 0};
+  bool waited = false, stop = false;
   const int lane = threadIdx.x & 31;
   const int nchunk = (g.vol + 31) >> 5;
   double* part = lz.part + (size_t)rhs * lz.nblk * 4;
+  // the scales of step j, once per warp, after the settle kernel has finished (see above); a
+  // breakdown found there stops the warp (no stores), the counters are still reset at the end
+  auto scales = [&]() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    waited = true;
+    if (lz.status[rhs]) {
+      stop = true;
+      return;
+    }
+    const double2 swd = lz.sw[o + j];
+    sc[0] = (R)lz.sv[o + j];
+    sc[1] = (R)swd.x;
+    sc[2] = (R)swd.y;
+  };
   for (;;) {
     int t = 0;
     if (lane == 0) t = (int)atomicAdd(lz.claim + rhs, 1u);
@@ -593,10 +765,13 @@ __global__ void __launch_bounds__(32 * kDynWarps) k_lz_pair_dyn(Geom g, Links U,
     const int c = t >> 1, s = c * 32 + lane;
     const bool is_w = t & 1;
     Red<R> acc[2];
-    if (s < g.vol) {
-      Spin<R> ov;
+    const bool live = s < g.vol;
+    Spin<R> ov;
+    if (live) dslash_site<LF, R>(g, U, s, is_w ? cm : cp, Loader<R, true>{is_w ? wj : vj, g.vol, false}, ov);
+    if (!waited) scales();  // warp-uniform: every lane reaches it, the status load is one value
+    if (stop) break;
+    if (live) {
       if (!is_w) {
-        dslash_site<LF, R>(g, U, s, cp, Loader<R, true>{vj, g.vol, false}, ov);
         cplx<R> wv[12];  // all loads of w_j before the stores of Av (see k_lz_pair)
 #pragma unroll
         for (int q = 0; q < 12; ++q) wv[q] = ldc<R>(wj, (size_t)q * g.vol + s);
@@ -611,7 +786,6 @@ __global__ void __launch_bounds__(32 * kDynWarps) k_lz_pair_dyn(Geom g, Links U,
         acc[0].add(a.re);
         acc[1].add(a.im);
       } else {
-        dslash_site<LF, R>(g, U, s, cm, Loader<R, true>{wj, g.vol, false}, ov);
         const cplx<R> sw = mk<R>(sc[1], sc[2]);
 #pragma unroll
         for (int q = 0; q < 12; ++q) {
@@ -633,25 +807,16 @@ __global__ void __launch_bounds__(32 * kDynWarps) k_lz_pair_dyn(Geom g, Links U,
         pc[1] = acc[1].get();
         pc[2] = 0.0;
         pc[3] = 0.0;
-        __threadfence();
       }
     }
   }
-  __syncthreads();  // every warp of the block has stopped claiming
-  __shared__ bool last;
-  if (lin_tid() == 0) {
-    __threadfence();
-    last = atomicAdd(lz.count + rhs, 1u) == gridDim.x - 1;
-    if (last) {  // no block claims any more: both counters back to zero for the next launch
-      lz.count[rhs] = 0u;
-      lz.claim[rhs] = 0u;
-    }
-  }
+  // the last block to finish resets the task counter (every block has stopped claiming by then);
+  // the chunk partials are summed by k_lz_alpha_finish or by the FP64 update's blocks
   __syncthreads();
-  if (!last) return;
-  double pv[4];
-  reduce_partials<4>(part, nchunk, pv);
-  if (lin_tid() == 0) lz_alpha_finish(lz, rhs, o, j, swd, pv);
+  if (lin_tid() == 0 && atomicAdd(lz.count + rhs, 1u) == gridDim.x - 1) {
+    lz.count[rhs] = 0u;
+    lz.claim[rhs] = 0u;
+  }
 }
 
 // vhat_{j+1} = Av_j - alpha_j v_j - beta_{j-1} v_{j-1}
@@ -663,35 +828,86 @@ __global__ void __launch_bounds__(32 * kDynWarps) k_lz_pair_dyn(Geom g, Links U,
 // give every SM the same share (324 blocks of six passes at 12^4 left the SMs idle half the time);
 // a block's partial sums sit at its own index, so the reductions keep a fixed order. The
 // coefficients come ready from the pair stencil's last block.
-template <class R>
-__global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typename V2<R>::T* vh,
+// BAL: one block per SM (launch_sm_fill), block b taking the contiguous elements
+// [b n / G, (b + 1) n / G) of its rhs, so every SM holds the same share of the FP64 work (the
+// hardware's placement of many short blocks left the busiest SM 1.4 times the mean SM time at
+// 12^4); otherwise many short grid-stride blocks.
+// XACC: the second pass of the two-pass mode (x += coef_{j+1} vhat_{j+1}), a compile-time choice:
+// as a runtime branch the compiler predicated its FP64 instructions, and predicated-off FP64
+// instructions still hold the FP64 pipe (ncu: FP64 pipe 83 % busy in the FP32 update with no FP64
+// operation executed).
+// nchunk > 0 (FP64 one-block-per-SM update after the dynamically scheduled pair stencil): every
+// block sums the stencil's nchunk chunk partials of alpha_j itself, in chunk order (so all blocks
+// get the same value), and forms the update coefficients; block 0 stores alpha_j and them. This
+// replaces a one-block finishing kernel (7.7 us under ncu at 12^4) by about a microsecond at the
+// start of every block.
+// defer (BAL only): the deferred step. The block that takes the last ticket at the start (every
+// block has read j by then) advances j and sets the pending flag; the sums of this update are
+// finished by the blocks of the next pair stencil (or by k_lz_settle) instead of a one-block kernel
+// after this one (7-10 us per step at 12^4, most of it the latency of a short serial FP64 chain).
+template <class R, bool BAL = false, bool XACC = false>
+__global__ void __launch_bounds__(BAL ? kBalBlock : kVecBlock) k_lz_update(Geom g, LzDev lz, typename V2<R>::T* vh,
                                                          typename V2<R>::T* wh, const typename V2<R>::T* av,
-                                                         const typename V2<R>::T* aw) {
+                                                         const typename V2<R>::T* aw, int nchunk, int defer) {
   using T = typename V2<R>::T;
   const int rhs = blockIdx.y;
   if (lz.status[rhs]) return;
-  const int j = lz.j[rhs];
+  __shared__ int jsh;
+  if (threadIdx.x == 0) {
+    jsh = lz.j[rhs];
+    if (BAL && defer) {
+      __threadfence();  // this block's read of j completes before its ticket
+      if (atomicAdd(lz.count + rhs, 1u) == gridDim.x - 1) {
+        lz.count[rhs] = 0u;
+        lz.j[rhs] = jsh + 1;
+        lz.pending[rhs] = 1;
+      }
+    }
+  }
+  __syncthreads();
+  const int j = jsh;
   const size_t n = (size_t)12 * g.vol;
   const size_t o = (size_t)rhs * (lz.kmax + 2);
   R u[8];  // the four complex coefficients of LzDev::ucoef
-  scalars_in<R, 8>((const double*)(lz.ucoef + (size_t)rhs * 4), u);
+  if (BAL && nchunk > 0) {
+    __shared__ double uc[8];
+    double pv[2];
+    sum_partials_by_warp<2, kBalBlock / 64>(lz.part + (size_t)rhs * lz.nblk * 4, nchunk, 4, pv);
+    if (threadIdx.x == 0) {
+      const double p4[4] = {pv[0], pv[1], 0.0, 0.0};
+      double2 c[4];
+      const zd alpha = lz_alpha_coeffs(lz, o, j, lz.sw[o + j], p4, c);
+      for (int i = 0; i < 4; ++i) {
+        uc[2 * i] = c[i].x;
+        uc[2 * i + 1] = c[i].y;
+      }
+      if (blockIdx.x == 0) lz_alpha_store(lz, rhs, o, j, alpha, c);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) u[i] = (R)uc[i];
+  } else {
+    scalars_in<R, 8>((const double*)(lz.ucoef + (size_t)rhs * 4), u);
+  }
   const cplx<R> a1 = mk<R>(u[0], u[1]), a2 = mk<R>(u[2], u[3]);
   const cplx<R> b1 = mk<R>(u[4], u[5]), b2 = mk<R>(u[6], u[7]);
   const T* vj = vh + vcol(lz, rhs, j, n);
   const T* vjm = vh + vcol(lz, rhs, j > 1 ? j - 1 : 1, n);
   T* vnew = vh + vcol(lz, rhs, j + 1, n);
-  double2* xa = lz.xacc ? lz.xacc + (size_t)rhs * n : nullptr;  // second pass: x += coef_{j+1} vhat_{j+1}
-  const zd xc = lz.xacc ? ldc<double>(lz.xcoef, o + j + 1) : mk(0.0, 0.0);
+  double2* xa = XACC ? lz.xacc + (size_t)rhs * n : nullptr;  // second pass: x += coef_{j+1} vhat_{j+1}
+  const zd xc = XACC ? ldc<double>(lz.xcoef, o + j + 1) : mk(0.0, 0.0);
   const T* wj = wh + ((size_t)(j & 1) * lz.nrhs + rhs) * n;
   T* wnew = wh + ((size_t)((j + 1) & 1) * lz.nrhs + rhs) * n;  // holds what_{j-1} until overwritten
   const T* avr = av + (size_t)rhs * n;
   const T* awr = aw + (size_t)rhs * n;
   const bool prev = j > 1;
   Red<R> acc[4];
-  const size_t step = (size_t)gridDim.x * blockDim.x * 2;
-  for (size_t e0 = (size_t)blockIdx.x * blockDim.x * 2 + threadIdx.x; e0 < n; e0 += step) {
+  const size_t hi = BAL ? n * (blockIdx.x + 1) / gridDim.x : n;
+  const size_t first = BAL ? n * blockIdx.x / gridDim.x + threadIdx.x : (size_t)blockIdx.x * blockDim.x * 2 + threadIdx.x;
+  const size_t step = BAL ? (size_t)blockDim.x * 2 : (size_t)gridDim.x * blockDim.x * 2;
+  for (size_t e0 = first; e0 < hi; e0 += step) {
     const size_t e1 = e0 + blockDim.x;
-    const bool has1 = e1 < n;
+    const bool has1 = e1 < hi;
     const cplx<R> z = mk<R>(0, 0);
     const cplx<R> A0 = ldc<R>(avr, e0), W0 = ldc<R>(awr, e0), v0 = ldc<R>(vj, e0), w0 = ldc<R>(wj, e0);
     const cplx<R> A1 = has1 ? ldc<R>(avr, e1) : z, W1 = has1 ? ldc<R>(awr, e1) : z;
@@ -715,7 +931,7 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typen
     }
     stc<R>(vnew, e0, x0);
     stc<R>(wnew, e0, y0);
-    if (xa) {  // the stored (rounded) vector, in the order of the one-pass combine
+    if constexpr (XACC) {  // the stored (rounded) vector, in the order of the one-pass combine
       const cplx<R> s0 = ldc<R>(vnew, e0);
       stc<double>(xa, e0, ldc<double>(xa, e0) + xc * mk((double)s0.re, (double)s0.im));
     }
@@ -726,7 +942,7 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typen
     if (has1) {
       stc<R>(vnew, e1, x1);
       stc<R>(wnew, e1, y1);
-      if (xa) {
+      if constexpr (XACC) {
         const cplx<R> s1 = ldc<R>(vnew, e1);
         stc<double>(xa, e1, ldc<double>(xa, e1) + xc * mk((double)s1.re, (double)s1.im));
       }
@@ -739,51 +955,101 @@ __global__ void __launch_bounds__(kVecBlock) k_lz_update(Geom g, LzDev lz, typen
   double tot[4];
   block_reduce4<R>(acc, tot);
   double* part = lz.part + (size_t)rhs * lz.nblk * 4;
+  if (BAL) {  // block partials only (above the chunk partials); k_lz_beta_finish sums them
+    if (lin_tid() == 0)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) part[(size_t)(lz.nblk - kMaxFillSMs + blockIdx.x) * 4 + i] = tot[i];
+    return;
+  }
   if (publish_partials<4>(tot, part, lz.count + rhs)) {
     double sums[4];
     reduce_partials<4>(part, gridDim.x, sums);
-    if (lin_tid() == 0) {
-      zd ip = mk(sums[0], sums[1]);
-      double aip = sqrt(norm2(ip));
-      if (!(aip > 1e-14 * sqrt(sums[2] * sums[3])) || !(aip < 1e300)) {
-        lz.status[rhs] = 1;  // breakdown (or non-finite)
-      } else {
-        double d = sqrt(aip);
-        zd bt = (1.0 / d) * ip;
-        lz.delta[o + j] = d;
-        lz.beta[o + j] = make_double2(bt.re, bt.im);
-        lz.sv[o + j + 1] = 1.0 / d;
-        double bb = norm2(bt);  // 1/conj(beta) = beta / |beta|^2
-        lz.sw[o + j + 1] = make_double2(bt.re / bb, bt.im / bb);
-        lz.vnorm[o + j + 1] = sqrt(sums[2]) / d;
-        lz.j[rhs] = j + 1;
-      }
-    }
+    if (lin_tid() == 0) lz_beta_finish(lz, rhs, o, j, sums);
   }
 }
 
-// As many blocks of k_lz_pair_dyn as the device holds at once (queried once per instance), at most
-// one warp per task.
+// The end of a balanced update or pair step in a kernel of its own (one block per rhs): the sum of
+// the partials and the scalars of the step. In the kernel that produced the partials, the last
+// block to finish did this after an atomic ticket and a memory fence per block. Every FP64 warp
+// instruction occupies GB300's FP64 pipe for many cycles (two FP64 lanes per SM and clock), so a
+// short serial FP64 chain is long: with eight warps summing all values through a block tree, the
+// update's finish took 10.2 us under ncu at 12^4. Here each warp sums one value over a share of
+// the partials (lane-strided, then a butterfly), and thread 0 adds the shares in a fixed order.
+constexpr int kFinishBlock = 256;  // 8 warps: (value, share) pairs of sum_partials_by_warp
+
+__global__ void __launch_bounds__(kFinishBlock) k_lz_beta_finish(LzDev lz, int nparts) {
+  const int rhs = blockIdx.y;
+  if (lz.status[rhs]) return;
+  const int j = lz.j[rhs];
+  double sums[4];
+  sum_partials_by_warp<4, 2>(lz.part + ((size_t)rhs * lz.nblk + lz.nblk - kMaxFillSMs) * 4, nparts, 4, sums);
+  if (threadIdx.x == 0) lz_beta_finish(lz, rhs, (size_t)rhs * (lz.kmax + 2), j, sums);
+}
+
+// The finish of a deferred update whose successor is not a pair stencil (the chunk's last step).
+__global__ void __launch_bounds__(kFinishBlock) k_lz_settle(LzDev lz, int nparts) {
+  // let the pair stencil that follows launch now (it reads the scales only after waiting for this)
+  asm volatile("griddepcontrol.launch_dependents;");
+  const int rhs = blockIdx.y;
+  __shared__ int go, jsh;
+  if (threadIdx.x == 0) {
+    go = ld_acquire(lz.pending + rhs) && !lz.status[rhs];
+    jsh = lz.j[rhs];
+  }
+  __syncthreads();
+  if (!go) return;
+  const int j = jsh;
+  double sums[4];
+  sum_partials_by_warp<4, 2>(lz.part + ((size_t)rhs * lz.nblk + lz.nblk - kMaxFillSMs) * 4, nparts, 4, sums);
+  if (threadIdx.x == 0) {
+    const BetaVals b = lz_beta_vals(sums);
+    lz_beta_store(lz, rhs, (size_t)rhs * (lz.kmax + 2), j - 1, b);
+    if (!b.ok) lz.j[rhs] = j - 1;
+    lz.pending[rhs] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kFinishBlock) k_lz_alpha_finish(LzDev lz, int nparts) {
+  const int rhs = blockIdx.y;
+  if (lz.status[rhs]) return;
+  const int j = lz.j[rhs];
+  const size_t o = (size_t)rhs * (lz.kmax + 2);
+  double pv[2];
+  sum_partials_by_warp<2, 4>(lz.part + (size_t)rhs * lz.nblk * 4, nparts, 4, pv);
+  if (threadIdx.x == 0) {
+    const double p4[4] = {pv[0], pv[1], 0.0, 0.0};
+    lz_alpha_finish(lz, rhs, o, j, lz.sw[o + j], p4);
+  }
+}
+
+// k_lz_pair_dyn on one block per SM, with as many warps as the tasks need (at most kDynMaxWarps).
+// True where the FP64 update runs one block per SM (and then, after pair variant 7, sums alpha's
+// chunk partials itself).
+static bool fp64_update_balanced() {
+  const int nsm = sm_count();
+  return nsm > 0 && nsm <= kMaxFillSMs;
+}
+
+// In the deferred FP64 step the settle kernel (the previous update's finish) runs first and the
+// stencil is launched early behind it (see k_lz_pair_dyn); `first` is recorded between them.
 template <class R, int LF>
 static cudaError_t pair_dyn_launch(const Geom& g, const Links& U, const HopCoef<R>& cp, const HopCoef<R>& cm,
-                                   const LzDev& lz, const LzVecs& vec, cudaStream_t st) {
-  static const int resident = [] {
-    int dev = 0, nsm = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lz_pair_dyn<R, LF>, 32 * kDynWarps, 0) !=
-            cudaSuccess) {
-      cudaGetLastError();
-      return 0;
-    }
-    return nsm * per_sm;
-  }();
-  if (resident <= 0) return cudaErrorLaunchFailure;
+                                   const LzDev& lz, const LzVecs& vec, cudaStream_t st, cudaEvent_t first,
+                                   cudaEvent_t mid) {
+  const int nsm = std::max(1, sm_count());
   const int ntask = 2 * ((g.vol + 31) >> 5);
-  const int nb = std::max(1, std::min(resident, (ntask + kDynWarps - 1) / kDynWarps));
+  const int warps = std::max(1, std::min(kDynMaxWarps, (ntask + nsm - 1) / nsm));
   using T = typename V2<R>::T;
-  return launch_plain(k_lz_pair_dyn<R, LF>, dim3(nb, lz.nrhs), dim3(32 * kDynWarps), st, g, U, cp, cm, lz,
-                      (const T*)vec.vh, (const T*)vec.wh, (T*)vec.av, (T*)vec.aw);
+  const bool deferred = sizeof(R) == 8 && fp64_update_balanced();
+  cudaError_t e;
+  if (deferred && (e = launch_plain(k_lz_settle, dim3(1, lz.nrhs), dim3(kFinishBlock), st, lz, nsm))) return e;
+  if (first && (e = record_timing(first, st))) return e;
+  e = launch_sm_fill(k_lz_pair_dyn<R, LF>, lz.nrhs, dim3(32 * warps), st, deferred, g, U, cp, cm, lz,
+                     (const T*)vec.vh, (const T*)vec.wh, (T*)vec.av, (T*)vec.aw);
+  if (e != cudaSuccess) return e;
+  if (mid && (e = record_timing(mid, st))) return e;
+  if (sizeof(R) == 8 && fp64_update_balanced()) return cudaSuccess;  // the update's blocks finish alpha
+  return launch_plain(k_lz_alpha_finish, dim3(1, lz.nrhs), dim3(kFinishBlock), st, lz, ntask / 2);
 }
 
 template <int PS, bool ONE_ROLE = false>
@@ -817,15 +1083,24 @@ static cudaError_t pair_split_launch(const Geom& g, const Links& U, int lf, bool
                       (const float2*)vec.vh, (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
 }
 
+int resolve_pair_variant(const Geom& g, int lf, bool f64) {
+  const int v = tuned_pair_variant(g.vol, f64 ? 0 : lf);
+  return v >= 0 ? v : (use_split(g) ? 1 : 0);
+}
+
+// FP64 steps with pair shape 7 and the one-block-per-SM update run deferred (see k_lz_update).
+static bool deferred_step(bool f64, int variant) { return f64 && variant == 7 && fp64_update_balanced(); }
+
 cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
-                                const LzDev& lz, const LzVecs& vec, cudaStream_t st, int variant) {
-  if (variant < 0) variant = tuned_pair_variant(g.vol, f64 ? 0 : lf);
-  if (variant < 0) variant = use_split(g) ? 1 : 0;
+                                const LzDev& lz, const LzVecs& vec, cudaStream_t st, int variant, cudaEvent_t mid,
+                                cudaEvent_t first) {
+  if (variant < 0) variant = resolve_pair_variant(g, lf, f64);
   const HopCoef<double> dp = hop_coef<double>(m_w, mu), dm = hop_coef<double>(m_w, -mu);
   const HopCoef<float> fp = hop_coef<float>(m_w, mu), fm = hop_coef<float>(m_w, -mu);
   const double2 *dv = (const double2*)vec.vh, *dw = (const double2*)vec.wh;
   const float2 *fv = (const float2*)vec.vh, *fw = (const float2*)vec.wh;
   cudaError_t e;
+  if (variant != 7 && first && (e = record_timing(first, st))) return e;
   if (variant == 1) {
     e = pair_split_launch<1, kSplitSites>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
   } else if (variant == 4) {  // held to 128 registers: two blocks per SM
@@ -839,35 +1114,76 @@ cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64,
   } else if (variant == 6) {
     e = pair_unsplit<32, true>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
   } else if (variant == 7) {
-    e = f64 ? pair_dyn_launch<double, LINK_F64>(g, U, dp, dm, lz, vec, st)
-            : lf == LINK_F16R12 ? pair_dyn_launch<float, LINK_F16R12>(g, U, fp, fm, lz, vec, st)
-                                : pair_dyn_launch<float, LINK_F32>(g, U, fp, fm, lz, vec, st);
+    e = f64 ? pair_dyn_launch<double, LINK_F64>(g, U, dp, dm, lz, vec, st, first, mid)
+            : lf == LINK_F16R12 ? pair_dyn_launch<float, LINK_F16R12>(g, U, fp, fm, lz, vec, st, first, mid)
+                                : pair_dyn_launch<float, LINK_F32>(g, U, fp, fm, lz, vec, st, first, mid);
+    first = mid = nullptr;  // recorded around the stencil kernel
   } else {
     e = pair_unsplit<kPairSites>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
   }
+  if (e == cudaSuccess && mid) e = record_timing(mid, st);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-cudaError_t launch_lanczos_update(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, cudaStream_t st) {
-  // FP64: two elements per thread, one pass (see k_lz_update); FP32: enough elements per thread to
-  // amortise the block reduction, at least four blocks per SM over the batch
+cudaError_t launch_lanczos_update(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, cudaStream_t st,
+                                  int variant, cudaEvent_t mid) {
+  // FP64 (bound by the FP64 pipe): one block per SM with an equal share of the elements; FP32
+  // (bound by HBM): enough elements per thread to amortise the block reduction, at least four
+  // blocks per SM over the batch
   const int elt = f64 ? 2 : std::max(2, (vec_elts(g, lz.nrhs, false) + 1) & ~1);
   dim3 grid(vec_blocks(g, elt), lz.nrhs);
   cudaError_t e;
-  if (f64)
-    e = launch_plain(k_lz_update<double>, grid, dim3(kVecBlock), st, g, lz, (double2*)vec.vh, (double2*)vec.wh,
-                   (const double2*)vec.av, (const double2*)vec.aw);
-  else
-    e = launch_plain(k_lz_update<float>, grid, dim3(kVecBlock), st, g, lz, (float2*)vec.vh, (float2*)vec.wh,
-                   (const float2*)vec.av, (const float2*)vec.aw);
+  const int nsm = f64 ? sm_count() : 0;
+  const bool xacc = lz.xacc != nullptr;
+  if (f64 && fp64_update_balanced()) {
+    // after pair variant 7 the blocks sum alpha's chunk partials themselves, and the step is deferred
+    const int nchunk = variant == 7 ? (g.vol + 31) >> 5 : 0;
+    const int defer = deferred_step(f64, variant) ? 1 : 0;
+    e = xacc ? launch_sm_fill(k_lz_update<double, true, true>, lz.nrhs, dim3(kBalBlock), st, false, g, lz,
+                              (double2*)vec.vh, (double2*)vec.wh, (const double2*)vec.av, (const double2*)vec.aw,
+                              nchunk, defer)
+             : launch_sm_fill(k_lz_update<double, true, false>, lz.nrhs, dim3(kBalBlock), st, false, g, lz,
+                              (double2*)vec.vh, (double2*)vec.wh, (const double2*)vec.av, (const double2*)vec.aw,
+                              nchunk, defer);
+    if (e == cudaSuccess && mid) e = record_timing(mid, st);
+    mid = nullptr;
+    if (e == cudaSuccess && !defer)
+      e = launch_plain(k_lz_beta_finish, dim3(1, lz.nrhs), dim3(kFinishBlock), st, lz, nsm);
+  } else if (f64) {
+    e = xacc ? launch_plain(k_lz_update<double, false, true>, grid, dim3(kVecBlock), st, g, lz, (double2*)vec.vh,
+                            (double2*)vec.wh, (const double2*)vec.av, (const double2*)vec.aw, 0, 0)
+             : launch_plain(k_lz_update<double, false, false>, grid, dim3(kVecBlock), st, g, lz, (double2*)vec.vh,
+                            (double2*)vec.wh, (const double2*)vec.av, (const double2*)vec.aw, 0, 0);
+  } else {
+    e = xacc ? launch_plain(k_lz_update<float, false, true>, grid, dim3(kVecBlock), st, g, lz, (float2*)vec.vh,
+                            (float2*)vec.wh, (const float2*)vec.av, (const float2*)vec.aw, 0, 0)
+             : launch_plain(k_lz_update<float, false, false>, grid, dim3(kVecBlock), st, g, lz, (float2*)vec.vh,
+                            (float2*)vec.wh, (const float2*)vec.av, (const float2*)vec.aw, 0, 0);
+  }
+  if (e == cudaSuccess && mid) e = record_timing(mid, st);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_lanczos_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, const LzDev& lz,
-                                const LzVecs& vec, cudaStream_t st) {
-  cudaError_t e = launch_lanczos_pair(g, U, lf, f64, m_w, mu, lz, vec, st);
+                                const LzVecs& vec, cudaStream_t st, int variant) {
+  cudaError_t e = launch_lanczos_pair(g, U, lf, f64, m_w, mu, lz, vec, st, variant);
   if (e != cudaSuccess) return e;
-  return launch_lanczos_update(g, f64, lz, vec, st);
+  return launch_lanczos_update(g, f64, lz, vec, st, variant);
+}
+
+cudaError_t launch_lanczos_settle(const Geom& g, bool f64, const LzDev& lz, cudaStream_t st, int variant) {
+  if (!deferred_step(f64, variant)) return cudaSuccess;
+  return launch_plain(k_lz_settle, dim3(1, lz.nrhs), dim3(kFinishBlock), st, lz, sm_count());
+}
+
+int lanczos_settle_launches(bool f64, int variant) { return deferred_step(f64, variant) ? 1 : 0; }
+
+int lanczos_step_launches(const Geom& g, int lf, bool f64, int variant) {
+  (void)g;
+  (void)lf;
+  const bool bal = f64 && fp64_update_balanced();
+  if (deferred_step(f64, variant)) return 3;  // settle, stencil, update
+  return (variant == 7 && !bal ? 2 : 1) + (bal ? 2 : 1);
 }
 
 // ------------------------------------------------------------------ combine

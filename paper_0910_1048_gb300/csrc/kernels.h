@@ -57,6 +57,7 @@ int tune_pair_variant(int vol, int prec, int (*measure)(void*), void* arg);
 // Sets the entry (variant >= 0) or removes it (-1).
 void set_pair_variant(int vol, int prec, int variant);
 constexpr int kVecBlock = 128;  // threads per block of the element-parallel vector kernels
+constexpr int kBalBlock = 512;  // threads per block of the one-block-per-SM FP64 update
 inline unsigned vec_blocks(const Geom& g) { return (unsigned)((12 * (size_t)g.vol + kVecBlock - 1) / kVecBlock); }
 // Elements per thread of the element-parallel kernels: enough to amortise the per-thread set-up and
 // the block reduction, while keeping at least about four (FP32) or two (FP64) blocks per SM over the
@@ -69,8 +70,11 @@ inline int vec_elts(const Geom& g, int nrhs, bool f64) {
 inline unsigned vec_blocks(const Geom& g, int elt) {
   return (unsigned)((12 * (size_t)g.vol + (size_t)kVecBlock * elt - 1) / ((size_t)kVecBlock * elt));
 }
-// partial-sum slots per rhs: the most blocks any reduction kernel launches (the element-parallel ones)
-inline int partial_slots(const Geom& g) { return (int)vec_blocks(g); }
+// partial-sum slots per rhs: the most blocks any reduction kernel launches (the element-parallel
+// ones), plus kMaxFillSMs at the top for the one-block-per-SM FP64 update, whose block partials
+// must not overwrite the pair stencil's chunk partials that its blocks are still reading
+constexpr int kMaxFillSMs = 256;  // the one-block-per-SM kernels run on GPUs with at most this many SMs
+inline int partial_slots(const Geom& g) { return (int)vec_blocks(g) + kMaxFillSMs; }
 
 // Device state of the two-sided Lanczos recurrences for nrhs right-hand sides.
 // Index conventions: column j = 1..kmax+1 of the basis, stored at slot (j - 1) % vcols; scalars
@@ -91,6 +95,7 @@ struct LzDev {
   double* part = nullptr;   // [nrhs][nblk][4] block partials
   unsigned* count = nullptr;// [nrhs] last-block counters (kept at 0 between launches)
   unsigned* claim = nullptr;// [nrhs] task counters of the dynamically scheduled pair stencil (kept at 0)
+  int* pending = nullptr;   // [nrhs] 1: the last update's sums await their finish (deferred mode)
   int vcols = 0;            // basis columns kept per rhs: kmax + 1, or 3 (two-pass: a rotating window)
   double2* xacc = nullptr;  // two-pass, second pass: [nrhs][12][V] FP64 sum of coef_j vhat_j so far
   const double2* xcoef = nullptr;  // two-pass: [nrhs][kmax + 2] coefficient of column j (0 beyond k)
@@ -130,13 +135,30 @@ cudaError_t launch_defl_dots(const Geom& g, int nrhs, int m, const double2* b, c
 cudaError_t launch_lanczos_start(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, const double2* b,
                                  int m, const double2* R, const double2* L, const double* lam_sign,
                                  double2* dots, cudaStream_t st);
-// The two launches of step j (read from lz.j): pair stencil + alpha, biorthogonal update.
+// A step = pair stencil (+ alpha), then the biorthogonal update. `variant` is the pair shape of the
+// solve (resolve_pair_variant once per solve, then the same value for every launch of it): with
+// shape 7 in FP64 the step runs deferred (the update's sums are finished by a settle kernel that
+// the next pair launch runs first, with the stencil launched early behind it; after a chunk's last
+// step launch_lanczos_settle finishes them before the host reads the scalars).
+int resolve_pair_variant(const Geom& g, int lf, bool f64);
+// Kernels one Lanczos step launches.
+int lanczos_step_launches(const Geom& g, int lf, bool f64, int variant);
+// `mid`, when given, is recorded (record_timing) after the stencil or update kernel itself, before the
+// one-block finishing kernel of the shapes that have one (or right after the single kernel).
+// `first`, when given, is recorded right before the stencil kernel (after the settle kernel that
+// precedes it in a deferred step).
 cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
-                                const LzDev& lz, const LzVecs& vec, cudaStream_t st, int variant = -1);
-cudaError_t launch_lanczos_update(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, cudaStream_t st);
+                                const LzDev& lz, const LzVecs& vec, cudaStream_t st, int variant,
+                                cudaEvent_t mid = nullptr, cudaEvent_t first = nullptr);
+cudaError_t launch_lanczos_update(const Geom& g, bool f64, const LzDev& lz, const LzVecs& vec, cudaStream_t st,
+                                  int variant, cudaEvent_t mid = nullptr);
+// Finishes a deferred step (no-op otherwise): after the last step of a chunk, before the host or a
+// later kernel reads alpha, beta, delta, the scales, |v|, j or the status.
+cudaError_t launch_lanczos_settle(const Geom& g, bool f64, const LzDev& lz, cudaStream_t st, int variant);
+int lanczos_settle_launches(bool f64, int variant);  // 1 where launch_lanczos_settle launches a kernel
 // One step j (read from lz.j): pair stencil + alpha, then the biorthogonal update.
 cudaError_t launch_lanczos_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu,
-                                const LzDev& lz, const LzVecs& vec, cudaStream_t st);
+                                const LzDev& lz, const LzVecs& vec, cudaStream_t st, int variant);
 // Element sampling of the stopping estimate: the norms ||V c|| of the change and of the iterate
 // enter only as a ratio, so on large lattices they are taken over runs of 32 consecutive
 // elements, one run in every 32 * stride (about 10^5 elements sampled; a fixed pattern, so the

@@ -330,7 +330,10 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_update(Geom g, MsDev ms, MsVec
 // the FP32 rate); with per-shift solutions kept (refinement), x^(i) is held in float-float
 // (re hi, re lo, im hi, im lo: the 16 bytes of a complex double) during the pass, so the
 // increments alpha^i p^i need no FP64 arithmetic; it is converted to FP64 in place afterwards.
-template <class R>
+// XS: per-shift solutions kept (v.xs set), a compile-time choice so that neither path's
+// instructions are issued predicated-off in the other (predicated-off FP64 instructions still hold
+// the FP64 pipe).
+template <class R, bool XS>
 __global__ void __launch_bounds__(kVecBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs v) {
   using T = typename V2<R>::T;
   const int rhs = blockIdx.y;
@@ -370,13 +373,13 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs 
   double2* X = v.X + voff<R>(rhs, n);
   {
     const cplx<R> rv = ldc<R>(r, e);
-    zd xa = v.xs ? mk(0.0, 0.0) : ldc<double>(X, e);  // X is not used when x^(i) are kept
+    zd xa = XS ? mk(0.0, 0.0) : ldc<double>(X, e);  // X is not used when x^(i) are kept
     Red<R> sre, sim;  // FP32: this iteration's sum over the shifts
     for (int i = 0; i < ms.s; ++i) {
       if (!act[i]) continue;
       T* pi = ps + (size_t)i * n;
       const cplx<R> pv = ldc<R>(pi, e);
-      if (v.xs) {  // keep x^(i) itself: x^(i) += alpha^i p^i
+      if constexpr (XS) {  // keep x^(i) itself: x^(i) += alpha^i p^i
         const T2 ca = coefa[i];
         if constexpr (sizeof(R) == 8) {
           double2* xi = v.xs + ((size_t)rhs * ms.s + i) * n;
@@ -404,7 +407,7 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_dirs(Geom g, MsDev ms, MsVecs 
         stc<R>(pi, e, nv);
       }
     }
-    if (!v.xs) {
+    if constexpr (!XS) {
       if constexpr (sizeof(R) == 4) {
         xa.re += sre.get();
         xa.im += sim.get();
@@ -453,7 +456,9 @@ static cudaError_t ms_step_t(const Geom& g, const Links& U, double m_w, double m
   if (e) return e;
   if ((e = launch_plain(k_ms_update<R>, dim3(vec_blocks(g, elt), ms.nrhs), dim3(kVecBlock), st, g, ms, v, elt))) return e;
   if (ev && (e = record_timing(ev[2], st))) return e;
-  if ((e = launch_plain(k_ms_dirs<R>, grid, dim3(kVecBlock), st, g, ms, v))) return e;
+  if ((e = v.xs ? launch_plain(k_ms_dirs<R, true>, grid, dim3(kVecBlock), st, g, ms, v)
+                : launch_plain(k_ms_dirs<R, false>, grid, dim3(kVecBlock), st, g, ms, v)))
+    return e;
   if (ev && (e = record_timing(ev[3], st))) return e;
   return cudaGetLastError();
 }

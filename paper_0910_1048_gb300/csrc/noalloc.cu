@@ -134,7 +134,7 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   size_t o_sv = take((size_t)nrhs * ks * 8), o_sw = take((size_t)nrhs * ks * 16);
   size_t o_al = take((size_t)nrhs * ks * 16), o_be = take((size_t)nrhs * ks * 16);
   size_t o_de = take((size_t)nrhs * ks * 8), o_vn = take((size_t)nrhs * ks * 8), o_b0 = take((size_t)nrhs * 8);
-  size_t o_pa = take((size_t)nrhs * std::max(m, 1) * nblk * 4 * 8), o_cn = take((size_t)nrhs * 8);
+  size_t o_pa = take((size_t)nrhs * std::max(m, 1) * nblk * 4 * 8), o_cn = take((size_t)nrhs * 12);
   size_t o_uc = take((size_t)nrhs * 4 * 16);
   size_t o_do = take((size_t)nrhs * 2 * std::max(m, 1) * 16), o_ls = take((size_t)std::max(m, 1) * 8);
   size_t o_co = take((size_t)nrhs * kmax * 16), o_kr = take((size_t)nrhs * 4);
@@ -164,6 +164,7 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   lz.part = (double*)(base + o_pa);
   lz.count = (unsigned*)(base + o_cn);
   lz.claim = lz.count + nrhs;
+  lz.pending = (int*)(lz.claim + nrhs);
   lz.ucoef = (double2*)(base + o_uc);
   LzVecs vec;
   vec.vh = base + o_vh;
@@ -181,7 +182,7 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
   unsigned* ncount = (unsigned*)(base + o_nc);
   double* nout = (double*)(base + o_no);
   // the array keeps the previous call's contents: the block counters must start at zero
-  OVL_CHECK_CUDA(cudaMemsetAsync(lz.count, 0, (size_t)nrhs * 8, st));
+  OVL_CHECK_CUDA(cudaMemsetAsync(lz.count, 0, (size_t)nrhs * 12, st));
   OVL_CHECK_CUDA(cudaMemsetAsync(ncount, 0, (size_t)nrhs * 4, st));
   std::vector<double> ls(std::max(m, 1));
   for (int i = 0; i < m; ++i) ls[i] = lat->src()->defl.lam[2 * i] >= 0 ? 1.0 : -1.0;
@@ -268,11 +269,14 @@ extern "C" ovl_status ovl_apply_sign_noalloc(ovl_lattice* lat, const ovl_sign_pa
     return OVL_OK;
   };
   int queued = 0, launches = 1 + (m > 0 ? 1 : 0) + 1;
+  const int pvar = resolve_pair_variant(g, lf, f64);  // one shape for every step of this call
   while (queued < kmax) {
     int ns = std::min(chunk, kmax - queued);
-    for (int i = 0; i < ns; ++i) OVL_CHECK_CUDA(launch_lanczos_step(g, U, lf, f64, p->m_W, p->mu, lz, vec, st));
+    for (int i = 0; i < ns; ++i)
+      OVL_CHECK_CUDA(launch_lanczos_step(g, U, lf, f64, p->m_W, p->mu, lz, vec, st, pvar));
+    OVL_CHECK_CUDA(launch_lanczos_settle(g, f64, lz, st, pvar));  // before the scalars are read
     queued += ns;
-    launches += 2 * ns;
+    launches += lanczos_step_launches(g, lf, f64, pvar) * ns + lanczos_settle_launches(f64, pvar);
     if (fixed) continue;
     OVL_CHECK_CUDA(snapshot());
     const bool final_snapshot = queued >= kmax;

@@ -54,9 +54,11 @@ struct DirectWS {
   void* h_block = nullptr;
   bool pageable = false;  // server views: host mirrors in pageable memory (no pinned alloc/free)
   // two graphs of `gchunk - 1` steps (alternating chunks); graph q records timing events around
-  // its middle step's pair stencil (tev[q][0..1]) and update (tev[q][2..3])
+  // its middle step's pair stencil (tev[q][0..1]) and update (tev[q][2..3]); tev[q][4] / [5] mark the
+  // end of the stencil / update kernel itself, before a finishing kernel, and tev[q][6] the start of
+  // the stencil kernel after the settle kernel of a deferred step
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  cudaEvent_t tev[2][4] = {};
+  cudaEvent_t tev[2][7] = {};
   int gchunk = 0;
   double g_mw = 0, g_mu = 0;
   int g_lf = -1;
@@ -138,7 +140,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   size_t o_vn = take((size_t)nrhs * ks * 8);
   size_t o_b0 = take((size_t)nrhs * 8);
   size_t o_pa = take((size_t)nrhs * std::max(m, 1) * nblk * 4 * 8);
-  size_t o_cn = take((size_t)nrhs * 8);  // last-block counters, then task counters
+  size_t o_cn = take((size_t)nrhs * 12);  // last-block counters, task counters, pending flags
   size_t o_uc = take((size_t)nrhs * 4 * 16);
   size_t o_do = take((size_t)nrhs * 2 * std::max(m, 1) * 16);
   size_t o_ls = take((size_t)std::max(m, 1) * 8);
@@ -195,6 +197,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   lz.part = (double*)(base + o_pa);
   lz.count = (unsigned*)(base + o_cn);
   lz.claim = lz.count + nrhs;
+  lz.pending = (int*)(lz.claim + nrhs);
   lz.ucoef = (double2*)(base + o_uc);
   w->dots = (double2*)(base + o_do);
   w->lam_sign = (double*)(base + o_ls);
@@ -212,7 +215,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
     w->xacc = (double2*)(base + o_xa);
     w->xcoef = (double2*)(base + o_xc);
   }
-  if (cudaMemsetAsync(lz.count, 0, (size_t)nrhs * 8, w->stream) != cudaSuccess ||
+  if (cudaMemsetAsync(lz.count, 0, (size_t)nrhs * 12, w->stream) != cudaSuccess ||
       cudaMemsetAsync(w->ncount, 0, (size_t)nrhs * 4, w->stream) != cudaSuccess) {
     free_direct_ws(w);
     set_error("apply_sign: cudaMemset failed");
@@ -245,7 +248,7 @@ static ovl_status ensure_ws(ovl_lattice* lat, int nrhs, int kmax, bool f64, int 
   }
   bool ev_ok = true;
   for (int q = 0; q < 2; ++q)
-    for (int i = 0; i < 4; ++i) ev_ok = ev_ok && cudaEventCreate(&w->tev[q][i]) == cudaSuccess;
+    for (int i = 0; i < 7; ++i) ev_ok = ev_ok && cudaEventCreate(&w->tev[q][i]) == cudaSuccess;
   if (!ev_ok || cudaEventCreateWithFlags(&w->ev, cudaEventDisableTiming) != cudaSuccess) {
     free_direct_ws(w);
     set_error("apply_sign: cannot create stream/event");
@@ -456,15 +459,18 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
     return ok ? pick : -1;
   };
   tune_pair_variant(g.vol, f64 ? 0 : lf, measure, &targ);
+  const int pvar = resolve_pair_variant(g, lf, f64);  // one shape for every step of this solve
   const int chunk = std::max(1, std::min(p->check_every > 0 ? p->check_every : 20, kmax));
   // one step, with timing events around its two launches when `tev` is given
   auto step = [&](cudaEvent_t* tev) -> cudaError_t {
     cudaError_t e;
     if (tev && (e = record_timing(tev[0], st))) return e;
-    if ((e = launch_lanczos_pair(g, U, lf, f64, p->m_W, p->mu, w->lz, vec, st))) return e;
+    if ((e = launch_lanczos_pair(g, U, lf, f64, p->m_W, p->mu, w->lz, vec, st, pvar, tev ? tev[4] : nullptr,
+                                 tev ? tev[6] : nullptr)))
+      return e;
     if (tev && (e = record_timing(tev[1], st))) return e;
     if (tev && (e = record_timing(tev[2], st))) return e;
-    if ((e = launch_lanczos_update(g, f64, w->lz, vec, st))) return e;
+    if ((e = launch_lanczos_update(g, f64, w->lz, vec, st, pvar, tev ? tev[5] : nullptr))) return e;
     if (tev && (e = record_timing(tev[3], st))) return e;
     return cudaSuccess;
   };
@@ -500,24 +506,32 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
     w->g_lf = lf;
   }
   int launches = 1 + (m > 0 ? 1 : 0) + 1;  // start (+ deflation dots) and the combine
+  // the chunk's steps, then the finish of a deferred last step (before the scalars are read)
   auto run_steps = [&](int nsteps, int q) -> cudaError_t {
-    launches += 2 * nsteps;
+    launches += lanczos_step_launches(g, lf, f64, pvar) * nsteps + lanczos_settle_launches(f64, pvar);
     const bool graph = use_graph && nsteps == chunk;
     cudaError_t e = step(graph ? nullptr : w->tev[q]);
-    if (e != cudaSuccess || nsteps == 1) return e;
-    if (graph) return cudaGraphLaunch(w->graph[q], st);
-    for (int i = 1; i < nsteps; ++i)
-      if ((e = step(nullptr)) != cudaSuccess) return e;
-    return cudaSuccess;
+    if (e != cudaSuccess) return e;
+    if (graph) {
+      if ((e = cudaGraphLaunch(w->graph[q], st))) return e;
+    } else {
+      for (int i = 1; i < nsteps; ++i)
+        if ((e = step(nullptr)) != cudaSuccess) return e;
+    }
+    return launch_lanczos_settle(g, f64, w->lz, st, pvar);
   };
-  double t_pair = 0, t_upd = 0;
+  double t_pair = 0, t_upd = 0, t_fin = 0;
   int nsamp = 0;
   auto sample = [&](int q) {  // durations of the sampled step of the chunk behind slot q
-    float a = 0, b = 0;
-    if (cudaEventElapsedTime(&a, w->tev[q][0], w->tev[q][1]) == cudaSuccess &&
-        cudaEventElapsedTime(&b, w->tev[q][2], w->tev[q][3]) == cudaSuccess) {
+    float a = 0, b = 0, f0 = 0, fa = 0, fb = 0;
+    if (cudaEventElapsedTime(&a, w->tev[q][6], w->tev[q][4]) == cudaSuccess &&
+        cudaEventElapsedTime(&b, w->tev[q][2], w->tev[q][5]) == cudaSuccess &&
+        cudaEventElapsedTime(&f0, w->tev[q][0], w->tev[q][6]) == cudaSuccess &&
+        cudaEventElapsedTime(&fa, w->tev[q][4], w->tev[q][1]) == cudaSuccess &&
+        cudaEventElapsedTime(&fb, w->tev[q][5], w->tev[q][3]) == cudaSuccess) {
       t_pair += a;
       t_upd += b;
+      t_fin += f0 + fa + fb;
       ++nsamp;
     }
     cudaGetLastError();  // a failed timing query must not surface as a launch error later
@@ -729,11 +743,13 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
     };
     OVL_CHECK_CUDA(retire(1));
     for (int j = 1; j < kmax2; ++j) {  // step j adds column j + 1
-      OVL_CHECK_CUDA(launch_lanczos_pair(g, U, lf, f64, p->m_W, p->mu, lz2, vec, st));
-      OVL_CHECK_CUDA(launch_lanczos_update(g, f64, lz2, vec, st));
-      launches += 2;
+      OVL_CHECK_CUDA(launch_lanczos_pair(g, U, lf, f64, p->m_W, p->mu, lz2, vec, st, pvar));
+      OVL_CHECK_CUDA(launch_lanczos_update(g, f64, lz2, vec, st, pvar));
+      launches += lanczos_step_launches(g, lf, f64, pvar);
       OVL_CHECK_CUDA(retire(j + 1));
     }
+    OVL_CHECK_CUDA(launch_lanczos_settle(g, f64, lz2, st, pvar));
+    launches += lanczos_settle_launches(f64, pvar);
     OVL_CHECK_CUDA(launch_ms_finish(g, nrhs, w->xacc, vec.xp, xd, st));
   }
   if (p->host_io) OVL_CHECK_CUDA(cudaMemcpyAsync(x, w->xdev, (size_t)nrhs * n * 16, cudaMemcpyDeviceToHost, st));
@@ -751,6 +767,7 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
       info[r].residual = 0;
       info[r].t_kernel_ms = nsamp ? t_pair / nsamp : 0;
       info[r].t_update_ms = nsamp ? t_upd / nsamp : 0;
+      info[r].t_finish_ms = nsamp ? t_fin / nsamp : 0;
       info[r].kernel_samples = nsamp;
       info[r].kernel_launches = launches;
       info[r].evaluations = rs[r].evals;
@@ -767,7 +784,9 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
 
 size_t direct_footprint(int vol, int nrhs, int kmax, bool f64) {
   const size_t n = (size_t)12 * vol, elt = f64 ? 16 : 8;
-  return (size_t)nrhs * ((size_t)(kmax + 1) * n * elt + 4 * n * elt + 3 * n * 16) + ((size_t)1 << 20);
+  const size_t slots = (n + kVecBlock - 1) / kVecBlock + kMaxFillSMs;  // partial_slots
+  return (size_t)nrhs * ((size_t)(kmax + 1) * n * elt + 4 * n * elt + 3 * n * 16 + 16 * slots * 32) +
+         ((size_t)1 << 20);
 }
 
 }  // namespace ovl

@@ -616,10 +616,11 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
 // largest), for the server's admission.
 size_t multishift_footprint(int vol, int nrhs, int s, bool f64, bool refine) {
   const size_t n = (size_t)12 * vol, elt = f64 ? 16 : 8, nr = (size_t)nrhs;
-  size_t b = nr * n * (8 * elt + (size_t)s * elt + 5 * 16);
+  const size_t slots = (n + kVecBlock - 1) / kVecBlock + kMaxFillSMs;  // partial_slots
+  size_t b = nr * n * (8 * elt + (size_t)s * elt + 5 * 16) + nr * 16 * slots * 32;  // (deflation dots: m <= 16)
   if (refine) {
     const size_t gq = std::min<size_t>(nr * s, kRefineGroup);
-    b += nr * s * n * 16 + nr * n * 16 + gq * n * (4 * 16 + 9 * 8 + 16);
+    b += nr * s * n * 16 + nr * n * 16 + gq * n * (4 * 16 + 9 * 8 + 16) + gq * slots * 32;
   }
   return b + ((size_t)1 << 20);
 }
