@@ -684,7 +684,8 @@ def run_ours(args, wl):
 
 
 SERVING = dict(sizes=(4, 8, 12, 16), fields_per_size=5, tols=(1e-6, 1e-8, 1e-10), nrhs_max=8, seed=42,
-               k_max_by_tol={1e-6: 600, 1e-8: 1200, 1e-10: 2000}, k_max_cap={4: 2000, 8: 2000, 12: 2000, 16: 1500},
+               k_max_by_tol={1e-6: 1500, 1e-8: 3000, 1e-10: 5000}, k_max_cap={4: 5000, 8: 5000, 12: 5000, 16: 5000},
+               two_pass_over_bytes=25 << 30,
                mean_interarrival_s=0.25)
 
 
@@ -723,7 +724,11 @@ def _serving_run(ovl, srv, ids, reqs, mean_gap_s):
         while i < len(reqs) and now >= t_next:
             r = reqs[i]
             k_max = min(cfg["k_max_by_tol"][r["tol"]], cfg["k_max_cap"][r["L"]])
-            tk = ovl.ovl_submit(srv, ids[r["fi"]], r["b"], r["mu"], r["tol"], k_max=k_max)
+            # the two-pass strategy (O(n) memory) where the basis of one request would take more than
+            # an eighth of the budget (8 slots)
+            basis = r["nrhs"] * (k_max + 1) * 12 * r["L"] ** 4 * 16
+            tk = ovl.ovl_submit(srv, ids[r["fi"]], r["b"], r["mu"], r["tol"], k_max=k_max,
+                                two_pass=int(basis > cfg["two_pass_over_bytes"]))
             pending[tk] = (r, now)
             i += 1
             if i < len(reqs):
@@ -748,9 +753,14 @@ def _serving_stats(ovl, done, wall):
     per_size = {}
     for r, d, _, _ in done:
         per_size.setdefault("%d^4" % r["L"], []).append(1e3 * d)
+    statuses = {}
+    for r, _, _, info in done:
+        for inf in info[:r["nrhs"]]:
+            nm = ovl.STATUS_NAMES.get(inf["status"], str(inf["status"]))
+            statuses[nm] = statuses.get(nm, 0) + 1
     return {"requests": len(done), "sources": sources, "wall_s": wall, "solves_per_s": sources / wall,
             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-            "success_rate": ok / max(1, sources),
+            "success_rate": ok / max(1, sources), "statuses": statuses,
             "p50_ms_by_size": {k: float(np.percentile(v, 50)) for k, v in sorted(per_size.items())}}
 
 
@@ -785,7 +795,8 @@ def serving_sample(ovl, ctx, n_requests, mem_budget=200 << 30, max_slots=8):
                 "sample": "%d requests of the 2000-request stream (Poisson, mean gap %g s)"
                           % (n_requests, cfg["mean_interarrival_s"]), "mem_budget_bytes": mem_budget,
                 "max_slots": max_slots, "k_max_by_tol": {"%g" % k: v for k, v in cfg["k_max_by_tol"].items()},
-                "k_max_cap": {"%d^4" % k: v for k, v in cfg["k_max_cap"].items()}})
+                "k_max_cap": {"%d^4" % k: v for k, v in cfg["k_max_cap"].items()},
+                "two_pass_when_basis_over_bytes": cfg["two_pass_over_bytes"]})
     return res
 
 

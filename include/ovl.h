@@ -204,12 +204,14 @@ ovl_status ovl_apply_sign(ovl_lattice* lat, const ovl_sign_params* p, int32_t nr
  * 32 sites per block; 2 / 3 as 0 with 48 / 32 sites per block; 4 as 1 held to two blocks per SM;
  * 5 eight threads per site, 16 sites per block, three blocks per SM; 6 one thread per site, 32
  * sites per one-warp block computing one of the two stencils; 7 one thread per site, the warps of
- * a grid that fills the GPU claiming 32-site tasks (one of the two stencils each) from a counter. The multishift method runs 1, 4, 5 as its eight-thread stencil and the others as its
+ * a grid that fills the GPU claiming 32-site tasks (one of the two stencils each) from a counter;
+ * 8 (FP32 batches) one thread per site and stencil for a group of four right-hand sides, each
+ * site's links loaded once per group (otherwise as 3). The multishift method runs 1, 4, 5 as its eight-thread stencil and the others as its
  * one-thread stencil. variant = -1
  * clears the entry: the next direct solve for that key times every shape on its own vectors and
  * keeps the fastest. Process-wide. All shapes compute the same step; results differ in the
  * rounding of the partial sums of alpha_j only.
- * Errors: EINVAL (variant outside -1..7, volume < 1, unknown precision). */
+ * Errors: EINVAL (variant outside -1..8, volume < 1, unknown precision). */
 ovl_status ovl_set_pair_variant(int64_t volume, int32_t precision, int32_t variant);
 
 /* The shape in use for (volume, precision); -1 if no solve has tuned it yet. */
@@ -283,6 +285,8 @@ typedef struct {
   int32_t rational_kind;    /* multishift: OVL_RAT_NEUBERGER | OVL_RAT_ZOLOTAREV */
   int32_t s;                /* multishift: poles (0: Eq. no_of_poles from the bounds, Neuberger) */
   double spec_lo, spec_hi;  /* multishift: bounds of |lambda| of the (deflated) spectrum */
+  int32_t two_pass;         /* direct: 1 = two-pass strategy (Section 2.3): device memory O(n) per
+                               source instead of the k_max + 1 basis columns, twice the stencils */
 } ovl_request;
 
 /* A request loop on worker threads: requests are admitted when their device footprint fits

@@ -72,7 +72,7 @@ class ovl_request(ctypes.Structure):
         ("tol", ctypes.c_double), ("k_max", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("b", ctypes.c_void_p), ("method", ctypes.c_int32), ("use_deflation", ctypes.c_int32),
         ("rational_kind", ctypes.c_int32), ("s", ctypes.c_int32), ("spec_lo", ctypes.c_double),
-        ("spec_hi", ctypes.c_double),
+        ("spec_hi", ctypes.c_double), ("two_pass", ctypes.c_int32),
     ]
 
 
@@ -393,7 +393,7 @@ def _nrhs_of(b: np.ndarray, nrhs):
 
 def ovl_submit(srv, field_id, b: np.ndarray, mu, tol, m_W=-2.0, k_max=600, precision=OVL_PREC_F64, nrhs=None,
                method=OVL_DIRECT_2SL, use_deflation=0, rational_kind=OVL_RAT_NEUBERGER, s=0, spec_lo=0.0,
-               spec_hi=0.0):
+               spec_hi=0.0, two_pass=0):
     """Queue x = sign(H_W(mu)) b on a registered field; b is copied before the call returns.
     method OVL_MULTISHIFT_BICG needs spec_lo < spec_hi (and s > 0 for Zolotarev)."""
     b = np.ascontiguousarray(b, dtype=np.complex128)
@@ -401,7 +401,7 @@ def ovl_submit(srv, field_id, b: np.ndarray, mu, tol, m_W=-2.0, k_max=600, preci
     if b.size % (12 * nr) != 0:
         raise ValueError("b does not hold nrhs whole spinors")
     req = ovl_request(field_id, nr, mu, m_W, tol, k_max, precision, b.ctypes.data, method, use_deflation,
-                      rational_kind, s, spec_lo, spec_hi)
+                      rational_kind, s, spec_lo, spec_hi, two_pass)
     t = ctypes.c_uint64()
     _check(lib.ovl_submit(srv, ctypes.byref(req), ctypes.byref(t)))
     return t.value

@@ -810,12 +810,123 @@ __global__ void __launch_bounds__(32 * kDynMaxWarps, 1) k_lz_pair_dyn(Geom g, Li
       }
     }
   }
+  // a warp that found no task has not waited yet: the kernel must not complete before the settle
+  // kernel it was launched behind (later kernels rely on stream order)
+  if (!waited) asm volatile("griddepcontrol.wait;" ::: "memory");
   // the last block to finish resets the task counter (every block has stopped claiming by then);
   // the chunk partials are summed by k_lz_alpha_finish or by the FP64 update's blocks
   __syncthreads();
   if (lin_tid() == 0 && atomicAdd(lz.count + rhs, 1u) == gridDim.x - 1) {
     lz.count[rhs] = 0u;
     lz.claim[rhs] = 0u;
+  }
+}
+
+// FP32 pair stencil for a batch with each site's links loaded once per group of G right-hand
+// sides (dslash_site_g): block (kGroupSites, 2), threadIdx.y = 0 applies H(mu) to the group's vhat_j,
+// = 1 applies H(-mu) to its what_j; the grid runs group-fastest (block b: site tile b / ngroups,
+// group b % ngroups) so that the groups of a tile share its link lines in L2. Each rhs of the group
+// gets its own alpha partials (one slot per tile) and the last tile block of the group finishes
+// alpha for each. Right-hand sides that have stopped (status != 0) are computed with the others
+// and not stored.
+constexpr int kGroupSites = 32;
+
+template <int LF, int G>
+__global__ void __launch_bounds__(2 * kGroupSites) k_lz_pair_group(Geom g, Links U, HopCoef<float> cp,
+                                                                  HopCoef<float> cm, LzDev lz, const float2* vh,
+                                                                  const float2* wh, float2* av, float2* aw) {
+  const int ngroups = (lz.nrhs + G - 1) / G;
+  const int tile = blockIdx.x / ngroups, grp = blockIdx.x % ngroups, ntiles = gridDim.x / ngroups;
+  const int r0 = grp * G, nact = min(G, lz.nrhs - r0);
+  const int s = tile * kGroupSites + threadIdx.x;
+  const bool is_w = threadIdx.y == 1;
+  const size_t n = (size_t)12 * g.vol;
+  // per-rhs state, staged once per block (FP64 -> FP32 conversions run on the FP64 pipe)
+  __shared__ int st[G], js[G];
+  __shared__ float scl[G][3];
+  if (lin_tid() < nact) {
+    const int r = r0 + lin_tid();
+    const int jr = lz.j[r];
+    const size_t o = (size_t)r * (lz.kmax + 2);
+    st[lin_tid()] = lz.status[r];
+    js[lin_tid()] = jr;
+    const double2 swd = lz.sw[o + jr];
+    scl[lin_tid()][0] = (float)lz.sv[o + jr];
+    scl[lin_tid()][1] = (float)swd.x;
+    scl[lin_tid()][2] = (float)swd.y;
+  }
+  __syncthreads();
+  bool any = false;
+  for (int r = 0; r < nact; ++r) any |= st[r] == 0;
+  if (!any) return;
+  Loader<float, true> ld[G];
+#pragma unroll
+  for (int r = 0; r < G; ++r) {
+    // a stopped rhs may hold j = 0 (breakdown at the start): any valid column does for its loads
+    const int rr = r0 + (r < nact ? r : 0), jr = max(js[r < nact ? r : 0], 1);
+    const float2* base = is_w ? wh + ((size_t)(jr & 1) * lz.nrhs + rr) * n : vh + vcol(lz, rr, jr, n);
+    ld[r] = Loader<float, true>{base, g.vol, false};
+  }
+  Red<float> acc[2 * G];
+  if (s < g.vol) {
+    Spin<float> o[G];
+    dslash_site_g<LF, G>(g, U, s, is_w ? cm : cp, ld, nact, o);
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+      if (r >= nact || st[r] != 0) continue;
+      const int rr = r0 + r;
+      if (!is_w) {
+        const float2* wj = wh + ((size_t)(js[r] & 1) * lz.nrhs + rr) * n;
+        cplx<float> wv[12];  // loads before the stores (see k_lz_pair)
+#pragma unroll
+        for (int q = 0; q < 12; ++q) wv[q] = ldc<float>(wj, (size_t)q * g.vol + s);
+        cplx<float> a = mk<float>(0, 0);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          cplx<float> x = scl[r][0] * o[r].c[q / 3][q % 3];
+          if (q >= 6) x = -x;  // gamma5
+          stc<float>(av + (size_t)rr * n, (size_t)q * g.vol + s, x);
+          a = a + cdot(wv[q], x);
+        }
+        acc[2 * r].add(a.re);
+        acc[2 * r + 1].add(a.im);
+      } else {
+        const cplx<float> sw = mk<float>(scl[r][1], scl[r][2]);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          cplx<float> y = sw * o[r].c[q / 3][q % 3];
+          if (q >= 6) y = -y;  // gamma5
+          stc<float>(aw + (size_t)rr * n, (size_t)q * g.vol + s, y);
+        }
+      }
+    }
+  }
+  double tot[2 * G];
+  block_reduce<float, 2 * G>(acc, tot);
+  __shared__ bool last;
+  if (lin_tid() == 0) {
+    for (int r = 0; r < nact; ++r) {
+      double* pr = lz.part + ((size_t)(r0 + r) * lz.nblk + tile) * 4;
+      pr[0] = tot[2 * r];
+      pr[1] = tot[2 * r + 1];
+      pr[2] = 0.0;
+      pr[3] = 0.0;
+    }
+    __threadfence();
+    last = atomicAdd(lz.count + r0, 1u) == (unsigned)ntiles - 1;
+    if (last) lz.count[r0] = 0u;
+  }
+  __syncthreads();
+  if (!last) return;
+  for (int r = 0; r < nact; ++r) {  // block-uniform loop: reduce_partials synchronises the block
+    if (st[r] != 0) continue;
+    const int rr = r0 + r;
+    double pv[4];
+    reduce_partials<4>(lz.part + (size_t)rr * lz.nblk * 4, ntiles, pv);
+    if (lin_tid() == 0) {
+      const size_t o = (size_t)rr * (lz.kmax + 2);
+      lz_alpha_finish(lz, rr, o, js[r], lz.sw[o + js[r]], pv);
+    }
   }
 }
 
@@ -1113,6 +1224,16 @@ cudaError_t launch_lanczos_pair(const Geom& g, const Links& U, int lf, bool f64,
     e = pair_unsplit<32>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
   } else if (variant == 6) {
     e = pair_unsplit<32, true>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
+  } else if (variant == 8 && !f64 && lz.nrhs > 1) {  // FP32 batches: links once per group of 4 sources
+    const unsigned ntile = (unsigned)((g.vol + kGroupSites - 1) / kGroupSites), ngroups = (unsigned)((lz.nrhs + 3) / 4);
+    const dim3 grid(ntile * ngroups), block(kGroupSites, 2);
+    e = lf == LINK_F16R12
+            ? launch_plain(k_lz_pair_group<LINK_F16R12, 4>, grid, block, st, g, U, fp, fm, lz,
+                           (const float2*)vec.vh, (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw)
+            : launch_plain(k_lz_pair_group<LINK_F32, 4>, grid, block, st, g, U, fp, fm, lz,
+                           (const float2*)vec.vh, (const float2*)vec.wh, (float2*)vec.av, (float2*)vec.aw);
+  } else if (variant == 8) {  // other cases: the 32-site one-thread-per-site shape
+    e = pair_unsplit<32>(g, U, lf, f64, dp, dm, fp, fm, lz, vec, st);
   } else if (variant == 7) {
     e = f64 ? pair_dyn_launch<double, LINK_F64>(g, U, dp, dm, lz, vec, st, first, mid)
             : lf == LINK_F16R12 ? pair_dyn_launch<float, LINK_F16R12>(g, U, fp, fm, lz, vec, st, first, mid)

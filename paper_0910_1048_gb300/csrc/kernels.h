@@ -44,12 +44,14 @@ inline cudaError_t record_timing(cudaEvent_t ev, cudaStream_t st) {
 // with 48 / 32 sites per block, 4 split held to 128 registers (two blocks per SM), 5 split with
 // 16 sites per block held to 168 registers (three blocks per SM), 6 one thread per site, 32 sites,
 // one stencil (H(mu) or H(-mu)) per one-warp block, 7 dynamically scheduled (warps of a resident
-// grid claim 32-site tasks from a counter). The FP64 stencil is bound by the FP64 pipe, so its time
-// follows the most loaded SM: at 12^4 ncu counted SM active cycles of max 206K against a mean of
-// 156K for variant 3 and 214K against 164K for variant 6. The multishift kernels run variants 0,
-// 2, 3, 6, 7 as 0 and 4, 5 as 1. Thread-safe, process-wide. (A 16-thread split, one hop per thread, measured
-// 54 us against 32 us for FP64 at 8^4: more index and reduction work than the extra warps hide.)
-constexpr int kPairVariants = 8;
+// grid claim 32-site tasks from a counter), 8 FP32 batches: each site's links loaded once for a
+// group of 4 sources (one thread per site and stencil, 32 sites per block; as 3 otherwise). The
+// FP64 stencil is bound by the FP64 pipe, so its time follows the most loaded SM: at 12^4 ncu
+// counted SM active cycles of max 206K against a mean of 156K for variant 3 and 214K against 164K
+// for variant 6. The multishift kernels run variants 0, 2, 3, 6, 7, 8 as 0 and 4, 5 as 1.
+// Thread-safe, process-wide. (A 16-thread split, one hop per thread, measured 54 us against 32 us
+// for FP64 at 8^4: more index and reduction work than the extra warps hide.)
+constexpr int kPairVariants = 9;
 int tuned_pair_variant(int vol, int prec);
 // Returns the variant for the key, running `measure` (which returns 0 or 1) under the table's
 // lock the first time, so that every solve in the process uses one decision per key.

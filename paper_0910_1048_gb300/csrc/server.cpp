@@ -25,7 +25,7 @@
 
 namespace ovl {
 ovl_lattice* lattice_view(ovl_lattice* parent);
-size_t direct_footprint(int vol, int nrhs, int kmax, bool f64);
+size_t direct_footprint(int vol, int nrhs, int kmax, bool f64, bool two_pass);
 size_t multishift_footprint(int vol, int nrhs, int s, bool f64, bool refine);
 void neuberger_for_spectrum(double lo, double hi, double eps, int* s_out, double* c_out, double* d_out);
 constexpr double kFp32FloorHost = 2e-6;  // below it the reduced-precision multishift refines (FP64)
@@ -77,7 +77,7 @@ size_t footprint(const ovl_server* s, const ovl_request& r) {
   if (r.method == OVL_MULTISHIFT_BICG)
     return ovl::multishift_footprint(lat->g.vol, r.nrhs, request_poles(r), f64,
                                      !f64 && r.tol < ovl::kFp32FloorHost);
-  return ovl::direct_footprint(lat->g.vol, r.nrhs, r.k_max, f64);
+  return ovl::direct_footprint(lat->g.vol, r.nrhs, r.k_max, f64, r.two_pass != 0);
 }
 
 constexpr double kMaxWait = 2.0;  // seconds after which the oldest request goes first
@@ -129,6 +129,7 @@ void worker(ovl_server* s, int slot) {
     p.s = r.s;
     p.spec_lo = r.spec_lo;
     p.spec_hi = r.spec_hi;
+    p.two_pass = r.two_pass;
     p.host_io = 1;
     std::vector<ovl_sign_info> info(r.nrhs);
     std::vector<double> x(job->b.size());
@@ -182,6 +183,8 @@ ovl_status ovl_submit(ovl_server* s, const ovl_request* r, uint64_t* ticket) {
   OVL_REQUIRE(r->nrhs >= 1 && r->nrhs <= 64 && r->k_max >= 1 && r->tol >= 0, "ovl_submit: invalid request");
   OVL_REQUIRE(r->precision >= OVL_PREC_F64 && r->precision <= OVL_PREC_F32_F16LINKS, "ovl_submit: precision");
   OVL_REQUIRE(r->method == OVL_DIRECT_2SL || r->method == OVL_MULTISHIFT_BICG, "ovl_submit: method");
+  OVL_REQUIRE(r->two_pass == 0 || (r->two_pass == 1 && r->method == OVL_DIRECT_2SL),
+              "ovl_submit: two_pass is 0, or 1 with the direct method");
   OVL_REQUIRE(r->method == OVL_DIRECT_2SL ||
                   (r->spec_lo > 0 && r->spec_hi > r->spec_lo &&
                    (r->rational_kind == OVL_RAT_NEUBERGER || r->rational_kind == OVL_RAT_ZOLOTAREV) &&
@@ -208,7 +211,8 @@ ovl_status ovl_submit(ovl_server* s, const ovl_request* r, uint64_t* ticket) {
   const size_t nd = (size_t)2 * 12 * lat->g.vol * r->nrhs;
   job->b.assign((const double*)r->b, (const double*)r->b + nd);
   job->req.b = nullptr;
-  job->work = (double)lat->g.vol * r->nrhs * r->k_max * (r->precision == OVL_PREC_F64 ? 1.0 : 0.5);
+  job->work = (double)lat->g.vol * r->nrhs * r->k_max * (r->precision == OVL_PREC_F64 ? 1.0 : 0.5) *
+              (r->two_pass ? 2.0 : 1.0);
   job->arrived = std::chrono::steady_clock::now();
   job->ticket = s->next_ticket++;
   *ticket = job->ticket;

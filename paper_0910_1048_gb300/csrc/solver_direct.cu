@@ -782,10 +782,12 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   return result;
 }
 
-size_t direct_footprint(int vol, int nrhs, int kmax, bool f64) {
+size_t direct_footprint(int vol, int nrhs, int kmax, bool f64, bool two_pass) {
   const size_t n = (size_t)12 * vol, elt = f64 ? 16 : 8;
+  if (two_pass) kmax = 2;  // three basis columns in a rotating window, plus the FP64 accumulator of x
+  const size_t xacc = two_pass ? n * 16 : 0;
   const size_t slots = (n + kVecBlock - 1) / kVecBlock + kMaxFillSMs;  // partial_slots
-  return (size_t)nrhs * ((size_t)(kmax + 1) * n * elt + 4 * n * elt + 3 * n * 16 + 16 * slots * 32) +
+  return (size_t)nrhs * ((size_t)(kmax + 1) * n * elt + 4 * n * elt + 3 * n * 16 + xacc + 16 * slots * 32) +
          ((size_t)1 << 20);
 }
 

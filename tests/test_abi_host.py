@@ -150,7 +150,7 @@ def test_pair_variant_table(ovl):
     assert ovl.ovl_get_pair_variant(vol, ovl.OVL_PREC_F64) == -1
     ovl.ovl_set_pair_variant(vol, ovl.OVL_PREC_F32, -1)
     assert ovl.ovl_get_pair_variant(vol, ovl.OVL_PREC_F32) == -1
-    for args in [(vol, ovl.OVL_PREC_F64, 8), (vol, ovl.OVL_PREC_F64, -2), (0, ovl.OVL_PREC_F64, 1),
+    for args in [(vol, ovl.OVL_PREC_F64, 9), (vol, ovl.OVL_PREC_F64, -2), (0, ovl.OVL_PREC_F64, 1),
                  (vol, 3, 1), (1 << 27, ovl.OVL_PREC_F64, 0)]:
         with pytest.raises(ovl.OvlError) as e:
             ovl.ovl_set_pair_variant(*args)

@@ -10,7 +10,8 @@ sizes where they run, and of the solver's edge cases.
 - 16^4 FP32 direct with 16 right-hand sides in one batch, equal k, each against the oracle's
   Algorithm 4 (the C FP64 two-sided Lanczos), 1e-4 (the bound of the 4^4 FP32 equal-k test).
 - every pair-stencil shape the autotuner may pick (pinned through ovl_set_pair_variant) at 12^4,
-  the headline size, FP64 and FP32, equal k against the oracle's Algorithm 4: 1e-10 / 1e-4.
+  the headline size, FP64 and FP32, equal k against the oracle's Algorithm 4: 1e-10 / 1e-4; the
+  grouped FP32 shape (links once per four sources) on batches of 6 at 8^4 and 16 at 16^4.
 - FP64 reliable updates with more than 64 correction systems in one batch (4 sources x s poles).
 - the spectral set-up (ARPACK through the library) against the oracle's critical eigenpairs.
 - breakdown at the start (shadow residual orthogonal to the residual), the ill-posed free field
@@ -129,7 +130,7 @@ def test_every_pair_shape_equal_k_1212(ovl, lat12, prec):
     bound = 1e-10 if prec == "f64" else 1e-4
     xs = []
     try:
-        for var in range(8):
+        for var in range(9):
             ovl.ovl_set_pair_variant(vol, pr, var)
             assert ovl.ovl_get_pair_variant(vol, pr) == var
             st, info, x = _solve(ovl, lat, b, mu=0.3, fixed_k=k, precision=pr, check_every=8)
@@ -142,6 +143,30 @@ def test_every_pair_shape_equal_k_1212(ovl, lat12, prec):
     # the shapes differ only in the order of alpha's partial sums
     for x in xs[1:]:
         assert _rel(x, xs[0]) < (1e-12 if prec == "f64" else 1e-5)
+
+
+@pytest.mark.parametrize("dims,nrhs", [((8, 8, 8, 8), 6), ((16, 16, 16, 16), 16)])
+def test_grouped_pair_batch_f32_equal_k(ovl, ctx, dims, nrhs):
+    """Pair shape 8 (links loaded once per group of four sources; 6 = one full group and one of
+    two) against the oracle's Algorithm 4 per rhs at equal k, FP32: 1e-4, and against shape 3."""
+    u = synth.gauge_links(dims, 0)
+    b = synth.gaussian_source(dims, 1000, nrhs=nrhs)
+    lat = ovl.ovl_create_lattice(ctx, dims, -1)
+    ovl.ovl_set_links(lat, u, ovl.OVL_F64 | ovl.OVL_F32)
+    vol, k = int(np.prod(dims)), 6
+    xs = {}
+    try:
+        for var in (8, 3):
+            ovl.ovl_set_pair_variant(vol, ovl.OVL_PREC_F32, var)
+            st, info, xs[var] = _solve(ovl, lat, b, mu=0.2, fixed_k=k, precision=ovl.OVL_PREC_F32, check_every=3)
+            assert st == ovl.OVL_OK and all(i["iterations"] == k for i in info)
+    finally:
+        ovl.ovl_set_pair_variant(vol, ovl.OVL_PREC_F32, -1)
+        ovl.ovl_destroy_lattice(lat)
+    for r in (0, nrhs - 1) if nrhs > 6 else range(nrhs):
+        xo, _, _ = krylov.direct_lanczos(u, dims, -2.0, 0.2, b[r], k)
+        assert _rel(xs[8][r], xo) < 1e-4, r
+    assert _rel(xs[8], xs[3]) < 1e-5
 
 
 def test_reliable_update_batch_over_64_systems(ovl, ctx, problem_4444):

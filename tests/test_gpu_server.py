@@ -107,6 +107,32 @@ def test_server_result_matches_oracle(ovl, env):
     ovl.ovl_server_destroy(srv)
 
 
+def test_two_pass_request(ovl, env):
+    """A direct request with two_pass = 1: admitted under a budget too small for its one-pass basis,
+    and its result bitwise the same as the two-pass solve alone; a two-pass multishift is refused."""
+    ctx, fields = env
+    dims, u, lat = fields[2]  # 6^4
+    b = synth.gaussian_source(dims, 41, nrhs=2)
+    p = ovl.ovl_sign_params_default(mu=0.4, tol=1e-9, k_max=3000, two_pass=1)
+    xa = np.zeros_like(b)
+    st_a, _ = ovl.ovl_apply_sign(lat, p, np.ascontiguousarray(b), xa)
+    # one-pass basis: 2 x 3001 x 12 x 1296 x 16 B = 1.9 GB; the budget admits only the two-pass state
+    srv = ovl.ovl_server_create(ctx, 256 << 20, max_slots=2)
+    fid = ovl.ovl_server_add_field(srv, lat)
+    with pytest.raises(ovl.OvlError):
+        ovl.ovl_submit(srv, fid, b, 0.4, 1e-9, k_max=3000)
+    t = ovl.ovl_submit(srv, fid, b, 0.4, 1e-9, k_max=3000, two_pass=1)
+    res = _drain(ovl, srv, [dict(t=t, b=b, nrhs=2)])
+    st, x, info = res[t]
+    assert st == st_a == ovl.OVL_OK, info
+    assert np.array_equal(x, xa)
+    with pytest.raises(ovl.OvlError) as e:
+        ovl.ovl_submit(srv, fid, b, 0.4, 1e-9, method=ovl.OVL_MULTISHIFT_BICG, spec_lo=0.05, spec_hi=2.7,
+                       two_pass=1)
+    assert e.value.status == ovl.OVL_EINVAL
+    ovl.ovl_server_destroy(srv)
+
+
 def test_admission_rejects_oversized(ovl, env):
     ctx, fields = env
     srv = ovl.ovl_server_create(ctx, 1 << 20, max_slots=1)  # 1 MiB: nothing fits
