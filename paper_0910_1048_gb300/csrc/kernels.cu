@@ -489,21 +489,41 @@ cudaError_t launch_lanczos_start(const Geom& g, bool f64, const LzDev& lz, const
 //   vhat_{j+1} = A v_j - (sv_j alpha_j) vhat_j - (sv_{j-1} beta_{j-1}) vhat_{j-1},
 //   what_{j+1} = A^H w_j - (sw_j conj(alpha_j)) what_j - (delta_{j-1} sw_{j-1}) what_{j-1}.
 // alpha_j = conj(sw_j) (sum of the partials), and the update coefficients in LzDev::ucoef order.
+// The scalars of earlier steps that alpha_j's coefficients need (loaded ahead of the sum).
+struct AlphaIn {
+  zd sw;   // sw_j
+  double sv;  // sv_j
+  zd a2, b2;  // sv_{j-1} beta_{j-1}, delta_{j-1} sw_{j-1} (0 at j = 1)
+};
+
+__device__ __forceinline__ AlphaIn lz_alpha_inputs(const LzDev& lz, size_t o, int j) {
+  AlphaIn in;
+  const double2 swd = lz.sw[o + j];
+  in.sw = mk(swd.x, swd.y);
+  in.sv = lz.sv[o + j];
+  in.a2 = in.b2 = mk(0.0, 0.0);
+  if (j > 1) {
+    in.a2 = lz.sv[o + j - 1] * ldc<double>(lz.beta, o + j - 1);
+    in.b2 = lz.delta[o + j - 1] * ldc<double>(lz.sw, o + j - 1);
+  }
+  return in;
+}
+
+__device__ __forceinline__ zd lz_alpha_coeffs(const AlphaIn& in, const double (&pv)[4], double2 (&c)[4]) {
+  const zd alpha = conj(in.sw) * mk(pv[0], pv[1]);
+  const zd a1 = in.sv * alpha, b1 = in.sw * conj(alpha);
+  c[0] = make_double2(a1.re, a1.im);
+  c[1] = make_double2(in.a2.re, in.a2.im);
+  c[2] = make_double2(b1.re, b1.im);
+  c[3] = make_double2(in.b2.re, in.b2.im);
+  return alpha;
+}
+
 __device__ __forceinline__ zd lz_alpha_coeffs(const LzDev& lz, size_t o, int j, double2 swd, const double (&pv)[4],
                                               double2 (&c)[4]) {
-  const zd sw = mk(swd.x, swd.y);
-  const zd alpha = conj(sw) * mk(pv[0], pv[1]);
-  const zd a1 = lz.sv[o + j] * alpha, b1 = sw * conj(alpha);
-  zd a2 = mk(0.0, 0.0), b2 = mk(0.0, 0.0);
-  if (j > 1) {
-    a2 = lz.sv[o + j - 1] * ldc<double>(lz.beta, o + j - 1);
-    b2 = lz.delta[o + j - 1] * ldc<double>(lz.sw, o + j - 1);
-  }
-  c[0] = make_double2(a1.re, a1.im);
-  c[1] = make_double2(a2.re, a2.im);
-  c[2] = make_double2(b1.re, b1.im);
-  c[3] = make_double2(b2.re, b2.im);
-  return alpha;
+  AlphaIn in = lz_alpha_inputs(lz, o, j);
+  in.sw = mk(swd.x, swd.y);
+  return lz_alpha_coeffs(in, pv, c);
 }
 
 __device__ __forceinline__ void lz_alpha_store(const LzDev& lz, int rhs, size_t o, int j, zd alpha,
@@ -982,12 +1002,15 @@ __global__ void __launch_bounds__(BAL ? kBalBlock : kVecBlock) k_lz_update(Geom 
   R u[8];  // the four complex coefficients of LzDev::ucoef
   if (BAL && nchunk > 0) {
     __shared__ double uc[8];
+    // the earlier steps' scalars are requested before the sum (their latency overlaps it)
+    AlphaIn ain{};
+    if (threadIdx.x == 0) ain = lz_alpha_inputs(lz, o, j);
     double pv[2];
     sum_partials_by_warp<2, kBalBlock / 64>(lz.part + (size_t)rhs * lz.nblk * 4, nchunk, 4, pv);
     if (threadIdx.x == 0) {
       const double p4[4] = {pv[0], pv[1], 0.0, 0.0};
       double2 c[4];
-      const zd alpha = lz_alpha_coeffs(lz, o, j, lz.sw[o + j], p4, c);
+      const zd alpha = lz_alpha_coeffs(ain, p4, c);
       for (int i = 0; i < 4; ++i) {
         uc[2 * i] = c[i].x;
         uc[2 * i + 1] = c[i].y;

@@ -53,8 +53,8 @@ inline cudaError_t record_timing(cudaEvent_t ev, cudaStream_t st) {
 // for FP64 at 8^4: more index and reduction work than the extra warps hide.)
 constexpr int kPairVariants = 9;
 int tuned_pair_variant(int vol, int prec);
-// Returns the variant for the key, running `measure` (which returns 0 or 1) under the table's
-// lock the first time, so that every solve in the process uses one decision per key.
+// Returns the variant for the key, running `measure` (which returns the fastest variant, or -1)
+// under the table's lock the first time, so that every solve in the process uses one decision per key.
 int tune_pair_variant(int vol, int prec, int (*measure)(void*), void* arg);
 // Sets the entry (variant >= 0) or removes it (-1).
 void set_pair_variant(int vol, int prec, int variant);

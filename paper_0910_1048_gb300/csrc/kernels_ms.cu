@@ -90,41 +90,77 @@ __global__ void __launch_bounds__(kBlock) k_ms_start(Geom g, MsDev ms, MsVecs v,
   }
 }
 
+// Every FP64 instruction is slow on GB300's narrow FP64 pipe, so the last blocks' recurrences keep
+// their dependent chains short (one division per shift, comparisons on squares). Blocks have at
+// least as many threads as shifts (s <= 127), so thread t holds shift t.
+struct MsAlphaIn {
+  zd rho, akm, bkm;  // rho_k, alpha_{k-1}, beta_{k-1}
+  int act;           // shift t: 0 retired, 1 live, 2 last direction update done
+  zd zm, z0;         // zeta^t_{k-1}, zeta^t_k
+  double dsig;       // sigma_t - sigma_1
+};
+
+__device__ __forceinline__ MsAlphaIn ms_alpha_inputs(const MsDev& ms, int rhs) {
+  MsAlphaIn in{};
+  const double2* sd = ms.seed + (size_t)rhs * 8;
+  const int t = lin_tid();
+  in.rho = ldc<double>(sd, 0);
+  in.akm = ldc<double>(sd, 2);
+  in.bkm = ldc<double>(sd, 3);
+  if (t < ms.s) {
+    const size_t si = (size_t)rhs * ms.s + t;
+    in.act = ms.active[si];
+    const double2* z = ms.zeta + si * 3;
+    in.zm = ldc<double>(z, 0);
+    in.z0 = ldc<double>(z, 1);
+    in.dsig = ms.dsig[t];
+  }
+  return in;
+}
+
 // last block of pair2: alpha_k, then zeta^i_{k+1} and alpha^i_k of the live shifts
-__device__ __forceinline__ void ms_alpha_and_shifts(MsDev& ms, int rhs, const double (&pv)[4]) {
+__device__ __forceinline__ void ms_alpha_and_shifts(MsDev& ms, int rhs, const double (&pv)[4], const MsAlphaIn& in) {
   __shared__ zd alpha_sh;
   __shared__ int bad;
   const int t = lin_tid();
   double2* sd = ms.seed + (size_t)rhs * 8;
   if (t == 0) {
     zd den = mk(pv[0], pv[1]);
-    zd rho = ldc<double>(sd, 0);
     double dd = norm2(den);
     bad = !(dd > 0.0) || !(dd < 1e300);
-    zd alpha = bad ? mk(0.0, 0.0) : (1.0 / dd) * (rho * conj(den));
+    zd alpha = bad ? mk(0.0, 0.0) : (1.0 / dd) * (in.rho * conj(den));
     alpha_sh = alpha;
     if (bad) ms.status[rhs] = 1;
     sd[1] = make_double2(alpha.re, alpha.im);
   }
   __syncthreads();
   if (bad) return;
-  const zd ak = alpha_sh, akm = ldc<double>(sd, 2), bkm = ldc<double>(sd, 3);
+  const zd ak = alpha_sh, akm = in.akm, bkm = in.bkm;
   for (int i = t; i < ms.s; i += lin_nthreads()) {
     const size_t si = (size_t)rhs * ms.s + i;
-    int act = ms.active[si];
+    double2* z = ms.zeta + si * 3;
+    const bool mine = i == t;
+    int act = mine ? in.act : ms.active[si];
     if (act == 2) ms.active[si] = act = 0;
     if (!act) continue;
-    double2* z = ms.zeta + si * 3;
-    zd zm = ldc<double>(z, 0), z0 = ldc<double>(z, 1);
-    zd d1 = mk(1.0 - ak.re * ms.dsig[i], -ak.im * ms.dsig[i]);
+    const zd zm = mine ? in.zm : ldc<double>(z, 0), z0 = mine ? in.z0 : ldc<double>(z, 1);
+    const double ds = mine ? in.dsig : ms.dsig[i];
+    zd d1 = mk(1.0 - ak.re * ds, -ak.im * ds);
     zd den = akm * zm * d1 + ak * bkm * (zm - z0);
     zd num = z0 * zm * akm;
-    double dn = norm2(den);
-    zd zp = dn > 0 ? (1.0 / dn) * (num * conj(den)) : mk(0.0, 0.0);
+    const double dn = norm2(den), z0n = norm2(z0);
+    const zd nc = num * conj(den);
+    zd zp = mk(0.0, 0.0), ai = mk(0.0, 0.0);
+    const double prod = dn * z0n;
+    if (prod > 1e-300 && prod < 1e300) {  // zeta^i_{k+1} = num / den, alpha^i_k = alpha_k zeta^i_{k+1} / zeta^i_k
+      const double inv = 1.0 / prod;
+      zp = (z0n * inv) * nc;
+      ai = ak * (inv * (nc * conj(z0)));
+    } else {  // the same with one division each (a product outside the safe range)
+      if (dn > 0) zp = (1.0 / dn) * nc;
+      if (z0n > 0) ai = ak * ((1.0 / z0n) * (zp * conj(z0)));
+    }
     z[2] = make_double2(zp.re, zp.im);
-    double z0n = norm2(z0);
-    zd ratio = z0n > 0 ? (1.0 / z0n) * (zp * conj(z0)) : mk(0.0, 0.0);
-    zd ai = ak * ratio;
     ms.ash[si] = make_double2(ai.re, ai.im);
   }
 }
@@ -182,8 +218,10 @@ __global__ void __launch_bounds__(2 * kPairSites) k_ms_pair(Geom g, Links U, Hop
   double* part = ms.part + (size_t)rhs * ms.nblk * 4;
   double pv[4] = {tot[0], tot[1], 0, 0};
   if (publish_partials<4>(pv, part, ms.count + rhs)) {
+    // (the inputs are loaded after the sum here: held across it they cost the whole stencil
+    // kernel registers, 80 -> 106, and occupancy)
     reduce_partials<4>(part, gridDim.x, pv);
-    ms_alpha_and_shifts(ms, rhs, pv);
+    ms_alpha_and_shifts(ms, rhs, pv, ms_alpha_inputs(ms, rhs));
   }
 }
 
@@ -237,8 +275,10 @@ __global__ void __launch_bounds__(8 * kSplitSites) k_ms_pair_split(Geom g, Links
   double* part = ms.part + (size_t)rhs * ms.nblk * 4;
   double pv[4] = {tot[0], tot[1], 0, 0};
   if (publish_partials<4>(pv, part, ms.count + rhs)) {
+    // (the inputs are loaded after the sum here: held across it they cost the whole stencil
+    // kernel registers, 80 -> 106, and occupancy)
     reduce_partials<4>(part, gridDim.x, pv);
-    ms_alpha_and_shifts(ms, rhs, pv);
+    ms_alpha_and_shifts(ms, rhs, pv, ms_alpha_inputs(ms, rhs));
   }
 }
 
@@ -274,19 +314,30 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_update(Geom g, MsDev ms, MsVec
   double* part = ms.part + (size_t)rhs * ms.nblk * 4;
   double pv[4] = {acc[0], acc[1], acc[2], 0};
   if (publish_partials<4>(pv, part, ms.count + rhs)) {
-    reduce_partials<4>(part, gridDim.x, pv);
-    const double tl = ms.tolv ? ms.tolv[rhs] : ms.tol;
-    __shared__ zd beta_sh;
-    __shared__ double rn_sh;
-    __shared__ int live;
+    // this block's inputs first (their latency overlaps the sum): rho_k, |r_0|, shift t's state
     const int t = lin_tid();
+    const double tl = ms.tolv ? ms.tolv[rhs] : ms.tol;
+    const zd rho = ldc<double>(sd, 0);
+    const double r0 = sd[4].x;
+    int act0 = 0;
+    zd z1 = mk(0.0, 0.0), z2 = mk(0.0, 0.0);
+    if (t < ms.s) {
+      const size_t si = (size_t)rhs * ms.s + t;
+      act0 = ms.active[si];
+      z1 = ldc<double>(ms.zeta + si * 3, 1);
+      z2 = ldc<double>(ms.zeta + si * 3, 2);
+    }
+    reduce_partials<4>(part, gridDim.x, pv);
+    __shared__ zd beta_sh;
+    __shared__ double r2_sh;
+    __shared__ int live;
     if (t == 0) {
-      zd rho = ldc<double>(sd, 0), rhon = mk(pv[0], pv[1]);
+      zd rhon = mk(pv[0], pv[1]);
       double rr = norm2(rho);
       zd beta = rr > 0 ? (1.0 / rr) * (rhon * conj(rho)) : mk(0.0, 0.0);
       double rn = sqrt(pv[2]);
       beta_sh = beta;
-      rn_sh = rn;
+      r2_sh = pv[2];
       live = 0;
       sd[0] = make_double2(rhon.re, rhon.im);
       sd[2] = sd[1];  // alpha_{k-1} <- alpha_k
@@ -300,20 +351,21 @@ __global__ void __launch_bounds__(kVecBlock) k_ms_update(Geom g, MsDev ms, MsVec
     }
     __syncthreads();
     const zd beta = beta_sh;
-    const double rn = rn_sh, r0 = sd[4].x;
+    const double r2 = r2_sh, lim = (tl * r0) * (tl * r0);
     int mylive = 0;
     for (int i = t; i < ms.s; i += lin_nthreads()) {
       const size_t si = (size_t)rhs * ms.s + i;
-      if (!ms.active[si]) continue;
+      const bool mine = i == t;
+      if (!(mine ? act0 : ms.active[si])) continue;
       double2* z = ms.zeta + si * 3;
-      zd z0 = ldc<double>(z, 1), zp = ldc<double>(z, 2);
+      const zd z0 = mine ? z1 : ldc<double>(z, 1), zp = mine ? z2 : ldc<double>(z, 2);
       double z0n = norm2(z0);
       zd ratio = z0n > 0 ? (1.0 / z0n) * (zp * conj(z0)) : mk(0.0, 0.0);
       zd bi = beta * (ratio * ratio);
       ms.bsh[si] = make_double2(bi.re, bi.im);
-      z[0] = z[1];
-      z[1] = z[2];
-      if (sqrt(norm2(zp)) * rn <= tl * r0)
+      z[0] = make_double2(z0.re, z0.im);
+      z[1] = make_double2(zp.re, zp.im);
+      if (norm2(zp) * r2 <= lim)  // |zeta^i_{k+1}| |r_{k+1}| <= tol |r_0|, on squares
         ms.active[si] = 2;  // this step's direction update is its last
       else
         mylive = 1;
