@@ -145,6 +145,32 @@ def test_every_pair_shape_equal_k_1212(ovl, lat12, prec):
         assert _rel(x, xs[0]) < (1e-12 if prec == "f64" else 1e-5)
 
 
+@pytest.mark.parametrize("var", [7, 3])
+def test_graph_chunks_equal_direct_launches(ovl, ctx, var):
+    """The chunks of steps as CUDA graphs (the default) and as direct launches give the same solve,
+    bitwise, for the headline's shape (deferred step, early launch behind the settle kernel) and a
+    plain one; 8^4 FP64, a fixed 75 steps (chunks of 20: three graphs and a partial chunk)."""
+    dims = (8, 8, 8, 8)
+    vol = int(np.prod(dims))
+    u = synth.gauge_links(dims, 3)
+    b = synth.gaussian_source(dims, 4, nrhs=2)
+    lat = ovl.ovl_create_lattice(ctx, dims, -1)
+    ovl.ovl_set_links(lat, u, ovl.OVL_F64)
+    xs = []
+    try:
+        ovl.ovl_set_pair_variant(vol, ovl.OVL_PREC_F64, var)
+        for graphs in (1, 0):
+            st, info, x = _solve(ovl, lat, b, mu=0.3, fixed_k=75, check_every=20, use_graphs=graphs)
+            assert st == ovl.OVL_OK and all(i["iterations"] == 75 for i in info)
+            xs.append(x)
+    finally:
+        ovl.ovl_set_pair_variant(vol, ovl.OVL_PREC_F64, -1)
+        ovl.ovl_destroy_lattice(lat)
+    assert np.array_equal(xs[0], xs[1])
+    xo, _, _ = krylov.direct_lanczos(u, dims, -2.0, 0.3, b[0], 75)
+    assert _rel(xs[0][0], xo) < 1e-10
+
+
 @pytest.mark.parametrize("dims,nrhs", [((8, 8, 8, 8), 6), ((16, 16, 16, 16), 16)])
 def test_grouped_pair_batch_f32_equal_k(ovl, ctx, dims, nrhs):
     """Pair shape 8 (links loaded once per group of four sources; 6 = one full group and one of
