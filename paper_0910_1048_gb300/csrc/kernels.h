@@ -229,6 +229,9 @@ cudaError_t launch_ms_start(const Geom& g, bool f64, const MsDev& ms, const MsVe
                             const double2* R, const double2* L, const double* lam_sign, double2* dots, cudaStream_t st);
 // One iteration (four launches). With timing events (may be null): ev[0] before the first
 // pair stencil, ev[1] after it, ev[2] before the direction update, ev[3] after it.
+// Whether the multishift iteration uses the eight-threads-per-site stencils (from the pair shape of
+// (volume, key), key = link format, 0 for FP64); the solvers key their cached graphs on it.
+bool ms_pair_split(const Geom& g, int key);
 cudaError_t launch_ms_step(const Geom& g, const Links& U, int lf, bool f64, double m_w, double mu, const MsDev& ms,
                            const MsVecs& v, cudaStream_t st, cudaEvent_t* ev = nullptr);
 // Reliable-update helpers. Residuals of the systems j0 .. j0+gn-1 of the flattened (rhs, shift)

@@ -487,6 +487,11 @@ cudaError_t launch_ms_start(const Geom& g, bool f64, const MsDev& ms, const MsVe
   return cudaGetLastError();
 }
 
+bool ms_pair_split(const Geom& g, int key) {
+  const int tv = tuned_pair_variant(g.vol, key);
+  return tv < 0 ? use_split(g) : (tv == 1 || tv == 4 || tv == 5);  // 0, 2, 3, 6, 7, 8: one thread per site
+}
+
 template <class R, int LF>
 static cudaError_t ms_step_t(const Geom& g, const Links& U, double m_w, double mu, const MsDev& ms, const MsVecs& v,
                              cudaStream_t st, cudaEvent_t* ev) {
@@ -494,8 +499,7 @@ static cudaError_t ms_step_t(const Geom& g, const Links& U, double m_w, double m
   dim3 pgrid((g.vol + kPairSites - 1) / kPairSites, ms.nrhs), pblock(kPairSites, 2);
   HopCoef<R> cp = hop_coef<R>(m_w, mu), cm = hop_coef<R>(m_w, -mu);
   dim3 sgrid((g.vol + kSplitSites - 1) / kSplitSites, ms.nrhs), sblock(kSplitSites, 8);
-  const int tv = tuned_pair_variant(g.vol, sizeof(R) == 8 ? 0 : LF);
-  const bool split = tv < 0 ? use_split(g) : (tv == 1 || tv == 4 || tv == 5);  // 0, 2, 3, 6, 7, 8: one thread per site
+  const bool split = ms_pair_split(g, sizeof(R) == 8 ? 0 : LF);
   const int elt = vec_elts(g, ms.nrhs, sizeof(R) == 8);
   cudaError_t e;
   if (ev && (e = record_timing(ev[0], st))) return e;

@@ -62,6 +62,7 @@ struct DirectWS {
   int gchunk = 0;
   double g_mw = 0, g_mu = 0;
   int g_lf = -1;
+  int g_var = -1;  // the pair-stencil shape the graphs launch (a pinned shape may change between solves)
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   // stopping estimate ||V (y_j - y_j')|| / ||V y_j||, computed on a side stream with its own
@@ -481,7 +482,7 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
   // step instead.
   bool use_graph = p->use_graphs != 0 && chunk > 1;
   if (use_graph && !(w->graph[0] && w->graph[1] && w->gchunk == chunk && w->g_mw == p->m_W && w->g_mu == p->mu &&
-                     w->g_lf == lf)) {
+                     w->g_lf == lf && w->g_var == pvar)) {
     const int mid = std::max(1, chunk / 2);
     for (int q = 0; q < 2; ++q) {
       if (w->graph[q]) cudaGraphExecDestroy(w->graph[q]);
@@ -504,6 +505,7 @@ ovl_status solve_direct(ovl_lattice* lat, const ovl_sign_params* p, int nrhs, co
     w->g_mw = p->m_W;
     w->g_mu = p->mu;
     w->g_lf = lf;
+    w->g_var = pvar;
   }
   int launches = 1 + (m > 0 ? 1 : 0) + 1;  // start (+ deflation dots) and the combine
   // the chunk's steps, then the finish of a deferred last step (before the scalars are read)

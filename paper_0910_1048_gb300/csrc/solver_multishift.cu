@@ -50,6 +50,7 @@ struct MultiWS {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // alternating chunks, each with its events
   cudaEvent_t tev[2][4] = {};
   int gchunk = 0, g_lf = -1;
+  int g_var = -1, rg_var = -1;  // the pair-stencil shape the graphs were captured with
   double g_mw = 0, g_mu = 0, g_s1 = 0, g_tol = 0;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -340,8 +341,9 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
   const bool use_graph = p->use_graphs != 0 && chunk > 1;
   // the chunks alternate between two graphs; graph q records timing events (tev[q]) around its
   // middle iteration, so the sampled launches are steady-state ones inside a busy stream
+  const int gvar = ms_pair_split(g, f64 ? 0 : lf) ? 1 : 0;  // the stencil shape the graphs launch
   if (use_graph && !(w->graph[0] && w->graph[1] && w->gchunk == chunk && w->g_lf == lf && w->g_mw == p->m_W &&
-                     w->g_mu == p->mu && w->g_s1 == s1 && w->g_tol == ms.tol)) {
+                     w->g_mu == p->mu && w->g_s1 == s1 && w->g_tol == ms.tol && w->g_var == gvar)) {
     const int mid = std::max(1, chunk / 2);
     for (int q = 0; q < 2; ++q) {
       if (w->graph[q]) cudaGraphExecDestroy(w->graph[q]);
@@ -360,6 +362,7 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
     }
     w->gchunk = chunk;
     w->g_lf = lf;
+    w->g_var = gvar;
     w->g_mw = p->m_W;
     w->g_mu = p->mu;
     w->g_s1 = s1;
@@ -494,8 +497,9 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
         // chunks of correction iterations, a CUDA graph per (batch size, chunk); two chunks in
         // flight so the host's status check overlaps the next chunk (finished systems skip it)
         const bool rg = p->use_graphs != 0 && chunk > 1;
+        const int rvar = ms_pair_split(g, lf_ref) ? 1 : 0;  // the corrections run in FP32
         if (rg && !(w->rgraph && w->rg_gn == gn && w->rg_chunk == chunk && w->rg_lf == lf_ref && w->rg_mw == p->m_W &&
-                    w->rg_mu == p->mu)) {
+                    w->rg_mu == p->mu && w->rg_var == rvar)) {
           if (w->rgraph) cudaGraphExecDestroy(w->rgraph);
           w->rgraph = nullptr;
           cudaGraph_t gr;
@@ -512,6 +516,7 @@ ovl_status solve_multishift(ovl_lattice* lat, const ovl_sign_params* p, int nrhs
           w->rg_gn = gn;
           w->rg_chunk = chunk;
           w->rg_lf = lf_ref;
+          w->rg_var = rvar;
           w->rg_mw = p->m_W;
           w->rg_mu = p->mu;
         }

@@ -22,7 +22,7 @@ import pytest
 
 import synth
 from conftest import fp16_quantised
-from oracle import deflation, krylov, lanczos, rational, wilson
+from oracle import deflation, krylov, lanczos, matsign, rational, wilson
 
 pytestmark = pytest.mark.gpu
 
@@ -143,6 +143,27 @@ def test_every_pair_shape_equal_k_1212(ovl, lat12, prec):
     # the shapes differ only in the order of alpha's partial sums
     for x in xs[1:]:
         assert _rel(x, xs[0]) < (1e-12 if prec == "f64" else 1e-5)
+
+
+def test_shape_change_between_solves(ovl, ctx):
+    """Solves on one lattice with different pinned pair shapes: the cached chunk graphs must follow
+    the shape (a graph captured for one shape replayed in a solve of another mixed a deferred step
+    with plain ones and broke the recurrence). 2x2x2x4 to 1e-10 against the dense sign."""
+    dims = (2, 2, 2, 4)
+    u = synth.gauge_links(dims, 35, 0.1)
+    b = synth.gaussian_source(dims, 36)
+    xs = matsign.sign_eig(wilson.dense_hw(u, dims, -2.0, 0.3), b.ravel()).reshape(b.shape)
+    lat = ovl.ovl_create_lattice(ctx, dims, -1)
+    ovl.ovl_set_links(lat, u, ovl.OVL_F64)
+    try:
+        for var in (4, 7, 5, 7, 3):
+            ovl.ovl_set_pair_variant(32, ovl.OVL_PREC_F64, var)
+            st, info, x = _solve(ovl, lat, b, mu=0.3, tol=1e-10, k_max=384, check_every=16)
+            assert st == ovl.OVL_OK, (var, info)
+            assert _rel(x, xs) < 1e-10, var
+    finally:
+        ovl.ovl_set_pair_variant(32, ovl.OVL_PREC_F64, -1)
+        ovl.ovl_destroy_lattice(lat)
 
 
 @pytest.mark.parametrize("var", [7, 3])
