@@ -68,3 +68,20 @@ def test_serving_stream_is_the_configured_distribution():
     assert {r["nrhs"] for r in a} == set(range(1, 9))
     assert abs(np.mean([r["gap"] for r in a]) - 1.0) < 0.1
     assert bench._serving_stream(200) == a[:200]  # a prefix is the first requests of the full stream
+
+
+def test_summarize_launches(tmp_path, capsys):
+    """--summarize-launches: per-kernel totals, shares and means of an ncu launch list, starting at
+    the first launch of a named kernel."""
+    rows = [("probe<double>", 100.0), ("ovl::k_lz_start<double>", 2.0), ("ovl::k_lz_pair_dyn<double, 0>", 80.0),
+            ("ovl::k_lz_update<double, 1, 0>", 20.0), ("ovl::k_lz_pair_dyn<double, 0>", 82.0)]
+    lines = ["==PROF== Connected to process 1", '"ID","Kernel Name","Metric Unit","Metric Value"']
+    for i, (name, us) in enumerate(rows):
+        lines.append('"%d","void %s(Geom, LzDev)","ns","%d"' % (i, name, int(us * 1000)))
+    p = tmp_path / "launches.csv"
+    p.write_text("\n".join(lines) + "\n")
+    bench.summarize_launches(str(p), "k_lz_start")
+    out = capsys.readouterr().out.splitlines()
+    assert out[0] == "launches=4 total_us=184.0"
+    first = out[2].split()
+    assert first[0] == "ovl::k_lz_pair_dyn<double," and first[-4:] == ["2", "162.0", "88.0%", "81.00"]
