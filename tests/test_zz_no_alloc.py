@@ -45,6 +45,27 @@ def test_matches_allocating_path_twice(setup, kw):
         assert _rel(x, x_ref) < 1e-10
 
 
+@pytest.mark.parametrize("var", [7, 1])
+def test_matches_with_pinned_pair_shape(setup, var):
+    """The same with the pair-stencil shape pinned: 7 (one block per SM, the deferred step and its
+    settle kernels, as the 12^4 FP64 workload runs) and 1 (the split stencil)."""
+    ovl, ctx, dims, lat = setup
+    vol = int(np.prod(dims))
+    b = torch.from_numpy(synth.gaussian_source(dims, 1000, nrhs=2)).cuda()
+    p = ovl.ovl_sign_params_default(mu=0.3, tol=1e-9, k_max=1200)
+    ovl.ovl_set_pair_variant(vol, ovl.OVL_PREC_F64, var)
+    try:
+        x_ref = torch.empty_like(b)
+        st_ref, info_ref = ovl.ovl_apply_sign(lat, p, b, x_ref)
+        x = torch.full_like(b, float("nan"))
+        st, info = ovl.ovl_apply_sign_noalloc(lat, p, b, x)
+    finally:
+        ovl.ovl_set_pair_variant(vol, ovl.OVL_PREC_F64, -1)
+    assert st == st_ref == ovl.OVL_OK
+    assert [i["iterations"] for i in info] == [i["iterations"] for i in info_ref]
+    assert _rel(x, x_ref) < 1e-10
+
+
 def test_batch_matches(setup):
     ovl, ctx, dims, lat = setup
     b = torch.from_numpy(synth.gaussian_source(dims, 7, nrhs=2)).cuda()
