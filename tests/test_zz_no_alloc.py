@@ -52,7 +52,8 @@ def test_matches_with_pinned_pair_shape(setup, var):
     ovl, ctx, dims, lat = setup
     vol = int(np.prod(dims))
     b = torch.from_numpy(synth.gaussian_source(dims, 1000, nrhs=2)).cuda()
-    p = ovl.ovl_sign_params_default(mu=0.3, tol=1e-9, k_max=1200)
+    # two rhs at k_max 600 fit the static array; both reach 1e-5 near k = 500 at mu = 0.2
+    p = ovl.ovl_sign_params_default(mu=0.2, tol=1e-5, k_max=600)
     ovl.ovl_set_pair_variant(vol, ovl.OVL_PREC_F64, var)
     try:
         x_ref = torch.empty_like(b)
