@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sgn(H_W)b solves/s at rel.err 1e-8"
 UNIT = "solves/s"
+M_W = -2.0  # Wilson mass of the paper's configurations (Section 6)
 
 # Workloads: the lattice, chemical potentials, method and precision of one step.
 WORKLOADS = {
@@ -279,7 +280,7 @@ def _setup(ovl, ctx, wl, rng_seed=0, cache=None):
                 t0 = time.time()
                 # untimed set-up; its inverse solves in mixed precision (FP64 reliable updates to
                 # the same 1e-12), about twice as fast as FP64 ones at 8^4
-                lam, R, L, gap, info = spectrum.critical_eigenpairs(ovl, lat, -2.0, mu, wl["m"],
+                lam, R, L, gap, info = spectrum.critical_eigenpairs(ovl, lat, M_W, mu, wl["m"],
                                                                     precision=ovl.OVL_PREC_F32)
                 d.update(lam=lam, R=R, L=L, gap=gap, setup_s=time.time() - t0,
                          setup_inverse_solves=info["inverse_solves"])
@@ -289,14 +290,14 @@ def _setup(ovl, ctx, wl, rng_seed=0, cache=None):
             if key + "_lo" in stored:
                 d["gap"] = float(stored[key + "_lo"])
             else:
-                d["gap"] = spectrum.smallest_modulus(ovl, lat, -2.0, mu, precision=ovl.OVL_PREC_F32)
+                d["gap"] = spectrum.smallest_modulus(ovl, lat, M_W, mu, precision=ovl.OVL_PREC_F32)
                 stored[key + "_lo"] = np.array(d["gap"])
                 changed = True
         if wl["method"] in ("multishift", "fom"):
             if key + "_hi" in stored:
                 d["spec_hi"] = float(stored[key + "_hi"])
             else:
-                d["spec_hi"] = 1.02 * spectrum.largest_modulus(ovl, lat, -2.0, mu)
+                d["spec_hi"] = 1.02 * spectrum.largest_modulus(ovl, lat, M_W, mu)
                 stored[key + "_hi"] = np.array(d["spec_hi"])
                 changed = True
         per_mu.append(d)
@@ -307,7 +308,7 @@ def _setup(ovl, ctx, wl, rng_seed=0, cache=None):
 
 def _params(ovl, wl, d):
     prec = {"f64": ovl.OVL_PREC_F64, "f32": ovl.OVL_PREC_F32, "f16": ovl.OVL_PREC_F32_F16LINKS}[wl["precision"]]
-    kw = dict(m_W=-2.0, mu=d["mu"], tol=wl["tol"], k_max=wl["k_max"], precision=prec,
+    kw = dict(m_W=M_W, mu=d["mu"], tol=wl["tol"], k_max=wl["k_max"], precision=prec,
               use_deflation=1 if wl["m"] > 0 else 0, check_every=25, two_pass=wl.get("two_pass", 0))
     if wl["method"] in ("multishift", "fom"):
         kw.update(method=ovl.OVL_MULTISHIFT_BICG if wl["method"] == "multishift" else ovl.OVL_FOM_RESTARTED,
@@ -353,7 +354,7 @@ def _time_workload(ovl, ctx, args, wl, u, per_mu, b, flush, world, steps=None, w
         lt = ovl.ovl_create_lattice(ctx, wl["dims"], -1)
         ovl.ovl_set_links(lt, u, ovl.OVL_F64 | ovl.OVL_F32 | ovl.OVL_F16R12)
         if wl["m"] > 0:
-            ovl.ovl_set_deflation(lt, -2.0, d["mu"], d["R"], d["L"], d["lam"])
+            ovl.ovl_set_deflation(lt, M_W, d["mu"], d["R"], d["L"], d["lam"])
         lats.append(lt)
     bdev = torch.from_numpy(b).cuda()
     xdevs = [torch.empty_like(bdev) for _ in per_mu]
@@ -446,13 +447,13 @@ def _dslash_gbs(ovl, ctx, u_fn, L=32, reps=20):
     for name, fl, per_site in (("f32", ovl.OVL_LINKS_F32, 480), ("f16_links", ovl.OVL_LINKS_F16R12, 288)):
         flags = fl | ovl.OVL_NATIVE | ovl.OVL_GAMMA5
         for _ in range(3):
-            ovl.ovl_apply_DW(lat, -2.0, 0.3, flags, x, y)
+            ovl.ovl_apply_DW(lat, M_W, 0.3, flags, x, y)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
-            ovl.ovl_apply_DW(lat, -2.0, 0.3, flags, x, y)
+            ovl.ovl_apply_DW(lat, M_W, 0.3, flags, x, y)
         e1.record(stream)
         e1.synchronize()
         t = e0.elapsed_time(e1) / reps
@@ -480,9 +481,9 @@ def _dslash_batch_gbs(ovl, ctx, u_fn, L=24, nrhs=16, reps=5):
     byts = vol * (288 + nrhs * 192)
     stream = torch.cuda.current_stream()
     res = {}
-    for name, run in (("f32_batch%d" % nrhs, lambda: ovl.ovl_apply_DW(lat, -2.0, 0.3, flags, x, y)),
+    for name, run in (("f32_batch%d" % nrhs, lambda: ovl.ovl_apply_DW(lat, M_W, 0.3, flags, x, y)),
                       ("f32_batch%d_one_by_one" % nrhs,
-                       lambda: [ovl.ovl_apply_DW(lat, -2.0, 0.3, flags, x[r * 12 * vol:(r + 1) * 12 * vol],
+                       lambda: [ovl.ovl_apply_DW(lat, M_W, 0.3, flags, x[r * 12 * vol:(r + 1) * 12 * vol],
                                                  y[r * 12 * vol:(r + 1) * 12 * vol]) for r in range(nrhs)])):
         for _ in range(2):
             run()
@@ -585,7 +586,7 @@ def _c2_line(ovl, ctx, args):
     bt = torch.from_numpy(b).cuda()
     out = []
     for d in per_mu:
-        ovl.ovl_set_deflation(lat, -2.0, d["mu"], d["R"], d["L"], d["lam"])
+        ovl.ovl_set_deflation(lat, M_W, d["mu"], d["R"], d["L"], d["lam"])
         row = {"mu": d["mu"], "deflated": wl["m"], "gap": d["gap"]}
         for tag, kw in (("fixed_k600", dict(fixed_k=C2["k_fixed"])),
                         ("tol1e-10", dict(tol=C2["tol"], k_max=C2["k_max"]))):
@@ -641,7 +642,7 @@ def run_ours(args, wl):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "f64" else "f32",
         "data": "synthetic: SU(3) links exp(0.5 i H) seed 0, Gaussian b seed 1000",
         "config": {"workload": args.workload, "lattice": "x".join(map(str, wl["dims"])), "n": int(n),
-                   "mu": list(wl["mus"]), "m_W": -2.0, "deflated": wl["m"], "method": wl["method"],
+                   "mu": list(wl["mus"]), "m_W": M_W, "deflated": wl["m"], "method": wl["method"],
                    "precision": prec, "tol": wl["tol"], "k_max": wl["k_max"], "nrhs": nrhs,
                    "solves_per_step": solves_per_step, "concurrent_solves": bool(args.concurrent),
                    "stream_priority": "longest solve most urgent" if args.concurrent and len(per_mu) > 1 else "default",
@@ -858,7 +859,7 @@ def _oracle_inputs(wl, mu):
     b0 = b[0] if wl.get("nrhs", 1) > 1 else b
     R = L = lam = None
     if wl["m"] > 0:
-        lam, R, L, _ = deflation.critical_sparse(u, dims, -2.0, mu, wl["m"])
+        lam, R, L, _ = deflation.critical_sparse(u, dims, M_W, mu, wl["m"])
     return u, b0, R, L, lam
 
 
@@ -872,7 +873,7 @@ def _oracle_solve(wl, mu, k, seconds):
 
     u, b0, R, L, lam = _oracle_inputs(wl, mu)
     dims = wl["dims"]
-    s = krylov.DirectSolve(u, dims, -2.0, mu, b0, k, R=R, L=L, lam=lam)
+    s = krylov.DirectSolve(u, dims, M_W, mu, b0, k, R=R, L=L, lam=lam)
     t0 = time.perf_counter()
     s.start()
     s.steps(10)
@@ -923,9 +924,9 @@ def run_reference(args, wl):
     solves = []
     for mu in wl["mus"]:
         u, b0, R, L, lam = _oracle_inputs(wl, mu)
-        solves.append(krylov.DirectSolve(u, wl["dims"], -2.0, mu, b0, int(ktab.get(mu, wl["k_max"])), R=R, L=L,
+        solves.append(krylov.DirectSolve(u, wl["dims"], M_W, mu, b0, int(ktab.get(mu, wl["k_max"])), R=R, L=L,
                                          lam=lam))
-    warm = krylov.DirectSolve(u, wl["dims"], -2.0, wl["mus"][0], b0, args.warmup + 1).start()
+    warm = krylov.DirectSolve(u, wl["dims"], M_W, wl["mus"][0], b0, args.warmup + 1).start()
     for _ in range(args.warmup):
         warm.steps(1)
     del warm
@@ -985,7 +986,7 @@ def run_profile_case(args):
         y = torch.empty_like(x)
         fl = {"f64": 0, "f32": ovl.OVL_LINKS_F32, "f16": ovl.OVL_LINKS_F16R12}[args.prec]
         for _ in range(3):
-            ovl.ovl_apply_DW(lat, -2.0, 0.3, fl | ovl.OVL_NATIVE | ovl.OVL_GAMMA5, x, y)
+            ovl.ovl_apply_DW(lat, M_W, 0.3, fl | ovl.OVL_NATIVE | ovl.OVL_GAMMA5, x, y)
     else:
         b = torch.from_numpy(synth.gaussian_source(dims, 1000, nrhs=args.nrhs if args.nrhs > 1 else None)).cuda()
         x = torch.empty_like(b)

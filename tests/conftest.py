@@ -15,6 +15,24 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: takes more than a few seconds on CPU")
 
 
+def read_paper_values():
+    """The values the paper prints (tests/golden/paper_values.txt, each line citing its passage),
+    as {key: float}."""
+    vals = {}
+    with open(os.path.join(ROOT, "tests", "golden", "paper_values.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = (x.strip() for x in line.split("=", 1))
+                vals[k] = float(v)
+    return vals
+
+
+@pytest.fixture(scope="session")
+def paper():
+    return read_paper_values()
+
+
 def fp16_quantised(u):
     """Links as the FP16 12-real format stores them: the first two rows' real and imaginary parts
     rounded to float32 and then to float16, the third row rebuilt as conj(row1 x row2) (SU(3)).
