@@ -897,15 +897,45 @@ def _oracle_solve(wl, mu, k, seconds):
                    "plus numpy eig of H_k scaled as k^3" % (lat, mu, kk, k, t_steps))
 
 
+def _oracle_step_scaling(wl, mu, seconds=4.0, max_steps=40):
+    """Milliseconds per Lanczos step of the C oracle (two stencil applications and the biorthogonal
+    update of Algorithm 4) on one core and on all of this host's cores, each timed over up to
+    `max_steps` steps within about seconds / 2, after two untimed steps."""
+    from oracle import krylov
+
+    u, b0, R, L, lam = _oracle_inputs(wl, mu)
+    all_cores = krylov.threads()
+    out = {}
+    try:
+        for nt in sorted({1, all_cores}):
+            krylov.threads(nt)
+            s = krylov.DirectSolve(u, wl["dims"], M_W, mu, b0, max_steps + 2, R=R, L=L, lam=lam).start()
+            s.steps(2)
+            k0 = s.k
+            t0 = time.perf_counter()
+            while s.k < k0 + max_steps and (s.k - k0 < 3 or time.perf_counter() - t0 < seconds / 2):
+                before = s.k
+                if s.steps(1) == before:  # breakdown, or nothing to start from
+                    break
+            done = s.k - k0
+            if done > 0:
+                out[str(nt)] = 1e3 * (time.perf_counter() - t0) / done
+    finally:
+        krylov.threads(all_cores)
+    return out
+
+
 def cpu_baseline(wl, workload, iterations, seconds=20.0):
     """The oracle on this host's cores, one solve of the workload's hardest mu at the k the GPU
-    needed (bounded: see _oracle_solve)."""
+    needed (bounded: see _oracle_solve), and its per-step time on one core and on all cores."""
     from oracle import krylov
 
     mu = wl["mus"][-1]
     k = int(round(float(np.mean(iterations)))) if len(iterations) else K_TABLE.get(workload, {}).get(mu, wl["k_max"])
     t, desc = _oracle_solve(wl, mu, k, seconds)
-    return {"value": 1.0 / t, "unit": UNIT, "cores": krylov.threads(), "kind": "oracle", "sample": desc}
+    res = {"value": 1.0 / t, "unit": UNIT, "cores": krylov.threads(), "kind": "oracle", "sample": desc}
+    res["step_ms_by_cores"] = _oracle_step_scaling(wl, mu)
+    return res
 
 
 def run_reference(args, wl):

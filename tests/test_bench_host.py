@@ -38,6 +38,20 @@ def test_reference_arm_runs_full_oracle_solves(capsys, monkeypatch):
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
 
 
+def test_cpu_baseline_reports_one_core_and_all_cores():
+    """The oracle leg of the bench line: one 4^4 solve at the tabled k, and the C oracle's time per
+    Lanczos step on one core and on all cores (the thread count is restored afterwards)."""
+    from oracle import krylov
+
+    wl = bench.WORKLOADS["lattice4_mu0.3_direct_f64"]
+    before = krylov.threads()
+    res = bench.cpu_baseline(wl, "lattice4_mu0.3_direct_f64", [], seconds=5.0)
+    assert krylov.threads() == before
+    assert res["kind"] == "oracle" and res["value"] > 0 and res["cores"] == before
+    steps = res["step_ms_by_cores"]
+    assert set(steps) == {"1", str(before)} and all(v > 0 for v in steps.values())
+
+
 def test_pair_bytes_count_links_once_per_batch():
     vol = 16 ** 4
     one = bench.pair_bytes("f32", vol, 1)
