@@ -97,7 +97,9 @@ int64_t ovl_lattice_n(const ovl_lattice* lat);
 
 /* Copy links U (canonical complex128 layout, host or device memory per U_on_device)
  * into library-owned device copies in each format of the `formats` bit set (OVL_F64 is
- * always kept). The caller's buffer may be freed on return (the call synchronises).
+ * always kept). Every format the lattice already holds from an earlier call is rewritten
+ * from U as well, so no copy keeps the previous field. The caller's buffer may be freed on
+ * return (the call synchronises).
  * Errors: EINVAL, EBUSY (a solve is reading the links), ENOMEM, ECUDA. */
 ovl_status ovl_set_links(ovl_lattice* lat, const void* U, int32_t U_on_device, uint32_t formats);
 

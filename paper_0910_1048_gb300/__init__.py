@@ -210,41 +210,78 @@ def ovl_lattice_n(lat) -> int:
     return int(lib.ovl_lattice_n(lat))
 
 
+def _host_or_device_c128(a, count, where, nm):
+    """A complex128 input of `count` elements: a numpy array (made contiguous complex128 here) or
+    a contiguous complex128 tensor (CUDA, or CPU). Returns (buffer, on_device)."""
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.complex128)
+        size, dev = a.size, False
+    elif hasattr(a, "data_ptr"):
+        if str(a.dtype) != "torch.complex128" or not a.is_contiguous():
+            raise TypeError("%s: %s must be a contiguous complex128 tensor" % (where, nm))
+        size, dev = a.numel(), _on_device(a)
+    else:
+        raise TypeError("%s: %s must be a numpy array or a torch tensor, got %r" % (where, nm, type(a)))
+    if size != count:
+        raise ValueError("%s: %s holds %d complex entries, %d expected" % (where, nm, size, count))
+    return a, dev
+
+
 def ovl_set_links(lat, U, formats: int = OVL_F64):
-    if isinstance(U, np.ndarray):
-        U = np.ascontiguousarray(U, dtype=np.complex128)
-    _check(lib.ovl_set_links(lat, _ptr(U), 1 if _on_device(U) else 0, formats))
+    """U: the canonical [4][Lt][Lz][Ly][Lx][3][3] complex128 links (36 V entries), host or device."""
+    U, dev = _host_or_device_c128(U, 3 * ovl_lattice_n(lat), "ovl_set_links", "U")
+    _check(lib.ovl_set_links(lat, _ptr(U), 1 if dev else 0, formats))
 
 
 def ovl_set_deflation(lat, m_W, mu, R, L, lam):
-    """R, L: [m][n] complex128 (canonical), lam: [m] complex128; host or device."""
+    """R, L: [m][n] complex128 (canonical), lam: [m] complex128; all on the host or all on the device."""
     if R is None or len(R) == 0:
         _check(lib.ovl_set_deflation(lat, m_W, mu, 0, None, None, None, 0))
         return
-    dev = _on_device(R)
-    if not dev:
-        R = np.ascontiguousarray(R, dtype=np.complex128)
-        L = np.ascontiguousarray(L, dtype=np.complex128)
-        lam = np.ascontiguousarray(lam, dtype=np.complex128)
-    _check(lib.ovl_set_deflation(lat, m_W, mu, int(R.shape[0]), _ptr(R), _ptr(L), _ptr(lam), 1 if dev else 0))
+    m, n = int(R.shape[0]), ovl_lattice_n(lat)
+    R, dev = _host_or_device_c128(R, m * n, "ovl_set_deflation", "R")
+    L, dev_l = _host_or_device_c128(L, m * n, "ovl_set_deflation", "L")
+    lam, dev_lam = _host_or_device_c128(lam, m, "ovl_set_deflation", "lam")
+    if not dev == dev_l == dev_lam:
+        raise TypeError("ovl_set_deflation: R, L and lam must all be host or all be device buffers")
+    _check(lib.ovl_set_deflation(lat, m_W, mu, m, _ptr(R), _ptr(L), _ptr(lam), 1 if dev else 0))
+
+
+def _spinor_pair(lat, inp, out, where):
+    """Validate the in / out pair of a stream-ordered spinor call before any pointer reaches the
+    library: contiguous CUDA tensors on the lattice's device, the same complex dtype, a whole
+    number of spinors each. Returns nrhs."""
+    n = ovl_lattice_n(lat)
+    for nm, a in (("in", inp), ("out", out)):
+        if not _on_device(a):
+            raise TypeError("%s: %s must be a CUDA tensor" % (where, nm))
+        if not a.is_contiguous():
+            raise TypeError("%s: %s must be contiguous" % (where, nm))
+        dev = _LAT_DEVICE.get(lat.value)
+        if dev is not None and a.device.index != dev:
+            raise ValueError("%s: %s is on cuda:%s, the lattice on cuda:%d" % (where, nm, a.device.index, dev))
+    _dtype_code(inp)
+    if out.dtype != inp.dtype:
+        raise TypeError("%s: in and out must have the same dtype" % where)
+    if inp.numel() == 0 or inp.numel() % n != 0 or out.numel() != inp.numel():
+        raise ValueError("%s: in/out must hold nrhs * n elements (n = %d), got %d and %d"
+                         % (where, n, inp.numel(), out.numel()))
+    return inp.numel() // n
 
 
 def ovl_to_native(lat, inp, out, stream=None):
-    nrhs = inp.numel() // ovl_lattice_n(lat)
+    nrhs = _spinor_pair(lat, inp, out, "ovl_to_native")
     _check(lib.ovl_to_native(lat, _dtype_code(inp), nrhs, _ptr(inp), _ptr(out), _stream(stream, inp)))
 
 
 def ovl_from_native(lat, inp, out, stream=None):
-    nrhs = inp.numel() // ovl_lattice_n(lat)
+    nrhs = _spinor_pair(lat, inp, out, "ovl_from_native")
     _check(lib.ovl_from_native(lat, _dtype_code(inp), nrhs, _ptr(inp), _ptr(out), _stream(stream, inp)))
 
 
 def ovl_apply_DW(lat, m_W, mu, flags, inp, out, stream=None):
     """out = D_W(mu) inp (flags OVL_DAGGER / OVL_GAMMA5 / OVL_NATIVE / OVL_LINKS_*); device tensors."""
-    n = ovl_lattice_n(lat)
-    nrhs = inp.numel() // n
-    if inp.numel() != nrhs * n or out.numel() != inp.numel() or out.dtype != inp.dtype:
-        raise ValueError("in/out must hold nrhs * n elements of the same dtype")
+    nrhs = _spinor_pair(lat, inp, out, "ovl_apply_DW")
     _check(lib.ovl_apply_DW(lat, m_W, mu, flags, _dtype_code(inp), nrhs, _ptr(inp), _ptr(out),
                             _stream(stream, inp, out)))
 

@@ -157,6 +157,9 @@ ovl_status ovl_set_links(ovl_lattice* lat, const void* U, int32_t U_on_device, u
   OVL_DEVICE_SCOPE(lat->ctx->device);
   const size_t nl = (size_t)36 * lat->g.vol;  // complex entries
   formats |= OVL_F64;
+  // a copy held from an earlier call is refreshed too: no format may keep the previous field
+  if (lat->u32) formats |= OVL_F32;
+  if (lat->u16) formats |= OVL_F16R12;
   if (!lat->u64) OVL_CHECK_CUDA(cudaMalloc(&lat->u64, nl * 16));
   if ((formats & OVL_F32) && !lat->u32) OVL_CHECK_CUDA(cudaMalloc(&lat->u32, nl * 8));
   if ((formats & OVL_F16R12) && !lat->u16) OVL_CHECK_CUDA(cudaMalloc(&lat->u16, (size_t)24 * lat->g.vol * 4));

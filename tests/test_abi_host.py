@@ -142,6 +142,41 @@ def test_sign_buffers_refused_before_the_library(ovl, monkeypatch):
             ovl.ovl_apply_sign_noalloc(lat, p, b, x)
 
 
+def test_stencil_and_set_up_buffers_refused_before_the_library(ovl, monkeypatch):
+    """The stencil and layout calls take CUDA tensors only (a host pointer would reach a kernel);
+    links and deflation vectors must be complex128 of the lattice's sizes (a short or mistyped
+    buffer would be read out of bounds by the copies)."""
+    import torch
+
+    n = 3072
+    monkeypatch.setattr(ovl, "ovl_lattice_n", lambda lat: n)
+    lat = ovl.ctypes.c_void_p(12345)
+    spinor_cases = [
+        (np.zeros(n, np.complex128), np.zeros(n, np.complex128)),                     # host arrays
+        (torch.zeros(n, dtype=torch.complex128), torch.zeros(n, dtype=torch.complex128)),  # CPU tensors
+    ]
+    for fn in (lambda a, b: ovl.ovl_apply_DW(lat, -2.0, 0.3, 0, a, b),
+               lambda a, b: ovl.ovl_to_native(lat, a, b),
+               lambda a, b: ovl.ovl_from_native(lat, a, b)):
+        for a, b in spinor_cases:
+            with pytest.raises(TypeError):
+                fn(a, b)
+    links = 3 * n  # 4 directions x 9 colour entries per site = 36 V = 3 n
+    for U in (np.zeros(links - 9, np.complex128),                  # too short
+              torch.zeros(links, dtype=torch.complex64),            # complex64 tensor
+              torch.zeros(2 * links, dtype=torch.complex128)[::2],  # not contiguous
+              [0.0] * links):                                        # not an array
+        with pytest.raises((TypeError, ValueError)):
+            ovl.ovl_set_links(lat, U, ovl.OVL_F64)
+    m = 2
+    R = np.zeros((m, n), np.complex128)
+    for args in ((R, np.zeros((m, n - 1), np.complex128), np.zeros(m, np.complex128)),   # L too short
+                 (R, R, np.zeros(m + 1, np.complex128)),                                 # lambda too long
+                 (R, torch.zeros(m * n, dtype=torch.complex64), np.zeros(m, np.complex128))):
+        with pytest.raises((TypeError, ValueError)):
+            ovl.ovl_set_deflation(lat, -2.0, 0.3, *args)
+
+
 def test_pair_variant_table(ovl):
     vol = 6 * 6 * 6 * 10  # a volume no other test solves
     assert ovl.ovl_get_pair_variant(vol, ovl.OVL_PREC_F32) == -1

@@ -82,6 +82,24 @@ def test_dslash_f32_links(ovl, ctx, dims, links, tol):
     ovl.ovl_destroy_lattice(lat)
 
 
+def test_set_links_again_rewrites_every_held_format(ovl, ctx):
+    """A second ovl_set_links that names only FP64 still rewrites the FP32 and FP16 copies the
+    lattice holds from the first call: the reduced-precision stencils then apply the new field."""
+    dims = (4, 4, 4, 4)
+    lat, _ = _lattice(ovl, ctx, dims, 21)
+    u2 = synth.gauge_links(dims, 22)
+    ovl.ovl_set_links(lat, u2, ovl.OVL_F64)
+    psi = synth.gaussian_source(dims, 23)
+    ref = wilson.apply_hw(u2, psi, -2.0, 0.3)
+    inp = torch.from_numpy(psi).to(torch.complex64).cuda()
+    for flag, tol in ((ovl.OVL_LINKS_F32, 2e-6), (ovl.OVL_LINKS_F16R12, 3e-3)):
+        out = torch.empty_like(inp)
+        ovl.ovl_apply_DW(lat, -2.0, 0.3, ovl.OVL_GAMMA5 | flag, inp, out)
+        err = np.abs(out.cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err < tol, (flag, err)
+    ovl.ovl_destroy_lattice(lat)
+
+
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_native_layout_roundtrip(ovl, ctx, dtype):
     dims = (6, 4, 2, 4)
