@@ -934,7 +934,10 @@ def cpu_baseline(wl, workload, iterations, seconds=20.0):
     k = int(round(float(np.mean(iterations)))) if len(iterations) else K_TABLE.get(workload, {}).get(mu, wl["k_max"])
     t, desc = _oracle_solve(wl, mu, k, seconds)
     res = {"value": 1.0 / t, "unit": UNIT, "cores": krylov.threads(), "kind": "oracle", "sample": desc}
-    res["step_ms_by_cores"] = _oracle_step_scaling(wl, mu)
+    try:
+        res["step_ms_by_cores"] = _oracle_step_scaling(wl, mu)
+    except Exception as e:  # a side figure: it never costs the line
+        res["step_ms_by_cores"] = {"error": "%s: %s" % (type(e).__name__, e)}
     return res
 
 
