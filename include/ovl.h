@@ -247,9 +247,13 @@ ovl_status ovl_get_tridiag(ovl_lattice* lat, int32_t rhs, int32_t k_cap, int32_t
 
 /* y = sign(T) e_1 for the k x k tridiagonal T (diagonal alpha[k], super beta[k-1],
  * sub delta[k-1], complex128), written to y[k] complex128 (Section 2: f of the small
- * projected matrix). Host-only, FP64. method 0 = automatic, 1 = O(k^2) complex-symmetric
- * QL with replayed rotations, 2 = dense scaled Newton (O(k^3)).
- * Errors: EINVAL; EILLPOSED when a Ritz value lies on the imaginary axis. */
+ * projected matrix). Host-only, FP64. method 0 = automatic (3, then 1, then 2 up to k = 200),
+ * 1 = O(k^2) complex-symmetric QL with replayed rotations, 2 = dense scaled Newton (O(k^3)),
+ * 3 = rational route: g_s(c T) e_1 of Section 5 (Eq. pfe_s) with c and s chosen from the Ritz
+ * values by Theorem 1's bound, two tridiagonal solves per pole, accepted when the involution
+ * residual |g(cT) y - e_1| is below 1e-11.
+ * Errors: EINVAL; EILLPOSED when a Ritz value lies on the imaginary axis; ENOCONV when the
+ * chosen route misses its accuracy check. */
 ovl_status ovl_small_sign(int32_t k, const void* alpha, const void* beta, const void* delta,
                           void* y, int32_t method);
 
