@@ -294,65 +294,74 @@ ovl_status small_sign_ql(int k, const cz* al, const cz* be, const cz* de, cz* y,
 
 namespace {
 
-// Eigenvalues only of the complex symmetric tridiagonal (same sweeps as cs_qr, no rotations kept).
-bool cs_eigs(std::vector<cz> d, std::vector<cz> e, std::vector<cz>& lam) {
+// Eigenvalues only of the complex symmetric tridiagonal with diagonal d and squared off-diagonal
+// e2 (the eigenvalues depend on the squares alone). Implicitly shifted QR sweeps from the top of the
+// unreduced block to its bottom, deflating there, in the root-free form of Pal, Walker and Kahan
+// (Parlett, The Symmetric Eigenvalue Problem, Section 8.15): the sweep carries gamma = c (d - shift)
+// - s gamma' and p = gamma^2 / c with c, s the squares of the rotation's cosine and sine, so a
+// rotation takes one reciprocal and no square root. The algebra holds for complex symmetric
+// matrices with complex orthogonal rotations (c + s = 1); a rotation whose r = p + e^2 cancels
+// (an isotropic column, where the complex symmetric QR breaks down) gives up.
+bool cs_eigs(std::vector<cz> d, std::vector<cz> e2, std::vector<cz>& lam) {
   const int k = (int)d.size();
-  const double eps = 1e-15;
+  const double eps2 = 1e-30;  // (1e-15)^2
   long long budget = 60LL * k + 100;
-  // |e_i| <= eps (|d_i| + |d_i+1|) in squared magnitudes (no square roots in the scan)
-  auto negligible = [&](int i) { return std::norm(e[i]) <= eps * eps * (std::norm(d[i]) + std::norm(d[i + 1])); };
+  // |e_i| <= eps (|d_i| + |d_i+1|), tested as |e_i^2|^2 <= eps^4 (|d_i|^2 + |d_i+1|^2)^2
+  auto negligible = [&](int i) {
+    const double t = std::norm(d[i]) + std::norm(d[i + 1]);
+    return std::norm(e2[i]) <= eps2 * eps2 * t * t;
+  };
   int hi = k - 1;
   while (hi > 0) {
     if (negligible(hi - 1)) {
-      e[hi - 1] = 0;
+      e2[hi - 1] = 0;
       --hi;
       continue;
     }
     int lo = hi - 1;
     while (lo > 0 && !negligible(lo - 1)) --lo;
-    if (lo > 0) e[lo - 1] = 0;
+    if (lo > 0) e2[lo - 1] = 0;
     if (--budget < 0) return false;
-    cz a = d[hi - 1], b = d[hi], ee = e[hi - 1];
-    cz half = 0.5 * (a - b);
-    cz disc = csqrt_fast(half * half + ee * ee);
-    cz m1 = 0.5 * (a + b) + disc, m2 = 0.5 * (a + b) - disc;
-    cz shift = std::abs(m1 - b) < std::abs(m2 - b) ? m1 : m2;
-    cz x = d[lo] - shift, z = e[lo];
-    for (int p = lo; p < hi; ++p) {
-      const int q = p + 1;
-      // complex orthogonal rotation: c = x / rho, s = -z / rho with rho^2 = x^2 + z^2; it fails
-      // (the complex symmetric QR breaks down) when |x^2 + z^2| << |x|^2 + |z|^2
-      const cz rho2 = x * x + z * z;
-      const double scale2 = std::norm(x) + std::norm(z);
-      if (!(std::norm(rho2) > 1e-32 * scale2 * scale2) || scale2 == 0.0) return false;
-      const cz rho = csqrt_fast(rho2);
-      const cz inv = std::conj(rho) * (1.0 / std::norm(rho));
-      cz c = x * inv, s = -z * inv;
-      if (p > lo) e[p - 1] = rho;
-      cz dp = d[p], dq = d[q], ep = e[p];
-      cz c2 = c * c, s2 = s * s, cs = c * s;
-      d[p] = dp * c2 - 2.0 * ep * cs + dq * s2;
-      d[q] = dp * s2 + 2.0 * ep * cs + dq * c2;
-      e[p] = cs * (dp - dq) + ep * (c2 - s2);
-      if (q < hi) {
-        z = -s * e[q];
-        e[q] = c * e[q];
-        x = e[p];
-      }
+    // Wilkinson shift: eigenvalue of the trailing 2x2 closer to d[hi]
+    const cz a = d[hi - 1], b = d[hi];
+    const cz half = 0.5 * (a - b);
+    const cz disc = csqrt_fast(half * half + e2[hi - 1]);
+    const cz m1 = 0.5 * (a + b) + disc, m2 = 0.5 * (a + b) - disc;
+    const cz shift = std::norm(m1 - b) < std::norm(m2 - b) ? m1 : m2;
+    cz c = 1.0, s = 0.0;
+    cz gam = d[lo] - shift;
+    cz p = gam * gam;
+    for (int i = lo; i < hi; ++i) {
+      const cz bb = e2[i];
+      const cz r = p + bb;
+      const double nr = std::norm(r);
+      if (!(nr > 1e-32 * (std::norm(p) + std::norm(bb)))) return false;  // cancellation, or not finite
+      const cz inv_r = std::conj(r) * (1.0 / nr);
+      if (i > lo) e2[i - 1] = s * r;
+      const cz oldc = c, oldgam = gam;
+      c = p * inv_r;
+      s = bb * inv_r;
+      const cz alpha = d[i + 1];
+      gam = c * (alpha - shift) - s * oldgam;
+      d[i] = oldgam + (alpha - gam);
+      const double nc = std::norm(c);
+      p = nc > 0.0 ? gam * gam * std::conj(c) * (1.0 / nc) : oldc * bb;
     }
+    e2[hi - 1] = s * p;
+    d[hi] = shift + gam;
   }
   lam = d;
   return true;
 }
 
-// Ritz values of H_k (via its complex symmetric similar S).
+// Ritz values of H_k: its complex symmetric similar S has the squared off-diagonal beta_j delta_j.
 bool ritz_values(int k, const cz* al, const cz* be, const cz* de, std::vector<cz>& lam) {
-  std::vector<cz> dg(al, al + k), gm(k - 1);
+  std::vector<cz> dg(al, al + k), g2(k - 1);
   for (int i = 0; i + 1 < k; ++i) {
-    gm[i] = std::sqrt(be[i] * de[i]);
-    if (gm[i] == cz(0)) return false;
+    g2[i] = be[i] * de[i];
+    if (g2[i] == cz(0)) return false;
   }
-  return cs_eigs(dg, gm, lam);
+  return cs_eigs(dg, g2, lam);
 }
 
 // (c, s): fewest poles with 2 |(c mu - 1)/(c mu + 1)|^{2s} <= eps over the Ritz values.
@@ -366,16 +375,21 @@ bool choose_scale(const std::vector<cz>& lam, double eps, int s_max, double* c_o
     amin = std::min(amin, std::abs(m));
     amax = std::max(amax, std::abs(m));
   }
-  double best_q = 1.0, best_c = 1.0;
+  // q(c) = max over mu of |c mu - 1| / |c mu + 1|, compared in squares (q2 = q^2)
+  double best_q2 = 1.0, best_c = 1.0;
   const int ng = 160;
   for (int t = 0; t <= ng; ++t) {
     double c = std::exp(std::log(1.0 / amax) + (std::log(1.0 / amin) - std::log(1.0 / amax)) * t / ng);
-    double q = 0;
-    for (cz m : mu) q = std::max(q, std::abs((c * m - 1.0) / (c * m + 1.0)));
-    if (q < best_q) best_q = q, best_c = c;
+    double q2 = 0;
+    for (cz m : mu) {
+      const double xr = c * m.real(), xi = c * m.imag();
+      const double num = (xr - 1.0) * (xr - 1.0) + xi * xi, den = (xr + 1.0) * (xr + 1.0) + xi * xi;
+      q2 = std::max(q2, num / den);
+    }
+    if (q2 < best_q2) best_q2 = q2, best_c = c;
   }
-  if (!(best_q < 1.0)) return false;
-  double sr = std::log(eps / 2.0) / (2.0 * std::log(best_q));
+  if (!(best_q2 < 1.0)) return false;
+  double sr = std::log(eps / 2.0) / std::log(best_q2);  // 2 q^{2s} <= eps
   int s = std::max(1, (int)std::ceil(sr));
   if (s > s_max) return false;
   *c_out = best_c;

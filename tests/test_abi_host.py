@@ -62,6 +62,22 @@ def test_small_sign_matches_eig(ovl, mu, k, method):
     assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < tol
 
 
+@pytest.mark.parametrize("mu,k", [(0.3, 400), (0.8, 600)])
+def test_rational_route_at_large_k(ovl, mu, k):
+    """The rational route alone (method 3: its scale c and pole count s come from the Ritz values of
+    H_k, no fallback) on H_k of the C oracle's Algorithm 4 at 4^4, against the eigendecomposition."""
+    from oracle import krylov
+
+    dims = (4, 4, 4, 4)
+    s = krylov.DirectSolve(synth.gauge_links(dims, 0), dims, -2.0, mu, synth.gaussian_source(dims, 1000), k).start()
+    s.steps(k)
+    al, be, de = s.alpha[:k], s.beta[:k - 1], s.delta[:k - 1]
+    ref = lanczos.sign_tridiag_e1(al, be, de)
+    st, y = ovl.ovl_small_sign(al, be, de, 3)
+    assert st == ovl.OVL_OK
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-10
+
+
 def test_small_sign_closed_forms(ovl):
     # 1x1 and a 2x2 with eigenvalues of opposite sign: sign(T) e1 from the 2x2 formula
     assert ovl.ovl_small_sign([2.0 + 1j], [], [])[1][0] == 1
