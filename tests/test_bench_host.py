@@ -63,6 +63,24 @@ def test_pair_bytes_count_links_once_per_batch():
     assert bench.PAIR_FLOPS_PER_SITE == 2 * 1368
 
 
+def test_roofline_arithmetic():
+    """The line's roofline: FP64 pair stencil = algorithmic flops (2 x 1368 per site and rhs) per
+    event-timed launch against the FP64 peak; FP32 = algorithmic bytes (links once per batch) per
+    launch against the measured HBM copy bandwidth."""
+    infos = [[(0, [{"t_kernel_ms": 0.08, "kernel_samples": 4}])], [(0, [{"t_kernel_ms": 0.12, "kernel_samples": 4}])]]
+    t = 0.1e-3  # mean of the two steps' samples, seconds
+    r = bench._roofline(bench.WORKLOADS["lattice12_mu0.3_direct_f64"], infos, 1.25, "probe")
+    assert r["bound"] == "alu" and r["peak"] == 1.25
+    assert abs(r["achieved"] - 2 * 1368 * 12 ** 4 / t / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 1.25) < 1e-12
+    wl = bench.WORKLOADS["lattice16_mu0.2_nrhs16_direct_f32"]
+    r = bench._roofline(wl, infos, 1.25, "probe")
+    peak = bench._peaks()[0]["hbm_gbs"]
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == peak
+    assert abs(r["achieved"] - bench.pair_bytes("f32", 16 ** 4, 16) / t / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / peak) < 1e-12
+
+
 def test_throughput_counts_every_rank():
     assert bench.throughput(steps=5, solves_per_step=3, world=2, max_ms=1000.0) == 30.0
 
